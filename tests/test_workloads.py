@@ -1,0 +1,56 @@
+"""Shape and structure of the seeded synthetic workloads."""
+import numpy as np
+
+import workloads as w
+from workloads.nodes import inside
+
+
+def test_cube_grid_counts():
+    ns = w.cube_grid(10)
+    assert (ns.n, ns.n_interior, ns.n_boundary) == (1000, 512, 488)
+    XI, XB = ns.X[:512], ns.X[512:]
+    assert np.all((XI > 0) & (XI < 1))
+    assert np.all(np.any((XB == 0) | (XB == 1), axis=1))
+
+
+def test_cube_halton_counts_and_unique_boundary():
+    ns = w.cube_faces_halton(8000, 21)
+    assert ns.n_boundary == 21 ** 3 - 19 ** 3 == 2402
+    assert ns.n_interior == 5598
+    B = ns.X[ns.n_interior:]
+    assert np.unique(B, axis=0).shape[0] == B.shape[0]
+    assert np.all((ns.X[:ns.n_interior] > 0) & (ns.X[:ns.n_interior] < 1))
+    assert np.array_equal(ns.X, w.cube_faces_halton(8000, 21).X)  # seeded
+
+
+def test_scrambled_halton_is_low_discrepancy():
+    P = w.scrambled_halton(4096, np.random.Generator(np.random.PCG64(1)))
+    # every 1/8-cube cell receives close to its share (Halton fills evenly)
+    cells = np.floor(P * 2).astype(int)
+    counts = np.bincount(cells[:, 0] * 4 + cells[:, 1] * 2 + cells[:, 2], minlength=8)
+    assert np.all(np.abs(counts - 512) <= 8)
+
+
+def test_sphere_set():
+    ns = w.sphere_fibonacci_ball(400, 1600, seed=11)
+    assert np.allclose(np.linalg.norm(ns.X[1600:], axis=1), 1.0)
+    assert np.all(np.linalg.norm(ns.X[:1600], axis=1) < 1.0)
+
+
+def test_batch_instances_ranges():
+    inst = w.batch_instances(12)
+    for ns in inst:
+        p = ns.params
+        assert 2000 <= ns.n <= 16000
+        assert 0.05 <= p["c"] <= 1.0 and 1.0 <= p["k"] <= 20.0
+        assert abs(np.linalg.norm(p["d"]) - 1) < 1e-12
+        share = ns.n_boundary / ns.n
+        assert (0.25 < share < 0.36) if ns.domain == "cube" else abs(share - 0.2) < 1e-3
+
+
+def test_pump_like_small():
+    ns = w.pump_like(300, 1200, seed=5)
+    assert ns.n == 1500
+    assert np.all(inside("pump", ns.X[:1200]))
+    P = w.test_points(ns, 200)
+    assert np.all(inside("pump", P))
