@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark: GKB steps/s and time-to-HKT-solution on one GB300 (or N replicas).
+
+Workload (default ``cube8000``): the N = 8000 Halton cube (21 x 21 face grid,
+2402 Dirichlet nodes, 5598 scrambled-Halton interior nodes), plane wave
+u = sin(k (x + y + z) / sqrt 3), FP64, assembled A (512 MB), 100 GKB steps, HKT
+with GCV, u at 2000 seeded test points.  One bench step = the six solves
+c in {0.1, 0.2, 0.5} x k in {2, 5}; each solve assembles A, runs GKB, the
+projected SVD, GCV, the projected solve, the lift and the reconstruction.
+
+value = GKB steps completed / device time (all ranks, max time over ranks).
+e2e   = the same metric through the C ABI with the step's inputs copied from
+        pinned host memory and u copied back inside the timed region.
+roofline: the dominant kernel is the matrix-vector product of the GKB; its
+        launches are timed live with CUDA events on the library stream.  The
+        FP64 product is bound by the FP64 pipe (1 FMA per 8-byte entry), so the
+        bound is "alu" with the peak 152 SMs x 2 FP64 FMA/clk x 2 flop x
+        2.07 GHz = 1.259 TFLOP/s; the HBM fraction is reported beside it.
+
+``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
+host cores, one full solve of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GKB steps/s and time-to-HKT-solution at N (fraction of HBM/FP32 roofline)"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # FP64 FMA pipe, max clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
+
+
+# --------------------------------------------------------------------------- workloads
+def workload(name):
+    import numpy as np
+
+    import workloads as w
+    if name == "cube8000":
+        ns = w.preset("cube8000")
+        cases = [(c, k) for c in (0.1, 0.2, 0.5) for k in (2.0, 5.0)]
+        steps, prec, storage = 100, "fp64", "assembled"
+    elif name == "cube8000-mixed-mf":
+        ns = w.preset("cube8000")
+        cases = [(c, k) for c in (0.1, 0.2, 0.5) for k in (2.0, 5.0)]
+        steps, prec, storage = 100, "mixed", "matrix_free"
+    elif name == "sphere20000":
+        ns = w.preset("sphere20000")
+        cases = [(0.15, 10.0)]
+        steps, prec, storage = 150, "mixed", "matrix_free"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    P = w.test_points(ns)
+    fs = {k: w.plane_wave_rhs(ns, k) for k in sorted({k for _, k in cases})}
+    return dict(name=name, ns=ns, cases=cases, steps=steps, precision=prec, storage=storage,
+                points=P, fs=fs, np=np)
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2511_09798_gb300 import pipeline as Pp
+    from paper_2511_09798_gb300 import rbfkr as R
+
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    wl = workload(args.workload)
+    ns, cases, L = wl["ns"], wl["cases"], wl["steps"]
+    prec = R.RBF_FP64 if wl["precision"] == "fp64" else R.RBF_MIXED
+    storage = R.RBF_ASSEMBLED if wl["storage"] == "assembled" else R.RBF_MATRIX_FREE
+    stream = torch.cuda.current_stream()
+    ctx = R.Context(local_rank, stream=stream, timing=2)
+    n, m = ns.n, wl["points"].shape[0]
+    # device-resident inputs
+    nodes_h = torch.from_numpy(ns.soa()).pin_memory()
+    pts_h = torch.from_numpy(np.ascontiguousarray(wl["points"].T)).pin_memory()
+    f_h = {k: torch.from_numpy(v).pin_memory() for k, v in wl["fs"].items()}
+    nodes_d = nodes_h.to(dev)
+    pts_d = pts_h.to(dev)
+    f_d = {k: v.to(dev) for k, v in f_h.items()}
+    lda = R.padded_lda(n, prec)
+    A = None
+    if storage == R.RBF_ASSEMBLED:
+        A = torch.empty((n, lda), dtype=torch.float64 if prec == R.RBF_FP64 else torch.float32, device=dev)
+    st, W, Z, al, be = R.make_state(torch, n, L, dev)
+    coef = torch.empty(n, dtype=torch.float64, device=dev)
+    u_d = torch.empty((len(cases), m), dtype=torch.float64, device=dev)
+    u_h = torch.empty((len(cases), m), dtype=torch.float64).pin_memory()
+
+    def one_step(e2e=False):
+        done = 0
+        if e2e:
+            nodes_d.copy_(nodes_h, non_blocking=True)
+            pts_d.copy_(pts_h, non_blocking=True)
+            for k in f_d:
+                f_d[k].copy_(f_h[k], non_blocking=True)
+        for ci, (c, k) in enumerate(cases):
+            op = ctx.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, storage, prec, R.RBF_FORM_C,
+                                       A, lda if A is not None else 0)
+            if A is not None:
+                ctx.rbf_assemble(op)
+            ctx.rbf_gkb(op, f_d[k], L, st)
+            done += st.steps_done
+            ctx.rbf_hkt(st, R.RBF_GCV, 0.0, coef)
+            ctx.rbf_evaluate(op, coef, pts_d, m, u_d[ci])
+        if e2e:
+            u_h.copy_(u_d, non_blocking=True)
+        return done
+
+    def timed(k_steps, e2e):
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        done = 0
+        for _ in range(k_steps):
+            done += one_step(e2e)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+            d = torch.tensor([done], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(d)
+            done = int(d.item())
+        return ms, done
+
+    for _ in range(args.warmup):
+        one_step()
+    ctx.rbf_get_counters(reset=True)
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms, done = timed(args.steps, False)
+    clocks = sampler.stop() if sampler else None
+    cnt = ctx.rbf_get_counters(reset=True)
+    ms_e2e, done_e2e = timed(args.steps, True)
+    # phase shares (separate context with synchronising per-phase timers)
+    ctx_ph = R.Context(local_rank, stream=stream, timing=1)
+    phases = {}
+    for ci, (c, k) in enumerate(cases[:1]):
+        op = ctx_ph.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, storage, prec, R.RBF_FORM_C,
+                                      A, lda if A is not None else 0)
+        t0 = time.perf_counter()
+        if A is not None:
+            ctx_ph.rbf_assemble(op)
+        ctx_ph.rbf_gkb(op, f_d[k], L, st)
+        ctx_ph.rbf_hkt(st, R.RBF_GCV, 0.0, coef)
+        ctx_ph.rbf_evaluate(op, coef, pts_d, m, u_d[ci])
+        phases = ctx_ph.rbf_get_timings()
+    ctx_ph.close()
+    if rank != 0:
+        return None
+    peaks = measured_peaks()
+    solves = args.steps * len(cases) * world
+    value = done / (ms / 1e3)
+    # dominant kernel: the GKB products (A z and A^T w)
+    p_ms, p_cnt = cnt["product_ms"], cnt["product_launches"]
+    kinds = ["gemv_n (p = A z)", "gemv_t (r = A^T w)"]
+    dom = 0 if p_ms[0] >= p_ms[1] else 1
+    avg_ms = p_ms[dom] / max(1, p_cnt[dom])
+    both_avg_ms = (p_ms[0] + p_ms[1]) / max(1, p_cnt[0] + p_cnt[1])
+    s = 8 if prec == R.RBF_FP64 else 4
+    if storage == R.RBF_ASSEMBLED:
+        alg_bytes = s * n * n
+        gbs = alg_bytes / (avg_ms / 1e3) / 1e9
+        if prec == R.RBF_FP64:
+            tflops = 2.0 * n * n / (avg_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                    "pipe": "fp64 (2 FMA/clk/SM; 1 FMA per 8-byte entry)",
+                    "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)",
+                    "hbm_achieved_gbs": round(gbs, 1), "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                    "hbm_frac": round(gbs / peaks.get("hbm_gbs", 6790.7), 4)}
+        else:
+            roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": round(gbs / peaks.get("hbm_gbs", 6790.7), 4), "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    else:
+        ent = n * n / (avg_ms / 1e3)
+        # 12 FP32-pipe operations + 1 MUFU rsqrt per regenerated entry
+        tflops = ent * 12 / 1e12
+        roof = {"bound": "alu", "achieved": round(tflops, 3), "peak": round(FP32_PEAK_TFLOPS, 3),
+                "unit": "TFLOP/s", "frac": round(tflops / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "entries_per_s": ent, "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts)"}
+    roof.update({"kernel": kinds[dom], "avg_launch_ms": round(avg_ms, 5),
+                 "avg_launch_ms_both": round(both_avg_ms, 5), "launches_timed": int(p_cnt[0] + p_cnt[1]),
+                 "algorithmic_per_launch": (f"{s * n * n} bytes, {2 * n * n} flop" if storage == R.RBF_ASSEMBLED
+                                            else f"{n * n} entries")})
+    h2d = nodes_h.numel() * 8 + pts_h.numel() * 8 + sum(v.numel() * 8 for v in f_h.values())
+    d2h = u_h.numel() * 8
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GKB steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == R.RBF_FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "n": n, "n_interior": ns.n_interior, "gkb_steps": L,
+                   "cases_c_k": cases, "solves_per_step": len(cases), "precision": wl["precision"],
+                   "storage": wl["storage"], "rule": "gcv", "test_points": m,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (A or node set streamed each product)"},
+        "time_to_solution_ms": round(ms / (args.steps * len(cases)), 3),
+        "gkb_steps_done": done, "solves": solves,
+        "roofline": roof,
+        "e2e": {"value": round(done_e2e / (ms_e2e / 1e3), 2), "unit": "GKB steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": round(ms_e2e / args.steps, 3)},
+        "gpu_launches": int(cnt["launches"]),
+        "phase_ms_one_solve": {k: round(v, 3) for k, v in phases.items() if k.endswith("_ms")},
+        "clocks": clocks,
+    }
+    ctx.close()
+    return out
+
+
+# --------------------------------------------------------------------------- oracle
+def oracle_solve(wl, c, k, steps):
+    from oracle import evaluate as OE
+    from oracle import gkb as OG
+    from oracle import mq as OM
+    from oracle import regularize as OR
+    ns = wl["ns"]
+    A = OM.assemble(ns.X, ns.n_interior, c, k)
+    g = OG.gkb(A, None, wl["fs"][k], steps)
+    h = OR.hkt(g, "gcv")
+    OE.reconstruct(h["coef"], ns.X, wl["points"], c)
+    return g.steps_done
+
+
+def cpu_baseline(wl, sample_steps):
+    if wl["ns"].n > 10000:
+        sample_steps = min(sample_steps, 10)
+    c, k = wl["cases"][0]
+    t0 = time.perf_counter()
+    done = oracle_solve(wl, c, k, sample_steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt, 3), "unit": "GKB steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one full solve (assemble, {sample_steps} GKB steps, SVD, GCV, lift, u at "
+                      f"{wl['points'].shape[0]} points) of {wl['name']} at c={c}, k={k}: {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    wl = workload(args.workload)
+    L = wl["steps"]
+    c, k = wl["cases"][0]
+    for _ in range(args.warmup):
+        oracle_solve(wl, c, k, L)
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(args.steps):
+        done += oracle_solve(wl, c, k, L)
+    dt = time.perf_counter() - t0
+    v = round(done / dt, 3)
+    return {"metric": METRIC, "value": v, "unit": "GKB steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl["name"], "n": wl["ns"].n, "gkb_steps": L, "cases_c_k": [(c, k)],
+                       "solves_per_step": 1, "precision": "fp64", "storage": "assembled", "rule": "gcv"},
+            "cpu_baseline": {"value": v, "unit": "GKB steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"one full solve of {wl['name']} at c={c}, k={k} per step"},
+            "e2e": {"value": v, "unit": "GKB steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def single_solve(args):
+    import torch
+
+    from paper_2511_09798_gb300 import rbfkr as R
+    wl = workload(args.workload)
+    ns, (c, k), L = wl["ns"], wl["cases"][0], wl["steps"]
+    prec = R.RBF_FP64 if wl["precision"] == "fp64" else R.RBF_MIXED
+    storage = R.RBF_ASSEMBLED if wl["storage"] == "assembled" else R.RBF_MATRIX_FREE
+    ctx = R.Context(0)
+    n, m = ns.n, wl["points"].shape[0]
+    nodes = torch.from_numpy(ns.soa()).cuda()
+    pts = torch.from_numpy(wl["points"].T.copy()).cuda()
+    f = torch.from_numpy(wl["fs"][k]).cuda()
+    lda = R.padded_lda(n, prec)
+    A = None
+    if storage == R.RBF_ASSEMBLED:
+        A = torch.empty((n, lda), dtype=torch.float64 if prec == R.RBF_FP64 else torch.float32, device="cuda")
+    st, *_ = R.make_state(torch, n, L)
+    coef = torch.empty(n, dtype=torch.float64, device="cuda")
+    u = torch.empty(m, dtype=torch.float64, device="cuda")
+    op = ctx.rbf_operator_init(nodes, n, ns.n_interior, c, k, storage, prec, R.RBF_FORM_C, A,
+                               lda if A is not None else 0)
+    if A is not None:
+        ctx.rbf_assemble(op)
+    ctx.rbf_gkb(op, f, L, st)
+    info = ctx.rbf_hkt(st, R.RBF_GCV, 0.0, coef)
+    ctx.rbf_evaluate(op, coef, pts, m, u)
+    torch.cuda.synchronize()
+    print(json.dumps({"single_solve": wl["name"], "steps_done": st.steps_done, "lambda": info.lambda_,
+                      "index": info.index, "launches": ctx.rbf_get_counters()["launches"]}))
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cube8000")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single-solve", action="store_true",
+                    help="run one untimed solve of the first case and exit (profiling target)")
+    args = ap.parse_args()
+    if args.single_solve:
+        single_solve(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+        if out is not None and not args.no_cpu_baseline:
+            wl = workload(args.workload)
+            out["cpu_baseline"] = cpu_baseline(wl, wl["steps"])
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

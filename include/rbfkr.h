@@ -1,0 +1,255 @@
+/*
+ * rbfkr.h -- C ABI of the GB300 (sm_103a) Krylov-regularization library for
+ * multiquadric (MQ) RBF Kansa collocation of the 3D Helmholtz equation.
+ *
+ * What it computes (arXiv 2511.09798):
+ *   - the Kansa collocation matrix A = [H; R] with MQ basis Phi(r) =
+ *     sqrt(r^2 + c^2): interior rows L Phi = Delta Phi + k^2 Phi, Dirichlet rows
+ *     Phi (Sec. 2.1, eqs. MQ, Lphi, H_entries, augmented_system);
+ *   - Golub-Kahan bidiagonalization with full reorthogonalization
+ *     (Algorithm 1, Sec. 3.1);
+ *   - the projected SVD C_l = U~ S~ V~^T, projected GCV / L-curve choice of
+ *     lambda, Hybrid Krylov-Tikhonov (Algorithm 4) and inexpensive TSVD
+ *     (Algorithm 2), lifted to coefficients alpha = Z_l y;
+ *   - reconstruction u(X) = sum_j alpha_j Phi(|X - X_j|) (eq. u_reconstruction).
+ *
+ * Conventions (all entry points):
+ *   - Every pointer named d_* is DEVICE memory owned by the caller, on the
+ *     device the context was created for.  The library owns only the internal
+ *     workspace it allocates inside the context (see rbf_workspace_bytes).
+ *   - Node coordinates are FP64 structure-of-arrays [3][n]: x[0..n), then
+ *     y[0..n), then z[0..n); interior (PDE) nodes first, boundary (Dirichlet)
+ *     nodes last.  Centres and collocation points coincide.
+ *   - Dense matrices are row-major with a leading dimension (lda >= n).
+ *     Krylov bases are column-major (each basis vector contiguous, ld >= n).
+ *   - Work is enqueued on the stream given to rbf_create.  Calls that return a
+ *     host scalar (steps done, lambda, rank) synchronise that stream; the
+ *     others do not.
+ *   - Errors are return codes; nothing throws across the ABI.  The message of
+ *     the last failure is available from rbf_last_error.  Asynchronous CUDA
+ *     errors surface at the next synchronising call as RBF_ERR_CUDA.
+ *   - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef RBFKR_H
+#define RBFKR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RBF_OK = 0,
+    RBF_ERR_INVALID = 1,     /* bad argument (size, pointer, parameter range) */
+    RBF_ERR_OOM = 2,         /* workspace allocation failed or exceeds the cap */
+    RBF_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    RBF_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    RBF_ERR_UNSUPPORTED = 5, /* combination not implemented */
+    RBF_ERR_INTERNAL = 6     /* device-side consistency check failed */
+} rbf_status;
+
+typedef enum {
+    RBF_FP64 = 0,  /* every step in IEEE FP64 */
+    RBF_MIXED = 1  /* matrix entries and A*x / A^T*y in FP32 (partial sums of
+                      short FP32 runs combined in FP64); reorthogonalization,
+                      norms, alpha/beta, projected SVD and GCV in FP64 */
+} rbf_precision;
+
+typedef enum {
+    RBF_ASSEMBLED = 0,   /* A stored densely (caller-owned buffer) */
+    RBF_MATRIX_FREE = 1  /* entries regenerated from node coordinates per product */
+} rbf_storage;
+
+typedef enum {
+    RBF_GCV = 0,     /* argmin of the projected GCV on the lambda grid (eq. gcv_proj) */
+    RBF_LCURVE = 1,  /* max discrete curvature of (ln rho_l, ln eta_l) on the grid */
+    RBF_FIXED = 2    /* lambda supplied by the caller */
+} rbf_rule;
+
+typedef enum {
+    RBF_FORM_C = 0,   /* Phi(r) = sqrt(r^2 + c^2) */
+    RBF_FORM_EPS = 1  /* phi(r; eps) = sqrt(1 + eps^2 r^2), eps = 1/c (eq. MQ): entries / c */
+} rbf_form;
+
+typedef struct rbf_ctx rbf_ctx;
+
+/* Options fixed at context creation.  Zero-initialised fields take defaults. */
+typedef struct {
+    int grid_j;              /* lambda grid points J (default 321) */
+    double grid_t_lo;        /* grid: lambda = s~_1 * 10^t, t in [t_lo, t_hi] (default -16) */
+    double grid_t_hi;        /* (default 0; used only when t_lo < t_hi) */
+    double breakdown_factor; /* tau = factor * N * eps * c_hat (default 64) */
+    double cluster_tol;      /* relative gap under which Ritz values are treated
+                                as a cluster in the projected SVD (default 1e-3) */
+    int64_t workspace_cap;   /* max workspace bytes, 0 = unlimited */
+    int timing;              /* bit 0: per-phase CUDA-event timings (synchronises at
+                                each phase end); bit 1: time every GKB product launch
+                                with CUDA events, no synchronisation (rbf_counters) */
+} rbf_options;
+
+/* Operator description; filled by rbf_operator_init. */
+typedef struct {
+    const double* d_nodes; /* device FP64 SoA [3][n] */
+    int64_t n;             /* number of nodes (= rows = columns of A) */
+    int64_t n_interior;    /* rows [0, n_interior) are PDE rows, the rest Dirichlet */
+    double c;              /* MQ shape parameter (c-form) */
+    double k;              /* wavenumber */
+    int storage;           /* rbf_storage */
+    int precision;         /* rbf_precision */
+    int form;              /* rbf_form */
+    void* d_A;             /* device, caller-owned: double (FP64) or float (MIXED),
+                              row-major n x lda; NULL for RBF_MATRIX_FREE */
+    int64_t lda;           /* leading dimension in elements; even (FP64) or a
+                              multiple of 4 (FP32); d_A 16-byte aligned */
+} rbf_operator;
+
+/* Golub-Kahan state.  The caller owns W, Z, alpha, beta (device).  The
+ * scalar fields steps_done / breakdown / c_hat are written by rbf_gkb and
+ * rbf_gkb_resume when they return. */
+typedef struct {
+    double* d_W;      /* n x (capacity+1), column-major, ld = ldw: w_1 .. w_{l+1} */
+    int64_t ldw;
+    double* d_Z;      /* n x capacity, column-major, ld = ldz: z_1 .. z_l */
+    int64_t ldz;
+    double* d_alpha;  /* [capacity]:   d_alpha[j-1] = alpha_j */
+    double* d_beta;   /* [capacity+1]: d_beta[j-1]  = beta_j (beta_1 = |f|) */
+    int capacity;     /* maximum number of steps the buffers hold */
+    int64_t n;
+    int steps_done;   /* l: completed steps */
+    int breakdown;    /* 0 none; 1 alpha_j <= tau (l = j-1); 2 beta_{j+1} <= tau (l = j,
+                         beta_{l+1} = 0, w_{l+1} = 0) */
+    double c_hat;     /* running estimate of |A|_2 used by the breakdown test */
+} rbf_gkb_state;
+
+/* Host-side results of a regularized solve. */
+typedef struct {
+    double lambda;   /* lambda used (HKT) */
+    int index;       /* grid index of lambda (-1 for RBF_FIXED) */
+    int rank;        /* truncation rank (Ine-TSVD) */
+    int steps;       /* l, the projected dimension used */
+    double sigma1;   /* largest Ritz value s~_1 */
+} rbf_solve_info;
+
+/* Per-phase device time of the last calls, milliseconds (timing option). */
+typedef struct {
+    double assemble_ms;
+    double gkb_ms;
+    double svd_ms;
+    double select_ms;  /* GCV / L-curve / rank choice and projected solve */
+    double lift_ms;
+    double evaluate_ms;
+    int gkb_steps;
+} rbf_timings;
+
+/* Counters since creation or the last reset: kernel launches made by the
+ * library, and (when bit 1 of opt.timing is set) the device time of the GKB matrix-vector
+ * product launches, measured with CUDA events recorded on the context stream
+ * around each product (index 0: p = A z, index 1: r = A^T w). */
+typedef struct {
+    int64_t launches;           /* every kernel launch issued by the library */
+    int64_t product_launches[2];/* timed product launches (A, A^T) */
+    double product_ms[2];       /* their summed device time, milliseconds */
+} rbf_counters;
+
+/* ---- context --------------------------------------------------------- */
+
+/* Create a context on `device` enqueuing on `cuda_stream` (a cudaStream_t, or
+ * NULL for the legacy default stream).  `opt` may be NULL (defaults).
+ * Errors: RBF_ERR_INVALID (ctx NULL), RBF_ERR_CUDA (device unusable). */
+rbf_status rbf_create(rbf_ctx** ctx, int device, void* cuda_stream, const rbf_options* opt);
+
+/* Release the context and its workspace.  NULL is accepted. */
+rbf_status rbf_destroy(rbf_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none). */
+const char* rbf_last_error(const rbf_ctx* ctx);
+
+/* Upper bound of the internal workspace bytes for a GKB of `steps` steps plus
+ * the projected solve, for an operator of size n. */
+size_t rbf_workspace_bytes(const rbf_ctx* ctx, int64_t n, int steps, int storage, int precision);
+
+/* Timings of the most recent calls (zeros unless opt.timing was set). */
+rbf_status rbf_get_timings(const rbf_ctx* ctx, rbf_timings* out);
+
+/* Read the counters (synchronises the stream when product timing is on) and
+ * reset them to zero when `reset` is non-zero.  Product timing keeps at most
+ * 8192 launches per reset; later launches are counted but not timed. */
+rbf_status rbf_get_counters(rbf_ctx* ctx, rbf_counters* out, int reset);
+
+/* ---- operator ------------------------------------------------------- */
+
+/* Fill *op after validating the arguments (Sec. 2.1: centres = collocation
+ * points, interior rows first).  No device work.  Errors: RBF_ERR_INVALID for
+ * n <= 0, n_interior outside [0, n], c <= 0, k < 0, d_nodes NULL, an assembled
+ * operator without d_A, lda < n or misaligned, unknown enum values. */
+rbf_status rbf_operator_init(rbf_ctx* ctx, rbf_operator* op, const double* d_nodes, int64_t n,
+                             int64_t n_interior, double c, double k, int storage, int precision,
+                             int form, void* d_A, int64_t lda);
+
+/* Fill the caller's d_A with the collocation matrix (eqs. H_entries,
+ * augmented_system): FP64 or FP32 entries by op->precision.  Assembled
+ * operators only (RBF_ERR_INVALID otherwise). */
+rbf_status rbf_assemble(rbf_ctx* ctx, const rbf_operator* op);
+
+/* d_y = A d_x (trans = 0) or d_y = A^T d_x (trans = 1), FP64 vectors of length
+ * n; the product runs in the operator's precision and storage (the matrix-vector
+ * product of Algorithm 1, steps r = A^T w and p = A z). */
+rbf_status rbf_matvec(rbf_ctx* ctx, const rbf_operator* op, int trans, const double* d_x, double* d_y);
+
+/* ---- Golub-Kahan bidiagonalization (Algorithm 1) --------------------- */
+
+/* Run `steps` steps from beta_1 = |f|, w_1 = f / beta_1 into *st (capacity >=
+ * steps, buffers sized for n = op->n).  Full reorthogonalization of r against
+ * z_1..z_{j-1} before alpha_j and of p against w_1..w_j before beta_{j+1}
+ * (classical Gram-Schmidt applied twice).  Stops early on breakdown (tau =
+ * factor * N * eps * c_hat).  Synchronises the stream to return steps_done. */
+rbf_status rbf_gkb(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int steps,
+                   rbf_gkb_state* st);
+
+/* Continue a state produced by rbf_gkb for `more_steps` further steps (same
+ * operator); a state that already broke down is returned unchanged. */
+rbf_status rbf_gkb_resume(rbf_ctx* ctx, const rbf_operator* op, rbf_gkb_state* st, int more_steps);
+
+/* ---- projected problem (Algorithms 2 and 4) -------------------------- */
+
+/* SVD of the (l+1) x l lower bidiagonal C_l of *st (l = st->steps_done):
+ * d_sigma[l] (descending), d_ftil[l+1] = U~^T (beta_1 e_1), d_V (l x l,
+ * column-major, ld = ldv >= l, columns v~_i).  FP64. */
+rbf_status rbf_projected_svd(rbf_ctx* ctx, const rbf_gkb_state* st, double* d_sigma, double* d_ftil,
+                             double* d_V, int64_t ldv);
+
+/* Hybrid Krylov-Tikhonov (Algorithm 4): choose lambda by `rule` on the grid
+ * lambda = s~_1 10^t (or take lambda_in for RBF_FIXED), solve the projected
+ * Tikhonov problem and lift: d_coef[n] = Z_l y_lambda.  d_curve (optional,
+ * length J) receives GCV_l on the grid (RBF_GCV) or the curvature (RBF_LCURVE,
+ * end points = -inf).  Synchronises; fills *info. */
+rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in,
+                   double* d_coef, double* d_curve, rbf_solve_info* info);
+
+/* Inexpensive TSVD (Algorithm 2): rank by GCV_l(k) when rank == 0, else the
+ * given rank (1..l); d_coef[n] = Z_l V~_k S~_k^{-1} f~_{1:k}.  d_curve
+ * (optional, length l) receives GCV_l(k).  Synchronises; fills *info. */
+rbf_status rbf_ine_tsvd(rbf_ctx* ctx, const rbf_gkb_state* st, int rank, double* d_coef,
+                        double* d_curve, rbf_solve_info* info);
+
+/* Full-SVD Tikhonov / TSVD (Algorithm 3, eq. tsvd_solution): not implemented
+ * on the GPU; returns RBF_ERR_UNSUPPORTED. */
+rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int rule,
+                        double lambda_in, double* d_coef, rbf_solve_info* info);
+
+/* ---- reconstruction (eq. u_reconstruction) --------------------------- */
+
+/* d_u[m] = sum_j d_coef[j] Phi(|P_t - X_j|) at the m points d_points (FP64 SoA
+ * [3][m]).  Always FP64 (also for RBF_MIXED operators): the coefficients of an
+ * ill-conditioned collocation system cancel, so FP32 basis values would lose
+ * the reconstruction.  Uses the operator's form (c or eps). */
+rbf_status rbf_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* d_coef,
+                        const double* d_points, int64_t m, double* d_u);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBFKR_H */

@@ -28,8 +28,10 @@ Readings where the paper is silent or ambiguous:
   curvature kappa = (x' y'' - x'' y') / (x'^2 + y'^2)^{3/2} with central
   differences in t over interior grid points; the corner is argmax kappa
   (positive at the corner when lambda increases along the curve).  Samples
-  where the curvature is undefined (zero speed: the curve is numerically
-  constant there) are not candidates.
+  where the curve is stationary -- speed |(x', y')| below 1e-4 per decade of
+  lambda, e.g. where rho and eta no longer change for lambda far below every
+  s~_i -- have no meaningful curvature (rounding noise over a vanishing speed)
+  and are not candidates; neither are samples where it is undefined.
 * Ine-TSVD rank (the paper allows Picard plot, discrepancy or GCV; Sec. 5 uses
   GCV throughout): GCV_l(k) = (sum_{i=k+1}^{l} f~_i^2 + f~_{l+1}^2) / ((l+1) - k)^2,
   argmin over k = 1..r_l with r_l = #{s~_i > (l+1) eps s~_1}, smallest k on ties.
@@ -46,6 +48,9 @@ import numpy as np
 
 EPS = np.finfo(np.float64).eps
 GRID_T_LO, GRID_T_HI, GRID_J = -16.0, 0.0, 321
+# L-curve points whose speed |d(ln rho, ln eta)/dt| is below 1e-4 per decade are
+# stationary: their discrete curvature is rounding noise over a vanishing speed.
+LCURVE_MIN_SPEED2 = 1e-8
 
 
 def lambda_grid(s1, J=GRID_J, t_lo=GRID_T_LO, t_hi=GRID_T_HI):
@@ -146,11 +151,13 @@ def choose_lambda_proj(ps: ProjectedSVD, rule="gcv", J=GRID_J):
         i = _argmin_first(g)
         return grid[i], i, grid, g
     if rule == "lcurve":
+        h = t[1] - t[0]
         with np.errstate(divide="ignore", invalid="ignore"):
             x = 0.5 * np.log(rho2_proj(ps, grid))
             y = 0.5 * np.log(eta2_proj(ps, grid))
-            kap = lcurve_curvature(x, y, t[1] - t[0])
-        kap = np.where(np.isfinite(kap), kap, -np.inf)
+            kap = lcurve_curvature(x, y, h)
+            speed2 = ((x[2:] - x[:-2]) / (2 * h)) ** 2 + ((y[2:] - y[:-2]) / (2 * h)) ** 2
+        kap = np.where(np.isfinite(kap) & (speed2 >= LCURVE_MIN_SPEED2), kap, -np.inf)
         m = np.max(kap)
         i = int(np.flatnonzero(kap == m)[0]) + 1
         return grid[i], i, grid, kap

@@ -1,0 +1,40 @@
+// Device helpers shared by the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define RBF_FULL_MASK 0xffffffffu
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(RBF_FULL_MASK, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(RBF_FULL_MASK, v, o);
+    return v;
+}
+
+// 1/sqrt(x) in FP64 for x in the normal float range: an FP32 hardware
+// estimate refined by one third-order step of the Newton iteration for
+// y = x^{-1/2}: with e = 1 - x y0^2, y = y0 (1 + e/2 + 3 e^2 / 8), which
+// cubes the relative error of y0 (about 2^-22) to below FP64 rounding.
+__device__ __forceinline__ double rsqrt_f64(double x) {
+    double y0 = (double)rsqrtf((float)x);
+    double t = x * y0;
+    double e = fma(-t, y0, 1.0);
+    double c = fma(0.375, e, 0.5);
+    return fma(y0 * e, c, y0);
+}
+
+__device__ __forceinline__ unsigned sign_bit(double v) {
+    return ((unsigned)__double2hiint(v)) >> 31;
+}
+
+// Done flag of a GKB run: every GKB kernel returns immediately once set.
+__device__ __forceinline__ bool gkb_done(const int* done) {
+    return done != nullptr && *(volatile const int*)done != 0;
+}

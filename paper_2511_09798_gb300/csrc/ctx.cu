@@ -1,0 +1,236 @@
+// Context, workspace, errors, timings and operator validation.
+#include <cstdlib>
+#include <cstring>
+
+#include "internal.h"
+
+rbf_status rbf_fail(rbf_ctx* ctx, rbf_status st, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+rbf_status rbf_ws_reserve(rbf_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes) return RBF_OK;
+    if (ctx->opt.workspace_cap > 0 && bytes > (size_t)ctx->opt.workspace_cap)
+        return rbf_fail(ctx, RBF_ERR_OOM, "workspace of %zu bytes exceeds the cap of %lld bytes",
+                        bytes, (long long)ctx->opt.workspace_cap);
+    if (ctx->ws) {
+        RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        RBF_CUDA(ctx, cudaFree(ctx->ws));
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    size_t grow = bytes + bytes / 4;
+    cudaError_t e = cudaMalloc(&ctx->ws, grow);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ws = nullptr;
+        return rbf_fail(ctx, RBF_ERR_OOM, "cudaMalloc of %zu workspace bytes failed: %s", grow,
+                        cudaGetErrorString(e));
+    }
+    ctx->ws_bytes = grow;
+    return RBF_OK;
+}
+
+int rbf_prod_begin(rbf_ctx* ctx, int trans) {
+    ctx->ptotal[trans]++;
+    if (!(ctx->opt.timing & 2) || !ctx->pev || ctx->pcount[trans] >= rbf_ctx::PMAX) return -1;
+    const int slot = ctx->pcount[trans]++;
+    cudaEventRecord(ctx->pev[((size_t)trans * rbf_ctx::PMAX + slot) * 2], ctx->stream);
+    return slot;
+}
+
+void rbf_prod_end(rbf_ctx* ctx, int trans, int slot) {
+    if (slot < 0) return;
+    cudaEventRecord(ctx->pev[((size_t)trans * rbf_ctx::PMAX + slot) * 2 + 1], ctx->stream);
+}
+
+void rbf_timer_start(rbf_ctx* ctx) {
+    if (ctx->opt.timing & 1) cudaEventRecord(ctx->ev[0], ctx->stream);
+}
+
+double rbf_timer_stop(rbf_ctx* ctx) {
+    if (!(ctx->opt.timing & 1)) return 0.0;
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    cudaEventSynchronize(ctx->ev[1]);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    return (double)ms;
+}
+
+extern "C" {
+
+rbf_status rbf_create(rbf_ctx** out, int device, void* cuda_stream, const rbf_options* opt) {
+    if (!out) return RBF_ERR_INVALID;
+    *out = nullptr;
+    rbf_ctx* ctx = new rbf_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if (opt) ctx->opt = *opt;
+    if (ctx->opt.grid_j <= 0) ctx->opt.grid_j = 321;
+    if (!(ctx->opt.grid_t_lo < ctx->opt.grid_t_hi)) {
+        ctx->opt.grid_t_lo = -16.0;
+        ctx->opt.grid_t_hi = 0.0;
+    }
+    if (ctx->opt.breakdown_factor <= 0) ctx->opt.breakdown_factor = 64.0;
+    if (ctx->opt.cluster_tol <= 0) ctx->opt.cluster_tol = 1e-3;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_state, sizeof(rbf_dev_state));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_state, sizeof(rbf_dev_state));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_state, 0, sizeof(rbf_dev_state));
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev[1]);
+    if (e == cudaSuccess && (ctx->opt.timing & 2)) {
+        const size_t ne = (size_t)2 * rbf_ctx::PMAX * 2;
+        ctx->pev = new cudaEvent_t[ne]();
+        for (size_t i = 0; i < ne && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->pev[i]);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rbf_destroy(ctx);
+        return RBF_ERR_CUDA;
+    }
+    *out = ctx;
+    return RBF_OK;
+}
+
+rbf_status rbf_get_counters(rbf_ctx* ctx, rbf_counters* out, int reset) {
+    if (!ctx || !out) return RBF_ERR_INVALID;
+    out->launches = ctx->launches;
+    for (int t = 0; t < 2; ++t) {
+        out->product_launches[t] = ctx->pcount[t];
+        out->product_ms[t] = 0.0;
+    }
+    if (ctx->pev && (ctx->pcount[0] || ctx->pcount[1])) {
+        RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int t = 0; t < 2; ++t)
+            for (int i = 0; i < ctx->pcount[t]; ++i) {
+                float ms = 0.f;
+                const size_t b = ((size_t)t * rbf_ctx::PMAX + i) * 2;
+                RBF_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->pev[b], ctx->pev[b + 1]));
+                out->product_ms[t] += ms;
+            }
+    }
+    if (reset) {
+        ctx->launches = 0;
+        ctx->pcount[0] = ctx->pcount[1] = 0;
+        ctx->ptotal[0] = ctx->ptotal[1] = 0;
+    }
+    return RBF_OK;
+}
+
+rbf_status rbf_destroy(rbf_ctx* ctx) {
+    if (!ctx) return RBF_OK;
+    if (ctx->stream || ctx->d_state) cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_state) cudaFree(ctx->d_state);
+    if (ctx->h_state) cudaFreeHost(ctx->h_state);
+    for (auto& ev : ctx->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (ctx->pev) {
+        for (size_t i = 0; i < (size_t)2 * rbf_ctx::PMAX * 2; ++i)
+            if (ctx->pev[i]) cudaEventDestroy(ctx->pev[i]);
+        delete[] ctx->pev;
+    }
+    delete ctx;
+    return RBF_OK;
+}
+
+const char* rbf_last_error(const rbf_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+rbf_status rbf_get_timings(const rbf_ctx* ctx, rbf_timings* out) {
+    if (!ctx || !out) return RBF_ERR_INVALID;
+    *out = ctx->tim;
+    return RBF_OK;
+}
+
+size_t rbf_workspace_bytes(const rbf_ctx* ctx, int64_t n, int steps, int storage, int precision) {
+    (void)storage;
+    if (!ctx || n <= 0 || steps <= 0) return 0;
+    size_t a = gkb_ws_bytes(ctx, n, steps, precision);
+    size_t b = svd_ws_bytes(steps) + select_ws_bytes(ctx, steps);
+    size_t c = gemv_ws_bytes(ctx, n) + ws_align((size_t)n * 8) * 2 + 4096;
+    size_t m = a > b ? a : b;
+    return m > c ? m : c;
+}
+
+rbf_status rbf_operator_init(rbf_ctx* ctx, rbf_operator* op, const double* d_nodes, int64_t n,
+                             int64_t n_interior, double c, double k, int storage, int precision,
+                             int form, void* d_A, int64_t lda) {
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!op) return rbf_fail(ctx, RBF_ERR_INVALID, "op is NULL");
+    if (!d_nodes) return rbf_fail(ctx, RBF_ERR_INVALID, "d_nodes is NULL");
+    if (n <= 0) return rbf_fail(ctx, RBF_ERR_INVALID, "n must be positive (got %lld)", (long long)n);
+    if (n > ((int64_t)1 << 31) - 1)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "n too large (%lld)", (long long)n);
+    if (n_interior < 0 || n_interior > n)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "n_interior %lld outside [0, n]", (long long)n_interior);
+    if (!(c > 0.0)) return rbf_fail(ctx, RBF_ERR_INVALID, "c must be positive");
+    if (!(k >= 0.0)) return rbf_fail(ctx, RBF_ERR_INVALID, "k must be non-negative");
+    if (storage != RBF_ASSEMBLED && storage != RBF_MATRIX_FREE)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "unknown storage %d", storage);
+    if (precision != RBF_FP64 && precision != RBF_MIXED)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "unknown precision %d", precision);
+    if (form != RBF_FORM_C && form != RBF_FORM_EPS)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "unknown form %d", form);
+    if (storage == RBF_ASSEMBLED) {
+        if (!d_A) return rbf_fail(ctx, RBF_ERR_INVALID, "assembled operator needs d_A");
+        if (lda < n) return rbf_fail(ctx, RBF_ERR_INVALID, "lda %lld < n %lld", (long long)lda, (long long)n);
+        int vec = precision == RBF_FP64 ? 2 : 4;
+        if (lda % vec != 0 || ((uintptr_t)d_A & 15u) != 0)
+            return rbf_fail(ctx, RBF_ERR_INVALID,
+                            "d_A must be 16-byte aligned and lda a multiple of %d elements", vec);
+    } else if (precision == RBF_FP64) {
+        return rbf_fail(ctx, RBF_ERR_UNSUPPORTED,
+                        "matrix-free operators regenerate entries in FP32: use RBF_MIXED");
+    }
+    op->d_nodes = d_nodes;
+    op->n = n;
+    op->n_interior = n_interior;
+    op->c = c;
+    op->k = k;
+    op->storage = storage;
+    op->precision = precision;
+    op->form = form;
+    op->d_A = storage == RBF_ASSEMBLED ? d_A : nullptr;
+    op->lda = storage == RBF_ASSEMBLED ? lda : 0;
+    return RBF_OK;
+}
+
+rbf_status rbf_assemble(rbf_ctx* ctx, const rbf_operator* op) {
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!op || op->storage != RBF_ASSEMBLED || !op->d_A)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_assemble needs an assembled operator");
+    rbf_timer_start(ctx);
+    RBF_TRY(launch_assemble(ctx, op));
+    ctx->tim.assemble_ms = rbf_timer_stop(ctx);
+    return RBF_OK;
+}
+
+rbf_status rbf_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* d_coef,
+                        const double* d_points, int64_t m, double* d_u) {
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!op || !d_coef || !d_points || !d_u)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_evaluate: NULL argument");
+    if (m <= 0) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_evaluate: m must be positive");
+    rbf_timer_start(ctx);
+    RBF_TRY(launch_evaluate(ctx, op, d_coef, d_points, m, d_u));
+    ctx->tim.evaluate_ms = rbf_timer_stop(ctx);
+    return RBF_OK;
+}
+
+rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int rule,
+                        double lambda_in, double* d_coef, rbf_solve_info* info) {
+    (void)op; (void)d_f; (void)rule; (void)lambda_in; (void)d_coef; (void)info;
+    if (!ctx) return RBF_ERR_INVALID;
+    return rbf_fail(ctx, RBF_ERR_UNSUPPORTED,
+                    "full-SVD Tikhonov (Algorithm 3) is not implemented on the GPU");
+}
+
+}  // extern "C"

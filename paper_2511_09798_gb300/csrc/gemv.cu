@@ -1,0 +1,318 @@
+// Assembled matrix-vector products of Algorithm 1: p = A z (row-major GEMV)
+// and r = A^T w (GEMV^T by row chunks with deterministic partial sums).
+//
+// A is streamed once per product with 16-byte vector loads (evict-first), the
+// input vector is read through L1.  FP64 operators use FP64 FMAs (on GB300 the
+// FP64 pipe, 2 FMA/clk/SM, and not HBM bounds this product).  FP32 (mixed)
+// operators multiply in FP32 and add short FP32 runs of products into FP64
+// accumulators.
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+constexpr int GN_THREADS = 256;  // 8 warps, one row per warp at a time
+constexpr int GT_THREADS = 256;
+constexpr int GT_MAX_CHUNK_ROWS = 4096;
+
+__device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
+__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
+
+// ---------------------------------------------------------------------------
+// y_i = sum_j A_ij x_j for the rows of this CTA's slab.
+// Epilogue (sc != nullptr): y_i = acc * sc[SC_INV_ALPHA] - sc[SC_ALPHA] * w_i and
+// z_out_i = x_i * sc[SC_INV_ALPHA]  (p = A z_j - alpha_j w_j with z_j = r / alpha_j).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(GN_THREADS) k_gemv_n_f64(
+    const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x,
+    double* __restrict__ y, const double* __restrict__ sc, const double* __restrict__ w,
+    double* __restrict__ z_out, const int* __restrict__ done) {
+    if (gkb_done(done)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * per;
+    const int64_t r1 = min(n, r0 + per);
+    const int64_t nvec = n >> 1;  // full double2 vectors per row
+    const double2* __restrict__ xv = reinterpret_cast<const double2*>(x);
+    for (int64_t i = r0 + warp; i < r1; i += GN_THREADS / 32) {
+        const double2* __restrict__ row = reinterpret_cast<const double2*>(A + i * lda);
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t v = lane;
+        for (; v + 96 < nvec; v += 128) {
+            double2 m0 = ld_stream(row + v), m1 = ld_stream(row + v + 32);
+            double2 m2 = ld_stream(row + v + 64), m3 = ld_stream(row + v + 96);
+            double2 x0 = __ldg(xv + v), x1 = __ldg(xv + v + 32);
+            double2 x2 = __ldg(xv + v + 64), x3 = __ldg(xv + v + 96);
+            a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
+            a1 = fma(m1.x, x1.x, a1); a1 = fma(m1.y, x1.y, a1);
+            a2 = fma(m2.x, x2.x, a2); a2 = fma(m2.y, x2.y, a2);
+            a3 = fma(m3.x, x3.x, a3); a3 = fma(m3.y, x3.y, a3);
+        }
+        for (; v < nvec; v += 32) {
+            double2 m0 = ld_stream(row + v), x0 = __ldg(xv + v);
+            a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
+        }
+        if ((n & 1) && lane == 0) a1 = fma(A[i * lda + n - 1], __ldg(x + n - 1), a1);
+        double acc = warp_sum((a0 + a1) + (a2 + a3));
+        if (lane == 0) {
+            if (sc) {
+                y[i] = acc * sc[SC_INV_ALPHA] - sc[SC_ALPHA] * w[i];
+                if (z_out) z_out[i] = x[i] * sc[SC_INV_ALPHA];
+            } else {
+                y[i] = acc;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(GN_THREADS) k_gemv_n_f32(
+    const float* __restrict__ A, int64_t lda, int64_t n, const float* __restrict__ x32,
+    const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ sc,
+    const double* __restrict__ w, double* __restrict__ z_out, const int* __restrict__ done) {
+    if (gkb_done(done)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * per;
+    const int64_t r1 = min(n, r0 + per);
+    const int64_t nvec = n >> 2;
+    const float4* __restrict__ xv = reinterpret_cast<const float4*>(x32);
+    for (int64_t i = r0 + warp; i < r1; i += GN_THREADS / 32) {
+        const float4* __restrict__ row = reinterpret_cast<const float4*>(A + i * lda);
+        double acc = 0.0;
+        int64_t v = lane;
+        for (; v + 96 < nvec; v += 128) {
+            float4 m0 = ld_stream(row + v), m1 = ld_stream(row + v + 32);
+            float4 m2 = ld_stream(row + v + 64), m3 = ld_stream(row + v + 96);
+            float4 x0 = __ldg(xv + v), x1 = __ldg(xv + v + 32);
+            float4 x2 = __ldg(xv + v + 64), x3 = __ldg(xv + v + 96);
+            float s0 = m0.x * x0.x, s1 = m1.x * x1.x, s2 = m2.x * x2.x, s3 = m3.x * x3.x;
+            s0 = fmaf(m0.y, x0.y, s0); s1 = fmaf(m1.y, x1.y, s1); s2 = fmaf(m2.y, x2.y, s2); s3 = fmaf(m3.y, x3.y, s3);
+            s0 = fmaf(m0.z, x0.z, s0); s1 = fmaf(m1.z, x1.z, s1); s2 = fmaf(m2.z, x2.z, s2); s3 = fmaf(m3.z, x3.z, s3);
+            s0 = fmaf(m0.w, x0.w, s0); s1 = fmaf(m1.w, x1.w, s1); s2 = fmaf(m2.w, x2.w, s2); s3 = fmaf(m3.w, x3.w, s3);
+            acc += (double)((s0 + s1) + (s2 + s3));
+        }
+        for (; v < nvec; v += 32) {
+            float4 m0 = ld_stream(row + v), x0 = __ldg(xv + v);
+            float s0 = m0.x * x0.x;
+            s0 = fmaf(m0.y, x0.y, s0); s0 = fmaf(m0.z, x0.z, s0); s0 = fmaf(m0.w, x0.w, s0);
+            acc += (double)s0;
+        }
+        for (int64_t c = nvec * 4 + lane; c < n; c += 32) acc += (double)(A[i * lda + c] * x32[c]);
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            if (sc) {
+                y[i] = acc * sc[SC_INV_ALPHA] - sc[SC_ALPHA] * w[i];
+                if (z_out) z_out[i] = x[i] * sc[SC_INV_ALPHA];
+            } else {
+                y[i] = acc;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// part[q][c] = sum_{i in row chunk q} A_ic x_i for the columns of this CTA's panel.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f64(
+    const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x,
+    int panel_cols, int chunks, double* __restrict__ part, const int* __restrict__ done) {
+    if (gkb_done(done)) return;
+    __shared__ double xs[GT_MAX_CHUNK_ROWS];
+    const int q = blockIdx.x % chunks;
+    const int pnl = blockIdx.x / chunks;
+    const int64_t per = (n + chunks - 1) / chunks;
+    const int64_t i0 = (int64_t)q * per;
+    const int64_t i1 = min(n, i0 + per);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += GT_THREADS) xs[i - i0] = x[i];
+    __syncthreads();
+    const int64_t c = (int64_t)pnl * panel_cols + 2 * threadIdx.x;
+    if (c >= n || i1 <= i0) {
+        if (c < n) {
+            part[(int64_t)q * n + c] = 0.0;
+            if (c + 1 < n) part[(int64_t)q * n + c + 1] = 0.0;
+        }
+        return;
+    }
+    const double* __restrict__ base = A + i0 * lda + c;
+    double ax0 = 0, ay0 = 0, ax1 = 0, ay1 = 0, ax2 = 0, ay2 = 0, ax3 = 0, ay3 = 0;
+    const int64_t rows = i1 - i0;
+    int64_t r = 0;
+    for (; r + 3 < rows; r += 4) {
+        double2 m0 = ld_stream(reinterpret_cast<const double2*>(base + (r + 0) * lda));
+        double2 m1 = ld_stream(reinterpret_cast<const double2*>(base + (r + 1) * lda));
+        double2 m2 = ld_stream(reinterpret_cast<const double2*>(base + (r + 2) * lda));
+        double2 m3 = ld_stream(reinterpret_cast<const double2*>(base + (r + 3) * lda));
+        ax0 = fma(m0.x, xs[r], ax0); ay0 = fma(m0.y, xs[r], ay0);
+        ax1 = fma(m1.x, xs[r + 1], ax1); ay1 = fma(m1.y, xs[r + 1], ay1);
+        ax2 = fma(m2.x, xs[r + 2], ax2); ay2 = fma(m2.y, xs[r + 2], ay2);
+        ax3 = fma(m3.x, xs[r + 3], ax3); ay3 = fma(m3.y, xs[r + 3], ay3);
+    }
+    for (; r < rows; ++r) {
+        double2 m0 = ld_stream(reinterpret_cast<const double2*>(base + r * lda));
+        ax0 = fma(m0.x, xs[r], ax0); ay0 = fma(m0.y, xs[r], ay0);
+    }
+    part[(int64_t)q * n + c] = (ax0 + ax1) + (ax2 + ax3);
+    if (c + 1 < n) part[(int64_t)q * n + c + 1] = (ay0 + ay1) + (ay2 + ay3);
+}
+
+__global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f32(
+    const float* __restrict__ A, int64_t lda, int64_t n, const float* __restrict__ x32,
+    int panel_cols, int chunks, double* __restrict__ part, const int* __restrict__ done) {
+    if (gkb_done(done)) return;
+    __shared__ float xs[GT_MAX_CHUNK_ROWS];
+    const int q = blockIdx.x % chunks;
+    const int pnl = blockIdx.x / chunks;
+    const int64_t per = (n + chunks - 1) / chunks;
+    const int64_t i0 = (int64_t)q * per;
+    const int64_t i1 = min(n, i0 + per);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += GT_THREADS) xs[i - i0] = x32[i];
+    __syncthreads();
+    const int64_t c = (int64_t)pnl * panel_cols + 4 * threadIdx.x;
+    if (c >= n) return;
+    const float* __restrict__ base = A + i0 * lda + c;
+    double d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+    const int64_t rows = i1 - i0;
+    int64_t r = 0;
+    for (; r + 7 < rows; r += 8) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            float4 m = ld_stream(reinterpret_cast<const float4*>(base + (r + u) * lda));
+            float xv = xs[r + u];
+            s0 = fmaf(m.x, xv, s0); s1 = fmaf(m.y, xv, s1); s2 = fmaf(m.z, xv, s2); s3 = fmaf(m.w, xv, s3);
+        }
+        d0 += (double)s0; d1 += (double)s1; d2 += (double)s2; d3 += (double)s3;
+    }
+    for (; r < rows; ++r) {
+        float4 m = ld_stream(reinterpret_cast<const float4*>(base + r * lda));
+        float xv = xs[r];
+        d0 += (double)(m.x * xv); d1 += (double)(m.y * xv); d2 += (double)(m.z * xv); d3 += (double)(m.w * xv);
+    }
+    double* out = part + (int64_t)q * n + c;
+    out[0] = d0;
+    if (c + 1 < n) out[1] = d1;
+    if (c + 2 < n) out[2] = d2;
+    if (c + 3 < n) out[3] = d3;
+}
+
+__global__ void k_reduce_partials(int64_t n, int chunks, const double* __restrict__ part,
+                                  double* __restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int q = 0; q < chunks; ++q) s += part[(int64_t)q * n + i];
+    y[i] = s;
+}
+
+__global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
+
+}  // namespace
+
+static void plan_t(const rbf_ctx* ctx, int64_t n, int vec, int* panel_cols, int* panels, int* chunks) {
+    *panel_cols = GT_THREADS * vec;
+    *panels = (int)((n + *panel_cols - 1) / *panel_cols);
+    const int slots = ctx->sm_count * 4;  // 4 CTAs of 256 threads per SM
+    int q = slots / *panels;
+    if (q < 1) q = 1;
+    // at least 8 rows per chunk, at most GT_MAX_CHUNK_ROWS
+    int64_t max_chunks = (n + 7) / 8;
+    if (q > max_chunks) q = (int)max_chunks;
+    int64_t min_chunks = (n + GT_MAX_CHUNK_ROWS - 1) / GT_MAX_CHUNK_ROWS;
+    if (q < min_chunks) q = (int)min_chunks;
+    *chunks = q;
+}
+
+size_t gemv_ws_bytes(const rbf_ctx* ctx, int64_t n) {
+    int pc, pn, ch;
+    plan_t(ctx, n, 2, &pc, &pn, &ch);
+    int pc4, pn4, ch4;
+    plan_t(ctx, n, 4, &pc4, &pn4, &ch4);
+    int c = ch > ch4 ? ch : ch4;
+    return ws_align((size_t)c * n * sizeof(double)) + ws_align((size_t)n * sizeof(float));
+}
+
+int gemv_t_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
+    int pc, pn, ch;
+    plan_t(ctx, op->n, op->precision == RBF_FP64 ? 2 : 4, &pc, &pn, &ch);
+    return ch;
+}
+
+static int gemv_n_grid(const rbf_ctx* ctx, int64_t n) {
+    int64_t g = (int64_t)ctx->sm_count * 4;
+    int64_t rows_min = (n + 7) / 8;
+    if (g > rows_min) g = rows_min;
+    return (int)(g < 1 ? 1 : g);
+}
+
+rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, const float* x32,
+                         double* y, const double* sc, const double* w, double* z_out,
+                         const int* done) {
+    const int grid = gemv_n_grid(ctx, op->n);
+    if (op->precision == RBF_FP64) {
+        k_gemv_n_f64<<<grid, GN_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x,
+                                                           y, sc, w, z_out, done);
+        RBF_LAUNCHED(ctx, "k_gemv_n_f64");
+    } else {
+        k_gemv_n_f32<<<grid, GN_THREADS, 0, ctx->stream>>>((const float*)op->d_A, op->lda, op->n, x32,
+                                                           x, y, sc, w, z_out, done);
+        RBF_LAUNCHED(ctx, "k_gemv_n_f32");
+    }
+    return RBF_OK;
+}
+
+rbf_status launch_gemv_t_partial(rbf_ctx* ctx, const rbf_operator* op, const double* x,
+                                 const float* x32, double* part, const int* done) {
+    int pc, pn, ch;
+    if (op->precision == RBF_FP64) {
+        plan_t(ctx, op->n, 2, &pc, &pn, &ch);
+        k_gemv_t_f64<<<pn * ch, GT_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n,
+                                                              x, pc, ch, part, done);
+        RBF_LAUNCHED(ctx, "k_gemv_t_f64");
+    } else {
+        plan_t(ctx, op->n, 4, &pc, &pn, &ch);
+        k_gemv_t_f32<<<pn * ch, GT_THREADS, 0, ctx->stream>>>((const float*)op->d_A, op->lda, op->n,
+                                                              x32, pc, ch, part, done);
+        RBF_LAUNCHED(ctx, "k_gemv_t_f32");
+    }
+    return RBF_OK;
+}
+
+rbf_status launch_reduce_partials(rbf_ctx* ctx, int64_t n, int chunks, const double* part, double* y) {
+    k_reduce_partials<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, chunks, part, y);
+    RBF_LAUNCHED(ctx, "k_reduce_partials");
+    return RBF_OK;
+}
+
+rbf_status launch_to_f32(rbf_ctx* ctx, int64_t n, const double* x, float* y) {
+    k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, x, y);
+    RBF_LAUNCHED(ctx, "k_to_f32");
+    return RBF_OK;
+}
+
+extern "C" rbf_status rbf_matvec(rbf_ctx* ctx, const rbf_operator* op, int trans, const double* d_x,
+                                 double* d_y) {
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!op || !d_x || !d_y) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_matvec: NULL argument");
+    const int64_t n = op->n;
+    if (op->storage == RBF_MATRIX_FREE) {
+        RBF_TRY(rbf_ws_reserve(ctx, mf_ws_bytes(ctx, n) + ws_align((size_t)n * sizeof(float))));
+        WsCarve wc(ctx->ws);
+        float* x32 = wc.take<float>((size_t)n);
+        double* part = wc.take<double>((size_t)mf_chunks(ctx, op) * n);
+        RBF_TRY(launch_to_f32(ctx, n, d_x, x32));
+        RBF_TRY(launch_mf_partial(ctx, op, trans, x32, part, nullptr));
+        return launch_reduce_partials(ctx, n, mf_chunks(ctx, op), part, d_y);
+    }
+    RBF_TRY(rbf_ws_reserve(ctx, gemv_ws_bytes(ctx, n)));
+    WsCarve wc(ctx->ws);
+    const int ch = gemv_t_chunks(ctx, op);
+    double* part = wc.take<double>((size_t)ch * n);
+    float* x32 = wc.take<float>((size_t)n);
+    if (op->precision == RBF_MIXED) RBF_TRY(launch_to_f32(ctx, n, d_x, x32));
+    if (trans == 0) return launch_gemv_n(ctx, op, d_x, x32, d_y, nullptr, nullptr, nullptr, nullptr);
+    RBF_TRY(launch_gemv_t_partial(ctx, op, d_x, x32, part, nullptr));
+    return launch_reduce_partials(ctx, n, ch, part, d_y);
+}

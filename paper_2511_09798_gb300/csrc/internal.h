@@ -1,0 +1,133 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+
+#include "rbfkr.h"
+
+// Device-side small state, one block per context (lives in the context's
+// fixed allocation, never in the growable workspace).
+struct rbf_dev_state {
+    int info[8];      // 0 steps_done, 1 breakdown, 2 done flag, 3 error code, 4 cur step
+    double scal[16];  // see SC_* below
+};
+enum {
+    SC_CHAT0 = 0,   // c_hat double buffer slot 0
+    SC_CHAT1 = 1,   // slot 1
+    SC_INV_BETA = 2,
+    SC_BETA = 3,
+    SC_INV_ALPHA = 4,
+    SC_ALPHA = 5,
+    SC_LAMBDA = 6,  // chosen lambda
+    SC_SIGMA1 = 7,
+    SC_FTIL_LAST = 8,
+};
+enum { IN_STEPS = 0, IN_BREAK = 1, IN_DONE = 2, IN_ERR = 3, IN_INDEX = 4, IN_RANK = 5 };
+
+struct rbf_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    rbf_options opt{};
+    int sm_count = 0;
+    char err[512] = {0};
+    void* ws = nullptr;          // growable workspace
+    size_t ws_bytes = 0;
+    rbf_dev_state* d_state = nullptr;
+    rbf_dev_state* h_state = nullptr;  // pinned mirror
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    rbf_timings tim{};
+    // counters
+    int64_t launches = 0;
+    static constexpr int PMAX = 8192;
+    cudaEvent_t* pev = nullptr;   // [2][PMAX][2] product start/stop events
+    int pcount[2] = {0, 0};       // recorded pairs per product kind
+    int64_t ptotal[2] = {0, 0};   // launches per product kind
+};
+
+// ---- error helpers ---------------------------------------------------------
+rbf_status rbf_fail(rbf_ctx* ctx, rbf_status st, const char* fmt, ...);
+
+#define RBF_CUDA(ctx, call)                                                             \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return rbf_fail((ctx), RBF_ERR_CUDA, "%s failed: %s (%s:%d)", #call,        \
+                            cudaGetErrorString(e_), __FILE__, __LINE__);                \
+    } while (0)
+
+#define RBF_LAUNCHED(ctx, name)                                                         \
+    do {                                                                                \
+        (ctx)->launches++;                                                              \
+        cudaError_t e_ = cudaGetLastError();                                            \
+        if (e_ != cudaSuccess)                                                          \
+            return rbf_fail((ctx), RBF_ERR_CUDA, "launch of %s failed: %s", name,       \
+                            cudaGetErrorString(e_));                                    \
+    } while (0)
+
+#define RBF_TRY(expr)                      \
+    do {                                   \
+        rbf_status s_ = (expr);            \
+        if (s_ != RBF_OK) return s_;       \
+    } while (0)
+
+// Grow the workspace to at least `bytes` (synchronises the stream when it
+// reallocates).  Returns RBF_ERR_OOM on failure or when above the cap.
+rbf_status rbf_ws_reserve(rbf_ctx* ctx, size_t bytes);
+
+// Simple bump allocator over the workspace (256-byte aligned slices).
+struct WsCarve {
+    char* base;
+    size_t off;
+    explicit WsCarve(void* b) : base((char*)b), off(0) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+inline size_t ws_align(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ---- timing ------------------------------------------------------------------
+// Product-launch timing (opt.timing >= 2): returns the slot or -1.
+int rbf_prod_begin(rbf_ctx* ctx, int trans);
+void rbf_prod_end(rbf_ctx* ctx, int trans, int slot);
+void rbf_timer_start(rbf_ctx* ctx);
+double rbf_timer_stop(rbf_ctx* ctx);  // ms, synchronises when timing is on
+
+// ---- launchers (one per translation unit family) ------------------------------
+// assemble.cu
+rbf_status launch_assemble(rbf_ctx* ctx, const rbf_operator* op);
+rbf_status launch_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* coef,
+                           const double* pts, int64_t m, double* u);
+// gemv.cu
+size_t gemv_ws_bytes(const rbf_ctx* ctx, int64_t n);
+int gemv_t_chunks(const rbf_ctx* ctx, const rbf_operator* op);
+rbf_status launch_to_f32(rbf_ctx* ctx, int64_t n, const double* x, float* y);
+// y = A x (trans 0) or partials of A^T x (trans 1), FP64 x, FP64 y.
+rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, const float* x32,
+                         double* y, const double* sc, const double* w, double* z_out,
+                         const int* done);
+rbf_status launch_gemv_t_partial(rbf_ctx* ctx, const rbf_operator* op, const double* x,
+                                 const float* x32, double* part, const int* done);
+rbf_status launch_reduce_partials(rbf_ctx* ctx, int64_t n, int chunks, const double* part, double* y);
+// mf.cu (matrix-free FP32 products; partial sums over `mf_chunks` centre chunks)
+int mf_chunks(const rbf_ctx* ctx, const rbf_operator* op);
+size_t mf_ws_bytes(const rbf_ctx* ctx, int64_t n);
+rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, const float* x32,
+                             double* part, const int* done);
+// gkb.cu
+rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_begin, int j_end,
+                   rbf_gkb_state* st);
+size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision);
+// svd.cu
+size_t svd_ws_bytes(int l);
+rbf_status launch_projected_svd(rbf_ctx* ctx, const double* alpha, const double* beta, int l,
+                                double* sigma, double* ftil, double* V, int64_t ldv, void* ws);
+// select.cu
+size_t select_ws_bytes(const rbf_ctx* ctx, int l);

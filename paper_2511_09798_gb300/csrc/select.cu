@@ -1,0 +1,315 @@
+// Parameter choice and projected solves (Algorithms 2 and 4), lift alpha = Z_l y.
+//
+// Grid: lambda_t = s~_1 10^{t}, t = t_lo + (t_hi - t_lo) * idx / (J - 1).
+// For each grid point (one thread each):
+//   q_i = lambda^2 / (s~_i^2 + lambda^2)         (= 1 - phi~_i)
+//   rho^2 = sum_i q_i^2 f~_i^2 + f~_{l+1}^2         (eq. rho_proj)
+//   eta^2 = sum_i (s~_i f~_i / (s~_i^2 + lambda^2))^2 (eq. eta_proj)
+//   GCV   = rho^2 / (1 + sum_i q_i)^2                (eq. gcv_proj: (l+1) - sum phi~_i)
+// GCV: grid argmin, smallest index on ties.  L-curve: signed curvature of
+// (ln rho, ln eta) by central differences in t at interior points, argmax over
+// the points whose speed is at least 1e-4 per decade (stationary stretches of
+// the curve carry only rounding noise).
+// HKT: y = V~ (s~_i f~_i / (s~_i^2 + lambda^2))_i (the SVD form of the normal
+// equations of Algorithm 4 step 9).  Ine-TSVD: GCV_l(k) = (sum_{i>k} f~_i^2 +
+// f~_{l+1}^2) / ((l+1) - k)^2 over k = 1..r_l, r_l = #{s~_i > (l+1) eps s~_1};
+// y = V~ (f~_i / s~_i for i <= k).
+#include <cfloat>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+// t_idx = t_lo + idx * step with step = (t_hi - t_lo) / (J - 1) rounded as two
+// separate operations (no contraction), and the last point exactly t_hi.
+__device__ __forceinline__ double grid_t(int idx, int J, double t_lo, double t_hi) {
+    if (idx == J - 1) return t_hi;
+    const double step = __ddiv_rn(t_hi - t_lo, (double)(J - 1));
+    return __dadd_rn(__dmul_rn((double)idx, step), t_lo);
+}
+
+__global__ void k_grid_terms(const double* __restrict__ sigma, const double* __restrict__ ftil, int l,
+                             int J, double t_lo, double t_hi, double* __restrict__ gcv,
+                             double* __restrict__ xr, double* __restrict__ ye) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= J) return;
+    const double lam = sigma[0] * exp10(grid_t(t, J, t_lo, t_hi));
+    const double lam2 = lam * lam;
+    double rho2 = 0.0, eta2 = 0.0, den = 1.0;
+    for (int i = 0; i < l; ++i) {
+        const double s = sigma[i], f = ftil[i];
+        const double inv = 1.0 / fma(s, s, lam2);
+        const double q = lam2 * inv;
+        const double g = s * f * inv;
+        rho2 = fma(q * q, f * f, rho2);
+        eta2 = fma(g, g, eta2);
+        den += q;
+    }
+    rho2 = fma(ftil[l], ftil[l], rho2);
+    gcv[t] = rho2 / (den * den);
+    xr[t] = 0.5 * log(rho2);
+    ye[t] = 0.5 * log(eta2);
+}
+
+// Choose lambda (rule 0 GCV, 1 L-curve, 2 fixed) and form the coefficient
+// vector cvec_i = s_i f_i / (s_i^2 + lambda^2).  One block.
+__global__ void k_choose_lambda(const double* __restrict__ sigma, const double* __restrict__ ftil, int l,
+                                int J, double t_lo, double t_hi, int rule, double lambda_in,
+                                const double* __restrict__ gcv, const double* __restrict__ xr,
+                                const double* __restrict__ ye, double* __restrict__ curve,
+                                double* __restrict__ cvec, rbf_dev_state* __restrict__ stt) {
+    __shared__ double bv[1024];
+    __shared__ int bi[1024];
+    __shared__ double lam_s;
+    const double h = (t_hi - t_lo) / (double)(J - 1);
+    // per-thread best over a strided subset, then a tree with lowest-index tie-break
+    double best = rule == 1 ? -INFINITY : INFINITY;
+    int besti = 0x7fffffff;
+    if (rule != 2) {
+        for (int t = threadIdx.x; t < J; t += blockDim.x) {
+            double v;
+            if (rule == 0) {
+                v = gcv[t];
+                if (curve) curve[t] = v;
+                if (isnan(v)) v = INFINITY;
+                if (v < best || (v == best && t < besti)) { best = v; besti = t; }
+            } else {
+                v = -INFINITY;
+                if (t > 0 && t < J - 1) {
+                    const double x1 = (xr[t + 1] - xr[t - 1]) / (2.0 * h);
+                    const double y1 = (ye[t + 1] - ye[t - 1]) / (2.0 * h);
+                    const double x2 = (xr[t + 1] - 2.0 * xr[t] + xr[t - 1]) / (h * h);
+                    const double y2 = (ye[t + 1] - 2.0 * ye[t] + ye[t - 1]) / (h * h);
+                    const double sp = x1 * x1 + y1 * y1;
+                    v = (x1 * y2 - x2 * y1) / (sp * sqrt(sp));
+                    // stationary points (speed < 1e-4 per decade) are not candidates
+                    if (!isfinite(v) || !(sp >= 1e-8)) v = -INFINITY;
+                }
+                if (curve) curve[t] = v;
+                if (v > best || (v == best && t < besti)) { best = v; besti = t; }
+            }
+        }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = besti;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) {
+            const double ov = bv[threadIdx.x + off];
+            const int oi = bi[threadIdx.x + off];
+            const double mv = bv[threadIdx.x];
+            const int mi = bi[threadIdx.x];
+            const bool take = rule == 1 ? (ov > mv || (ov == mv && oi < mi)) : (ov < mv || (ov == mv && oi < mi));
+            if (take) {
+                bv[threadIdx.x] = ov;
+                bi[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double lam;
+        int idx;
+        if (rule == 2) {
+            lam = lambda_in;
+            idx = -1;
+        } else {
+            idx = bi[0];
+            if (idx < 0 || idx >= J) idx = 0;
+            lam = sigma[0] * exp10(grid_t(idx, J, t_lo, t_hi));
+        }
+        lam_s = lam;
+        stt->scal[SC_LAMBDA] = lam;
+        stt->scal[SC_SIGMA1] = sigma[0];
+        stt->info[IN_INDEX] = idx;
+    }
+    __syncthreads();
+    const double lam2 = lam_s * lam_s;
+    for (int i = threadIdx.x; i < l; i += blockDim.x) {
+        const double s = sigma[i];
+        cvec[i] = s * ftil[i] / fma(s, s, lam2);
+    }
+}
+
+// Ine-TSVD rank by GCV_l(k) (or the given rank) and cvec_i = f_i / s_i, i <= k.
+__global__ void k_choose_rank(const double* __restrict__ sigma, const double* __restrict__ ftil, int l,
+                              int rank_in, double* __restrict__ curve, double* __restrict__ cvec,
+                              double* __restrict__ work, rbf_dev_state* __restrict__ stt) {
+    __shared__ int k_s;
+    if (threadIdx.x == 0) {
+        const double s1 = sigma[0];
+        int r = 0;
+        for (int i = 0; i < l; ++i) r += sigma[i] > (double)(l + 1) * DBL_EPSILON * s1 ? 1 : 0;
+        int k = rank_in;
+        if (k <= 0) {
+            // suffix sums S_k = sum_{i=k+1}^{l} f_i^2 + f_{l+1}^2 (1-based i), k = l..1
+            double acc = ftil[l] * ftil[l];
+            for (int kk = l; kk >= 1; --kk) {
+                work[kk] = acc;       // S_kk
+                acc = fma(ftil[kk - 1], ftil[kk - 1], acc);
+            }
+            double best = INFINITY;
+            k = 1;
+            for (int kk = 1; kk <= r; ++kk) {
+                const double d = (double)(l + 1 - kk);
+                const double g = work[kk] / (d * d);
+                if (curve) curve[kk - 1] = g;
+                if (g < best) {
+                    best = g;
+                    k = kk;
+                }
+            }
+            if (r == 0) k = 1;
+        }
+        if (k > l) k = l;
+        k_s = k;
+        stt->info[IN_RANK] = k;
+        stt->scal[SC_SIGMA1] = s1;
+    }
+    __syncthreads();
+    const int k = k_s;
+    for (int i = threadIdx.x; i < l; i += blockDim.x) cvec[i] = i < k ? ftil[i] / sigma[i] : 0.0;
+}
+
+// y = V cvec (V column-major l x l, ld ldv)
+__global__ void k_vmul(const double* __restrict__ V, int64_t ldv, int l, const double* __restrict__ cvec,
+                       double* __restrict__ y) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= l) return;
+    double acc = 0.0;
+    for (int i = 0; i < l; ++i) acc = fma(V[(int64_t)i * ldv + r], cvec[i], acc);
+    y[r] = acc;
+}
+
+// coef = Z y (Z column-major n x l): 32 rows x 4 column groups per CTA
+__global__ void __launch_bounds__(128) k_lift(const double* __restrict__ Z, int64_t ldz, int64_t n, int l,
+                                              const double* __restrict__ y, double* __restrict__ coef) {
+    __shared__ double red[4][32];
+    __shared__ double ys[1024];
+    for (int m = threadIdx.x; m < l; m += 128) ys[m] = y[m];
+    __syncthreads();
+    const int row = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + row;
+    double acc = 0.0;
+    if (i < n)
+        for (int m = grp; m < l; m += 4) acc = fma(Z[(int64_t)m * ldz + i], ys[m], acc);
+    red[grp][row] = acc;
+    __syncthreads();
+    if (grp == 0 && i < n) coef[i] = (red[0][row] + red[1][row]) + (red[2][row] + red[3][row]);
+}
+
+}  // namespace
+
+size_t select_ws_bytes(const rbf_ctx* ctx, int l) {
+    const int J = ctx->opt.grid_j;
+    size_t b = 0;
+    b += ws_align((size_t)l * 8) + ws_align((size_t)(l + 1) * 8) + ws_align((size_t)l * l * 8);  // sigma, ftil, V
+    b += 3 * ws_align((size_t)J * 8);                                                           // gcv, x, y
+    b += 3 * ws_align((size_t)(l + 2) * 8);                                                     // cvec, y, work
+    return b + 4096;
+}
+
+namespace {
+
+struct ProjWs {
+    double *sigma, *ftil, *V, *gcv, *xr, *ye, *cvec, *y, *work;
+    void* svd;
+};
+
+rbf_status proj_prepare(rbf_ctx* ctx, const rbf_gkb_state* st, ProjWs* w) {
+    const int l = st->steps_done;
+    if (l < 1) return rbf_fail(ctx, RBF_ERR_INVALID, "state has no completed step");
+    if (l > 1023) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "projected dimension above 1023");
+    const int J = ctx->opt.grid_j;
+    RBF_TRY(rbf_ws_reserve(ctx, select_ws_bytes(ctx, l) + svd_ws_bytes(l)));
+    WsCarve wc(ctx->ws);
+    w->sigma = wc.take<double>(l);
+    w->ftil = wc.take<double>(l + 1);
+    w->V = wc.take<double>((size_t)l * l);
+    w->gcv = wc.take<double>(J);
+    w->xr = wc.take<double>(J);
+    w->ye = wc.take<double>(J);
+    w->cvec = wc.take<double>(l + 2);
+    w->y = wc.take<double>(l + 2);
+    w->work = wc.take<double>(l + 2);
+    w->svd = (void*)wc.take<char>(svd_ws_bytes(l));
+    return RBF_OK;
+}
+
+rbf_status read_info(rbf_ctx* ctx, rbf_solve_info* info, int l) {
+    RBF_CUDA(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(rbf_dev_state),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    RBF_CUDA(ctx, cudaGetLastError());
+    if (info) {
+        info->lambda = ctx->h_state->scal[SC_LAMBDA];
+        info->index = ctx->h_state->info[IN_INDEX];
+        info->rank = ctx->h_state->info[IN_RANK];
+        info->steps = l;
+        info->sigma1 = ctx->h_state->scal[SC_SIGMA1];
+    }
+    return RBF_OK;
+}
+
+}  // namespace
+
+extern "C" rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in,
+                              double* d_coef, double* d_curve, rbf_solve_info* info) {
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!st || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_hkt: NULL argument");
+    if (rule != RBF_GCV && rule != RBF_LCURVE && rule != RBF_FIXED)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "unknown rule %d", rule);
+    if (rule == RBF_FIXED && !(lambda_in >= 0.0))
+        return rbf_fail(ctx, RBF_ERR_INVALID, "fixed lambda must be >= 0");
+    const int l = st->steps_done;
+    ProjWs w;
+    RBF_TRY(proj_prepare(ctx, st, &w));
+    cudaStream_t s = ctx->stream;
+    const int J = ctx->opt.grid_j;
+    const double tlo = ctx->opt.grid_t_lo, thi = ctx->opt.grid_t_hi;
+    rbf_timer_start(ctx);
+    RBF_TRY(launch_projected_svd(ctx, st->d_alpha, st->d_beta, l, w.sigma, w.ftil, w.V, l, w.svd));
+    ctx->tim.svd_ms = rbf_timer_stop(ctx);
+    rbf_timer_start(ctx);
+    if (rule != RBF_FIXED) {
+        k_grid_terms<<<(J + 31) / 32, 32, 0, s>>>(w.sigma, w.ftil, l, J, tlo, thi, w.gcv, w.xr, w.ye);
+        RBF_LAUNCHED(ctx, "k_grid_terms");
+    }
+    k_choose_lambda<<<1, 1024, 0, s>>>(w.sigma, w.ftil, l, J, tlo, thi, rule, lambda_in, w.gcv, w.xr,
+                                       w.ye, d_curve, w.cvec, ctx->d_state);
+    RBF_LAUNCHED(ctx, "k_choose_lambda");
+    k_vmul<<<(l + 127) / 128, 128, 0, s>>>(w.V, l, l, w.cvec, w.y);
+    RBF_LAUNCHED(ctx, "k_vmul");
+    ctx->tim.select_ms = rbf_timer_stop(ctx);
+    rbf_timer_start(ctx);
+    k_lift<<<(unsigned)((st->n + 31) / 32), 128, 0, s>>>(st->d_Z, st->ldz, st->n, l, w.y, d_coef);
+    RBF_LAUNCHED(ctx, "k_lift");
+    ctx->tim.lift_ms = rbf_timer_stop(ctx);
+    return read_info(ctx, info, l);
+}
+
+extern "C" rbf_status rbf_ine_tsvd(rbf_ctx* ctx, const rbf_gkb_state* st, int rank, double* d_coef,
+                                   double* d_curve, rbf_solve_info* info) {
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!st || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_ine_tsvd: NULL argument");
+    const int l = st->steps_done;
+    if (rank < 0 || rank > l) return rbf_fail(ctx, RBF_ERR_INVALID, "rank %d outside [0, l=%d]", rank, l);
+    ProjWs w;
+    RBF_TRY(proj_prepare(ctx, st, &w));
+    cudaStream_t s = ctx->stream;
+    rbf_timer_start(ctx);
+    RBF_TRY(launch_projected_svd(ctx, st->d_alpha, st->d_beta, l, w.sigma, w.ftil, w.V, l, w.svd));
+    ctx->tim.svd_ms = rbf_timer_stop(ctx);
+    rbf_timer_start(ctx);
+    k_choose_rank<<<1, 256, 0, s>>>(w.sigma, w.ftil, l, rank, d_curve, w.cvec, w.work, ctx->d_state);
+    RBF_LAUNCHED(ctx, "k_choose_rank");
+    k_vmul<<<(l + 127) / 128, 128, 0, s>>>(w.V, l, l, w.cvec, w.y);
+    RBF_LAUNCHED(ctx, "k_vmul");
+    ctx->tim.select_ms = rbf_timer_stop(ctx);
+    rbf_timer_start(ctx);
+    k_lift<<<(unsigned)((st->n + 31) / 32), 128, 0, s>>>(st->d_Z, st->ldz, st->n, l, w.y, d_coef);
+    RBF_LAUNCHED(ctx, "k_lift");
+    ctx->tim.lift_ms = rbf_timer_stop(ctx);
+    return read_info(ctx, info, l);
+}

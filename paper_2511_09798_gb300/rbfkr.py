@@ -1,0 +1,248 @@
+"""Thin ctypes binding of ``include/rbfkr.h`` (argument marshalling only).
+
+Device buffers are passed as torch CUDA tensors (their ``data_ptr()``); every
+step of the computation runs in ``librbfkr.so``.  Each function raises
+``RbfError`` with the library's message when the C call fails.  There is no
+fallback: if the shared library is missing or cannot be loaded, importing
+functions from here raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librbfkr.so")
+
+RBF_OK, RBF_ERR_INVALID, RBF_ERR_OOM, RBF_ERR_CUDA, RBF_ERR_TIMEOUT, RBF_ERR_UNSUPPORTED, RBF_ERR_INTERNAL = range(7)
+RBF_FP64, RBF_MIXED = 0, 1
+RBF_ASSEMBLED, RBF_MATRIX_FREE = 0, 1
+RBF_GCV, RBF_LCURVE, RBF_FIXED = 0, 1, 2
+RBF_FORM_C, RBF_FORM_EPS = 0, 1
+
+STATUS_NAMES = {0: "RBF_OK", 1: "RBF_ERR_INVALID", 2: "RBF_ERR_OOM", 3: "RBF_ERR_CUDA",
+                4: "RBF_ERR_TIMEOUT", 5: "RBF_ERR_UNSUPPORTED", 6: "RBF_ERR_INTERNAL"}
+
+
+class RbfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("grid_j", C.c_int), ("grid_t_lo", C.c_double), ("grid_t_hi", C.c_double),
+                ("breakdown_factor", C.c_double), ("cluster_tol", C.c_double),
+                ("workspace_cap", C.c_int64), ("timing", C.c_int)]
+
+
+class Operator(C.Structure):
+    _fields_ = [("d_nodes", C.c_void_p), ("n", C.c_int64), ("n_interior", C.c_int64),
+                ("c", C.c_double), ("k", C.c_double), ("storage", C.c_int),
+                ("precision", C.c_int), ("form", C.c_int), ("d_A", C.c_void_p), ("lda", C.c_int64)]
+
+
+class GkbState(C.Structure):
+    _fields_ = [("d_W", C.c_void_p), ("ldw", C.c_int64), ("d_Z", C.c_void_p), ("ldz", C.c_int64),
+                ("d_alpha", C.c_void_p), ("d_beta", C.c_void_p), ("capacity", C.c_int),
+                ("n", C.c_int64), ("steps_done", C.c_int), ("breakdown", C.c_int),
+                ("c_hat", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("index", C.c_int), ("rank", C.c_int), ("steps", C.c_int),
+                ("sigma1", C.c_double)]
+
+
+class Counters(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("product_launches", C.c_int64 * 2),
+                ("product_ms", C.c_double * 2)]
+
+
+class Timings(C.Structure):
+    _fields_ = [("assemble_ms", C.c_double), ("gkb_ms", C.c_double), ("svd_ms", C.c_double),
+                ("select_ms", C.c_double), ("lift_ms", C.c_double), ("evaluate_ms", C.c_double),
+                ("gkb_steps", C.c_int)]
+
+
+EXPORTS = {
+    "rbf_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.POINTER(Options)]),
+    "rbf_destroy": (C.c_int, [C.c_void_p]),
+    "rbf_last_error": (C.c_char_p, [C.c_void_p]),
+    "rbf_workspace_bytes": (C.c_size_t, [C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int]),
+    "rbf_get_timings": (C.c_int, [C.c_void_p, C.POINTER(Timings)]),
+    "rbf_get_counters": (C.c_int, [C.c_void_p, C.POINTER(Counters), C.c_int]),
+    "rbf_operator_init": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_int64, C.c_int64,
+                                    C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                    C.c_int64]),
+    "rbf_assemble": (C.c_int, [C.c_void_p, C.POINTER(Operator)]),
+    "rbf_matvec": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_int, C.c_void_p, C.c_void_p]),
+    "rbf_gkb": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_int, C.POINTER(GkbState)]),
+    "rbf_gkb_resume": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.POINTER(GkbState), C.c_int]),
+    "rbf_projected_svd": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int64]),
+    "rbf_hkt": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_int, C.c_double, C.c_void_p,
+                          C.c_void_p, C.POINTER(SolveInfo)]),
+    "rbf_ine_tsvd": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_int, C.c_void_p, C.c_void_p,
+                               C.POINTER(SolveInfo)]),
+    "rbf_tikhonov": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_int, C.c_double,
+                               C.c_void_p, C.POINTER(SolveInfo)]),
+    "rbf_evaluate": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_void_p, C.c_int64,
+                               C.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load librbfkr.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    p = path or LIB_PATH
+    if path is None:
+        _build.build()
+    if not os.path.exists(p):
+        raise RuntimeError(f"librbfkr.so not found at {p}; the CUDA library is required")
+    lib = C.CDLL(p)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_cuda:
+            raise ValueError("device buffers must be CUDA tensors")
+        if not t.is_contiguous():
+            raise ValueError("device buffers must be contiguous")
+        return t.data_ptr()
+    return int(t)
+
+
+class Context:
+    """Owns one rbf_ctx.  Methods mirror the C entry points."""
+
+    def __init__(self, device: int = 0, stream=None, timing: bool = False, **opts):
+        self.lib = load()
+        o = Options()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        o.timing = int(timing)
+        h = C.c_void_p()
+        s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        st = self.lib.rbf_create(C.byref(h), device, s, C.byref(o))
+        if st != RBF_OK:
+            raise RbfError(st, "rbf_create failed")
+        self.h = h
+
+    def _check(self, st):
+        if st != RBF_OK:
+            raise RbfError(st, self.lib.rbf_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rbf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- C entry points -------------------------------------------------
+    def rbf_workspace_bytes(self, n, steps, storage, precision):
+        return self.lib.rbf_workspace_bytes(self.h, n, steps, storage, precision)
+
+    def rbf_get_timings(self):
+        t = Timings()
+        self._check(self.lib.rbf_get_timings(self.h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Timings._fields_}
+
+    def rbf_get_counters(self, reset=False):
+        c = Counters()
+        self._check(self.lib.rbf_get_counters(self.h, C.byref(c), 1 if reset else 0))
+        return {"launches": c.launches, "product_launches": list(c.product_launches),
+                "product_ms": list(c.product_ms)}
+
+    def rbf_operator_init(self, nodes, n, n_interior, c, k, storage=RBF_ASSEMBLED, precision=RBF_FP64,
+                          form=RBF_FORM_C, A=None, lda=0):
+        op = Operator()
+        self._check(self.lib.rbf_operator_init(self.h, C.byref(op), _ptr(nodes), n, n_interior, c, k,
+                                               storage, precision, form, _ptr(A), lda))
+        op._keep = (nodes, A)
+        return op
+
+    def rbf_assemble(self, op):
+        self._check(self.lib.rbf_assemble(self.h, C.byref(op)))
+
+    def rbf_matvec(self, op, trans, x, y):
+        self._check(self.lib.rbf_matvec(self.h, C.byref(op), trans, _ptr(x), _ptr(y)))
+
+    def rbf_gkb(self, op, f, steps, state):
+        self._check(self.lib.rbf_gkb(self.h, C.byref(op), _ptr(f), steps, C.byref(state)))
+        return state.steps_done
+
+    def rbf_gkb_resume(self, op, state, more):
+        self._check(self.lib.rbf_gkb_resume(self.h, C.byref(op), C.byref(state), more))
+        return state.steps_done
+
+    def rbf_projected_svd(self, state, sigma, ftil, V, ldv):
+        self._check(self.lib.rbf_projected_svd(self.h, C.byref(state), _ptr(sigma), _ptr(ftil),
+                                               _ptr(V), ldv))
+
+    def rbf_hkt(self, state, rule, lambda_in, coef, curve=None):
+        info = SolveInfo()
+        self._check(self.lib.rbf_hkt(self.h, C.byref(state), rule, float(lambda_in), _ptr(coef),
+                                     _ptr(curve), C.byref(info)))
+        return info
+
+    def rbf_ine_tsvd(self, state, rank, coef, curve=None):
+        info = SolveInfo()
+        self._check(self.lib.rbf_ine_tsvd(self.h, C.byref(state), rank, _ptr(coef), _ptr(curve),
+                                          C.byref(info)))
+        return info
+
+    def rbf_tikhonov(self, op, f, rule, lambda_in, coef):
+        info = SolveInfo()
+        self._check(self.lib.rbf_tikhonov(self.h, C.byref(op), _ptr(f), rule, float(lambda_in),
+                                          _ptr(coef), C.byref(info)))
+        return info
+
+    def rbf_evaluate(self, op, coef, points, m, u):
+        self._check(self.lib.rbf_evaluate(self.h, C.byref(op), _ptr(coef), _ptr(points), m, _ptr(u)))
+
+
+def make_state(torch, n, capacity, device="cuda"):
+    """Allocate caller-owned GKB buffers as torch tensors and wrap them."""
+    ld = n
+    W = torch.zeros((capacity + 1, ld), dtype=torch.float64, device=device)  # column j = W[j]
+    Z = torch.zeros((capacity, ld), dtype=torch.float64, device=device)
+    alpha = torch.zeros(capacity, dtype=torch.float64, device=device)
+    beta = torch.zeros(capacity + 1, dtype=torch.float64, device=device)
+    st = GkbState()
+    st.d_W, st.ldw = W.data_ptr(), ld
+    st.d_Z, st.ldz = Z.data_ptr(), ld
+    st.d_alpha, st.d_beta = alpha.data_ptr(), beta.data_ptr()
+    st.capacity, st.n = capacity, n
+    st.steps_done, st.breakdown, st.c_hat = 0, 0, 0.0
+    st._keep = (W, Z, alpha, beta)
+    return st, W, Z, alpha, beta
+
+
+def padded_lda(n, precision):
+    """Leading dimension used for assembled matrices: a multiple of 32 elements."""
+    return ((n + 31) // 32) * 32

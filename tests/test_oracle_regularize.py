@@ -161,3 +161,21 @@ def test_lcurve_corner_near_optimal_lambda():
     assert abs(h["index"] - best) <= 40  # within two decades on the 0.05-decade grid
     # far better than either end of the grid (no / full regularization)
     assert errs[h["index"]] < 0.25 * min(errs[0], errs[-1])
+
+
+def test_lcurve_ignores_stationary_stretch():
+    # l < N with noisy data: for lambda far below every s~_i, rho -> f~_{l+1} and
+    # eta -> |y_0| are constant to rounding; those samples are not candidates
+    rng = np.random.default_rng(12)
+    n = 60
+    U, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    V, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    A = U @ np.diag(10.0 ** (-np.arange(n) / 8.0)) @ V.T
+    f = A @ rng.normal(size=n) + 1e-3 * rng.normal(size=n)
+    g = G.gkb(A, None, f, 20)
+    h = R.hkt(g, "lcurve")
+    t = R.grid_t()
+    s_min = h["ps"].sigma[-1] / h["ps"].sigma[0]
+    below = t[1:-1] < np.log10(s_min) - 3.0
+    assert np.all(np.isneginf(h["curve"][below]))
+    assert t[h["index"]] > np.log10(s_min) - 3.0
