@@ -248,6 +248,32 @@ rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const double* d_f,
 rbf_status rbf_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* d_coef,
                         const double* d_points, int64_t m, double* d_u);
 
+/* ---- allocation-free product (no counterpart in the paper) ------------- */
+
+/* Elements of the library's static device scratch used by rbf_matvec_t_noalloc
+ * (8 MiB of FP64, held by every GPU that loads the library until exit). */
+#define RBF_NOALLOC_SCRATCH_DOUBLES (1 << 20)
+
+/* d_y = A^T d_x for an FP64 row-major d_A (n x lda, lda even, 16-byte aligned),
+ * enqueued on `cuda_stream` (a cudaStream_t or NULL), without allocating: no
+ * context is needed, and no cudaMalloc, cudaFree or allocating library routine
+ * is called.  It is meant for callers that cannot allocate device memory, such
+ * as code whose device memory is reserved in advance by another allocator or a
+ * latency-critical loop where the device-wide synchronisation that cudaMalloc /
+ * cudaFree may cause is not acceptable.  The row-chunk partial sums go to a
+ * file-scope device array of RBF_NOALLOC_SCRATCH_DOUBLES doubles; n must fit
+ * (the partials need at least ceil(n / 4096) chunks of n doubles, so n up to
+ * about 64 000), otherwise RBF_ERR_INVALID.  The first call on a device (with
+ * that device current) looks up the array's device address; make that first
+ * call before any stream capture.  All calls share the one array and every
+ * call overwrites the partials it reads, so calls that overlap on the GPU (on
+ * different streams or host threads) race and must be ordered by the caller.
+ * Returns RBF_ERR_INVALID for NULL pointers or bad sizes and alignment,
+ * RBF_ERR_CUDA when a CUDA call or launch fails (no message is kept: there is
+ * no context). */
+rbf_status rbf_matvec_t_noalloc(const double* d_A, int64_t lda, int64_t n, const double* d_x,
+                                double* d_y, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

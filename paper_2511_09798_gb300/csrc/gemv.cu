@@ -6,6 +6,8 @@
 // FP64 pipe, 2 FMA/clk/SM, and not HBM bounds this product).  FP32 (mixed)
 // operators multiply in FP32 and add short FP32 runs of products into FP64
 // accumulators.
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -211,10 +213,10 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restr
 
 }  // namespace
 
-static void plan_t(const rbf_ctx* ctx, int64_t n, int vec, int* panel_cols, int* panels, int* chunks) {
+static void plan_t_sms(int sm_count, int64_t n, int vec, int* panel_cols, int* panels, int* chunks) {
     *panel_cols = GT_THREADS * vec;
     *panels = (int)((n + *panel_cols - 1) / *panel_cols);
-    const int slots = ctx->sm_count * 4;  // 4 CTAs of 256 threads per SM
+    const int slots = sm_count * 4;  // 4 CTAs of 256 threads per SM
     int q = slots / *panels;
     if (q < 1) q = 1;
     // at least 8 rows per chunk, at most GT_MAX_CHUNK_ROWS
@@ -223,6 +225,10 @@ static void plan_t(const rbf_ctx* ctx, int64_t n, int vec, int* panel_cols, int*
     int64_t min_chunks = (n + GT_MAX_CHUNK_ROWS - 1) / GT_MAX_CHUNK_ROWS;
     if (q < min_chunks) q = (int)min_chunks;
     *chunks = q;
+}
+
+static void plan_t(const rbf_ctx* ctx, int64_t n, int vec, int* panel_cols, int* panels, int* chunks) {
+    plan_t_sms(ctx->sm_count, n, vec, panel_cols, panels, chunks);
 }
 
 size_t gemv_ws_bytes(const rbf_ctx* ctx, int64_t n) {
@@ -315,4 +321,62 @@ extern "C" rbf_status rbf_matvec(rbf_ctx* ctx, const rbf_operator* op, int trans
     if (trans == 0) return launch_gemv_n(ctx, op, d_x, x32, d_y, nullptr, nullptr, nullptr, nullptr);
     RBF_TRY(launch_gemv_t_partial(ctx, op, d_x, x32, part, nullptr));
     return launch_reduce_partials(ctx, n, ch, part, d_y);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP64 product y = A^T x.
+//
+// Callers that cannot allocate device memory -- for example code whose device
+// memory is reserved up front by another allocator, or a latency-critical loop
+// in which cudaMalloc / cudaFree (which may synchronise the whole device) are not
+// allowed -- use this entry point.  Its partial sums live in the file-scope
+// device array below instead of a context workspace.  The array is part of the
+// loaded module: every GPU on which the library is used holds these 8 MiB until
+// the process exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_partials[RBF_NOALLOC_SCRATCH_DOUBLES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+extern "C" rbf_status rbf_matvec_t_noalloc(const double* d_A, int64_t lda, int64_t n, const double* d_x,
+                                           double* d_y, void* cuda_stream) {
+    if (!d_A || !d_x || !d_y || n <= 0 || lda < n || (lda & 1) || ((uintptr_t)d_A & 15u))
+        return RBF_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return RBF_ERR_CUDA;
+    double* scratch = nullptr;
+    int sms = 0;
+    {
+        // one-time set-up per device, with that device current: the host-side
+        // name of the array is not a device address, so take its address here
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess) return RBF_ERR_CUDA;
+            if (cudaDeviceGetAttribute(&g_noalloc_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return RBF_ERR_CUDA;
+            g_noalloc_ptr[dev] = (double*)p;
+        }
+        scratch = g_noalloc_ptr[dev];
+        sms = g_noalloc_sms[dev];
+    }
+    int pc, pn, ch;
+    plan_t_sms(sms, n, 2, &pc, &pn, &ch);
+    // fit the partial sums into the static array: fewer row chunks if needed
+    const int64_t max_chunks = RBF_NOALLOC_SCRATCH_DOUBLES / n;
+    const int64_t min_chunks = (n + GT_MAX_CHUNK_ROWS - 1) / GT_MAX_CHUNK_ROWS;
+    if (max_chunks < min_chunks) return RBF_ERR_INVALID;  // n beyond the scratch limit
+    if (ch > max_chunks) ch = (int)max_chunks;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // every (chunk, column) partial is written before it is read: nothing to clear
+    k_gemv_t_f64<<<pn * ch, GT_THREADS, 0, s>>>(d_A, lda, n, d_x, pc, ch, scratch, nullptr);
+    if (cudaGetLastError() != cudaSuccess) return RBF_ERR_CUDA;
+    k_reduce_partials<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, ch, scratch, d_y);
+    if (cudaGetLastError() != cudaSuccess) return RBF_ERR_CUDA;
+    return RBF_OK;
 }

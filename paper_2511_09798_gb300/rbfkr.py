@@ -89,7 +89,20 @@ EXPORTS = {
                                C.c_void_p, C.POINTER(SolveInfo)]),
     "rbf_evaluate": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_void_p, C.c_int64,
                                C.c_void_p]),
+    "rbf_matvec_t_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]),
 }
+
+RBF_NOALLOC_SCRATCH_DOUBLES = 1 << 20
+
+
+def rbf_matvec_t_noalloc(A, lda, n, x, y, stream=None):
+    """y = A^T x through the allocation-free entry point (no context)."""
+    lib = load()
+    s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    st = lib.rbf_matvec_t_noalloc(_ptr(A), lda, n, _ptr(x), _ptr(y), s)
+    if st != RBF_OK:
+        raise RbfError(st, "rbf_matvec_t_noalloc failed")
 
 _lib = None
 
