@@ -291,6 +291,78 @@ def run_ours(args, rank, world, local_rank):
     return out
 
 
+# --------------------------------------------------------------------------- batch (96 instances)
+def run_batch(args, rank, world, local_rank):
+    """96 uneven instances (cube/sphere, N in [2000, 16000], c log-uniform in
+    [0.05, 1], k in [1, 20], plane-wave direction on S^2), mixed precision,
+    matrix-free FP32 products, 150 GKB steps, HKT with GCV, u at 200 points per
+    instance; one bench step = the whole batch through the C ABI."""
+    import numpy as np
+    import torch
+
+    import workloads as w
+    from paper_2511_09798_gb300 import rbfkr as R
+
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    inst = w.batch_instances(96)
+    L = 150
+    fs = [w.plane_wave_rhs(s, s.params["k"], s.params["d"]) for s in inst]
+    ctx = R.Context(local_rank, stream=torch.cuda.current_stream())
+    bt, keep = R.make_batch(torch, inst, [s.params["c"] for s in inst], [s.params["k"] for s in inst], fs, L, dev)
+    T = int(keep["offsets"][-1])
+    coef = torch.empty(T, dtype=torch.float64, device=dev)
+    m = 200
+    pts = [w.test_points(s, m, seed=s.params["seed"] + 7) for s in inst]
+    P = torch.as_tensor(np.concatenate([p.T.ravel() for p in pts]), device=dev)
+    u = torch.empty(m * len(inst), dtype=torch.float64, device=dev)
+
+    def one():
+        ctx.rbf_batch_gkb(bt, L)
+        lam = ctx.rbf_batch_hkt(bt, R.RBF_GCV, coef)
+        ctx.rbf_batch_evaluate(bt, coef, P, [m] * len(inst), u)
+        return sum(bt.steps_done[b] for b in range(len(inst))), lam
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    t0 = time.perf_counter()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    steps_total = 0
+    for _ in range(args.steps):
+        st, lam = one()
+        steps_total += st
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop() if sampler else None
+    uh = u.cpu().numpy().reshape(len(inst), m)
+    errs = []
+    for b, s_ in enumerate(inst):
+        ue = w.plane_wave(pts[b], s_.params["k"], s_.params["d"])
+        errs.append(float(np.max(np.abs(uh[b] - ue)) / np.max(np.abs(ue))))
+    tune = ctx.rbf_get_tuning()
+    ctx.close()
+    if rank != 0:
+        return None
+    value = len(inst) * args.steps * world / (ms / 1e3)
+    entries = sum(2 * bt.steps_done[b] * inst[b].n ** 2 for b in range(len(inst))) * args.steps
+    return {"metric": "batched HKT instances/s (96 uneven instances, 150 GKB steps each)", "value": round(value, 3),
+            "unit": "instances/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "batch96", "instances": len(inst), "rows_total": T, "gkb_steps": L,
+                       "precision": "mixed", "storage": "matrix_free", "rule": "gcv", "test_points_per_instance": m},
+            "gkb_steps_per_s": round(steps_total / (ms / 1e3), 1),
+            "regenerated_entries_per_s": entries / (ms / 1e3),
+            "re_vs_exact": {"median": float(np.median(errs)), "max": float(np.max(errs))},
+            "tuning": tune, "clocks": clocks}
+
+
 # --------------------------------------------------------------------------- oracle
 def oracle_solve(wl, c, k, steps):
     from oracle import evaluate as OE
@@ -397,6 +469,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "batch96":
+        out = run_batch(args, rank, world, local_rank)
     else:
         out = run_ours(args, rank, world, local_rank)
         if out is not None and not args.no_cpu_baseline:

@@ -248,6 +248,65 @@ rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const double* d_f,
 rbf_status rbf_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* d_coef,
                         const double* d_points, int64_t m, double* d_u);
 
+/* ---- batched instances (many uneven problems in one graph launch) ------ */
+
+/* A batch of independent collocation problems of uneven size, advanced through
+ * GKB together.  Concatenated layouts use off_b = sum_{a<b} n_a. */
+typedef struct {
+    int count;                   /* number of instances B >= 1 */
+    const int64_t* n;            /* host [B] nodes per instance */
+    const int64_t* n_interior;   /* host [B] PDE rows per instance */
+    const double* c;             /* host [B] MQ shape parameters */
+    const double* k;             /* host [B] wavenumbers */
+    const double* d_nodes;       /* device FP64: instance b's SoA [3][n_b] at 3 * off_b */
+    const double* d_f;           /* device FP64: f_b at off_b */
+    int capacity;                /* L: maximum GKB steps per instance */
+    double* d_W;                 /* device: W_b (n_b x (L+1), column-major, ld n_b) at (L+1) * off_b */
+    double* d_Z;                 /* device: Z_b (n_b x L, ld n_b) at L * off_b */
+    double* d_alpha;             /* device [B][L] */
+    double* d_beta;              /* device [B][L+1] */
+    int* steps_done;             /* host [B], written by rbf_batch_gkb */
+    int* breakdown;              /* host [B], written by rbf_batch_gkb */
+} rbf_batch;
+
+/* Autotuner choice for the batched matrix-free product (see rbf_batch_gkb). */
+typedef struct {
+    int mf_outputs_per_thread;   /* outputs held in registers per thread */
+    int mf_threads;              /* threads per CTA */
+    int candidates;              /* configurations timed */
+    double best_ms;              /* time of one A and one A^T product of the batch, best config */
+    int graph_kernels;           /* kernels in the captured step graph (0 if not captured) */
+} rbf_tuning;
+
+/* Run `steps` GKB steps (Algorithm 1, same reorthogonalization and breakdown
+ * rule as rbf_gkb) on every instance of the batch, mixed precision with the
+ * matrix-free FP32 product (entries regenerated from the nodes; FP64
+ * reorthogonalization, norms and scalars).  All instances advance in lock
+ * step: per step one batched A^T product, one cooperative reorthogonalization
+ * kernel over the concatenated rows, one batched A product and one more
+ * reorthogonalization kernel; the whole step loop is captured once into a CUDA
+ * graph and launched as one graph.  Instances that break down stop
+ * individually.  On the first call for a batch shape the product's tile shape
+ * is chosen by timing candidate configurations on the batch itself (see
+ * rbf_get_tuning).  Synchronises; fills steps_done and breakdown.  Errors:
+ * RBF_ERR_INVALID (sizes, pointers, steps > capacity or > n_b), RBF_ERR_TIMEOUT
+ * (a bounded grid barrier gave up). */
+rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* batch, int steps, int form);
+
+/* HKT (Algorithm 4) for every instance of a batch after rbf_batch_gkb: projected
+ * SVD, lambda by `rule` (RBF_GCV or RBF_LCURVE) on each instance's grid, solve
+ * and lift into d_coef (device, instance b at off_b).  h_lambda: host [B] out. */
+rbf_status rbf_batch_hkt(rbf_ctx* ctx, const rbf_batch* batch, int rule, double* d_coef, double* h_lambda);
+
+/* Reconstruction for every instance: d_u (device, instance b at moff_b =
+ * sum_{a<b} m_a) at the m_b points of d_points (device FP64 SoA [3][m_b] at
+ * 3 * moff_b), FP64. */
+rbf_status rbf_batch_evaluate(rbf_ctx* ctx, const rbf_batch* batch, int form, const double* d_coef,
+                              const double* d_points, const int64_t* m, double* d_u);
+
+/* The autotuner's last choice. */
+rbf_status rbf_get_tuning(const rbf_ctx* ctx, rbf_tuning* out);
+
 /* ---- allocation-free product (no counterpart in the paper) ------------- */
 
 /* Elements of the library's static device scratch used by rbf_matvec_t_noalloc

@@ -128,6 +128,7 @@ rbf_status rbf_get_counters(rbf_ctx* ctx, rbf_counters* out, int reset) {
 rbf_status rbf_destroy(rbf_ctx* ctx) {
     if (!ctx) return RBF_OK;
     if (ctx->stream || ctx->d_state) cudaStreamSynchronize(ctx->stream);
+    rbf_batch_state_free(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_state) cudaFree(ctx->d_state);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);

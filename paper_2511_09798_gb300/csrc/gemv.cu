@@ -31,9 +31,8 @@ __global__ void __launch_bounds__(GN_THREADS) k_gemv_n_f64(
     double* __restrict__ z_out, const int* __restrict__ done) {
     if (gkb_done(done)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t r0 = (int64_t)blockIdx.x * per;
-    const int64_t r1 = min(n, r0 + per);
+    const int64_t r0 = n * (int64_t)blockIdx.x / gridDim.x;  // balanced row partition
+    const int64_t r1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
     const int64_t nvec = n >> 1;  // full double2 vectors per row
     const double2* __restrict__ xv = reinterpret_cast<const double2*>(x);
     for (int64_t i = r0 + warp; i < r1; i += GN_THREADS / 32) {
@@ -73,9 +72,8 @@ __global__ void __launch_bounds__(GN_THREADS) k_gemv_n_f32(
     const double* __restrict__ w, double* __restrict__ z_out, const int* __restrict__ done) {
     if (gkb_done(done)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t r0 = (int64_t)blockIdx.x * per;
-    const int64_t r1 = min(n, r0 + per);
+    const int64_t r0 = n * (int64_t)blockIdx.x / gridDim.x;  // balanced row partition
+    const int64_t r1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
     const int64_t nvec = n >> 2;
     const float4* __restrict__ xv = reinterpret_cast<const float4*>(x32);
     for (int64_t i = r0 + warp; i < r1; i += GN_THREADS / 32) {
@@ -122,9 +120,8 @@ __global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f64(
     __shared__ double xs[GT_MAX_CHUNK_ROWS];
     const int q = blockIdx.x % chunks;
     const int pnl = blockIdx.x / chunks;
-    const int64_t per = (n + chunks - 1) / chunks;
-    const int64_t i0 = (int64_t)q * per;
-    const int64_t i1 = min(n, i0 + per);
+    const int64_t i0 = n * (int64_t)q / chunks;  // balanced row chunks
+    const int64_t i1 = n * (int64_t)(q + 1) / chunks;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += GT_THREADS) xs[i - i0] = x[i];
     __syncthreads();
     const int64_t c = (int64_t)pnl * panel_cols + 2 * threadIdx.x;
@@ -164,9 +161,8 @@ __global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f32(
     __shared__ float xs[GT_MAX_CHUNK_ROWS];
     const int q = blockIdx.x % chunks;
     const int pnl = blockIdx.x / chunks;
-    const int64_t per = (n + chunks - 1) / chunks;
-    const int64_t i0 = (int64_t)q * per;
-    const int64_t i1 = min(n, i0 + per);
+    const int64_t i0 = n * (int64_t)q / chunks;  // balanced row chunks
+    const int64_t i1 = n * (int64_t)(q + 1) / chunks;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += GT_THREADS) xs[i - i0] = x32[i];
     __syncthreads();
     const int64_t c = (int64_t)pnl * panel_cols + 4 * threadIdx.x;

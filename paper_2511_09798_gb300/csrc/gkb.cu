@@ -1,26 +1,26 @@
 // Golub-Kahan bidiagonalization with full reorthogonalization (Algorithm 1).
 //
 // One half-step (r-side: r = A^T w_j - beta_j z_{j-1}; p-side: p = A z_j -
-// alpha_j w_j) is a fixed chain of kernels on the context stream:
+// alpha_j w_j) is two launches on the context stream:
 //
-//   finalize  1 CTA   nrm = |q_raw| from per-slab partials; breakdown test
-//                     (tau = factor * N * eps * c_hat); stores alpha_j or beta_j
-//   product           partial sums of A^T q_raw or A q_raw (assembled or
-//                     matrix-free), one row of partials per chunk
-//   R1        slab    v = (sum of partials) / nrm - nrm * u;  writes the
-//                     normalised previous vector q_raw / nrm into its basis;
-//                     per-slab partials of Q^T v
-//   reduce            h = Q^T v
-//   R2        slab    v -= Q h; per-slab partials of Q^T v
-//   reduce            h = Q^T v
-//   R3        slab    v -= Q h; per-slab partials of |v|^2 (+ FP32 copy of v)
+//   product   partial sums of A^T q_raw or A q_raw (assembled or matrix-free),
+//             one row of partials per chunk (q_raw unnormalised)
+//   k_half    one cooperative kernel, one CTA per SM, each CTA owning a slab
+//             of rows:  finalize nrm = |q_raw| from the previous |v|^2
+//             partials (alpha_j or beta_j, breakdown test tau = factor * N *
+//             eps * c_hat) -> v = (sum of partials) / nrm - nrm * u, store
+//             q_raw / nrm into its basis -> [per-slab Q^T v partials, grid
+//             barrier, distributed reduction, grid barrier, v -= Q h] twice
+//             -> |v|^2 partials.  The CTA's slab of Q and of the product
+//             partials is staged in shared memory (cp.async) while the norm
+//             is finalised.
 //
 // i.e. classical Gram-Schmidt applied twice ("twice is enough") against the
 // current basis before the norm, which is the reorthogonalization placement
 // chosen for Algorithm 1 step 7.  All reductions are deterministic (fixed
-// order), so repeated runs are bitwise identical.  Once a breakdown is found the
-// finalize kernel sets a device flag and every later kernel of the run returns
-// immediately.
+// order), so repeated runs are bitwise identical.  Grid barriers poll a bounded
+// number of times and report RBF_ERR_TIMEOUT instead of hanging.  Once a
+// breakdown is found a device flag makes every later kernel return at once.
 #include <cfloat>
 
 #include "common.cuh"
@@ -37,54 +37,12 @@ constexpr int UPD_GROUPS = SL_THREADS / UPD_ROWS;
 struct Slab {
     int64_t r0, r1;
 };
+// Balanced contiguous partition: CTA b owns rows [n b / G, n (b+1) / G).
 __device__ __forceinline__ Slab slab_of(int64_t n) {
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     Slab s;
-    s.r0 = (int64_t)blockIdx.x * per;
-    s.r1 = min(n, s.r0 + per);
-    if (s.r1 < s.r0) s.r1 = s.r0;
+    s.r0 = n * (int64_t)blockIdx.x / gridDim.x;
+    s.r1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
     return s;
-}
-
-// hpart[m * G + b] = sum_{i in slab b} Q[m][i] v[i]   (warp per basis vector)
-__device__ __forceinline__ void slab_dot(const double* __restrict__ Q, int64_t ldq, int mcount,
-                                         const double* __restrict__ vs, Slab s,
-                                         double* __restrict__ hpart) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t rows = s.r1 - s.r0;
-    for (int m = warp; m < mcount; m += SL_WARPS) {
-        const double* __restrict__ q = Q + (int64_t)m * ldq + s.r0;
-        double acc = 0.0;
-        for (int64_t i = lane; i < rows; i += 32) acc = fma(q[i], vs[i], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) hpart[(int64_t)m * gridDim.x + blockIdx.x] = acc;
-    }
-}
-
-// vs[i] -= sum_m Q[m][i] h[m] for the slab rows.
-__device__ __forceinline__ void slab_update(const double* __restrict__ Q, int64_t ldq, int mcount,
-                                            const double* __restrict__ hs, double* __restrict__ vs,
-                                            Slab s, double* red /* [UPD_GROUPS][UPD_ROWS] */) {
-    const int row = threadIdx.x % UPD_ROWS;
-    const int grp = threadIdx.x / UPD_ROWS;
-    const int64_t rows = s.r1 - s.r0;
-    for (int64_t base = 0; base < rows; base += UPD_ROWS) {
-        const int64_t i = base + row;
-        double acc = 0.0;
-        if (i < rows) {
-            const double* __restrict__ q = Q + s.r0 + i;
-            for (int m = grp; m < mcount; m += UPD_GROUPS) acc = fma(q[(int64_t)m * ldq], hs[m], acc);
-        }
-        red[grp * UPD_ROWS + row] = acc;
-        __syncthreads();
-        if (grp == 0 && i < rows) {
-            double t = 0.0;
-#pragma unroll
-            for (int g = 0; g < UPD_GROUPS; ++g) t += red[g * UPD_ROWS + row];
-            vs[i] -= t;
-        }
-        __syncthreads();
-    }
 }
 
 // Block-wide deterministic sum of v over [0, count).
@@ -142,9 +100,10 @@ __global__ void k_finalize(rbf_dev_state* __restrict__ stt, const double* __rest
                 sc[SC_INV_BETA] = 1.0 / nrm;
                 sc[SC_CHAT0] = 0.0;
             }
-        } else {  // beta_j closes step j-1
-            double ch = fmax(sc[SC_CHAT0], hypot(alpha[j - 2], nrm));
+        } else {  // beta_j closes step j-1 (c_hat slot j&1 in, both slots out)
+            double ch = fmax(sc[SC_CHAT0 + (j & 1)], hypot(alpha[j - 2], nrm));
             sc[SC_CHAT0] = ch;
+            sc[SC_CHAT1] = ch;
             double tau = factor * (double)n * eps * ch;
             if (nrm <= tau) {
                 brk = 2;
@@ -168,85 +127,263 @@ __global__ void k_finalize(rbf_dev_state* __restrict__ stt, const double* __rest
 }
 
 // ---------------------------------------------------------------------------
-// R1: v = inv * sum_q part[q][i] - nrm * u[i]; basis_out = q_raw * inv;
-//     hpart = Q^T v (mcount vectors)
+// Grid barrier for the cooperative half-step kernel: two levels so that no
+// L2 address sees more than ~sqrt(G) atomics (one address with all G CTAs
+// serialises ~14 ns per atomic).  bar[0..K) are group counters, bar[K] the top
+// counter, bar[K+1] the generation; each on its own 128-byte line (stride 32).
+// Bounded: after `budget` polls it records RBF_ERR_TIMEOUT in the device state,
+// stops the run and returns false; the caller's CTA then exits without further
+// barriers.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(SL_THREADS) k_r1(const rbf_dev_state* __restrict__ stt, int64_t n,
-                                                   int chunks, const double* __restrict__ part,
-                                                   int inv_idx, int nrm_idx,
-                                                   const double* __restrict__ u,
-                                                   const double* __restrict__ q_raw,
-                                                   double* __restrict__ basis_out,
-                                                   double* __restrict__ v_out,
-                                                   const double* __restrict__ Q, int64_t ldq,
-                                                   int mcount, double* __restrict__ hpart) {
-    if (stt->info[IN_DONE]) return;
-    __shared__ double vs[SL_MAX_ROWS];
-    const Slab s = slab_of(n);
-    const double inv = stt->scal[inv_idx];
-    const double nrm = stt->scal[nrm_idx];
-    for (int64_t i = s.r0 + threadIdx.x; i < s.r1; i += SL_THREADS) {
-        double acc = 0.0;
-        for (int q = 0; q < chunks; ++q) acc += part[(int64_t)q * n + i];
-        double v = acc * inv;
-        if (u) v = fma(-nrm, u[i], v);
-        v_out[i] = v;
-        vs[i - s.r0] = v;
-        if (basis_out) basis_out[i] = q_raw[i] * inv;
-    }
-    __syncthreads();
-    slab_dot(Q, ldq, mcount, vs, s, hpart);
-}
+constexpr int BAR_STRIDE = 32;
 
-// h[m] = sum_b hpart[m * G + b]   (warp per m)
-__global__ void k_reduce_h(const rbf_dev_state* __restrict__ stt, const double* __restrict__ hpart,
-                           int G, int mcount, double* __restrict__ h) {
-    if (stt->info[IN_DONE]) return;
-    const int m = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (m >= mcount) return;
-    double acc = 0.0;
-    for (int b = lane; b < G; b += 32) acc += hpart[(int64_t)m * G + b];
-    acc = warp_sum(acc);
-    if (lane == 0) h[m] = acc;
-}
-
-// R2 (mode 0): v -= Q h; hpart = Q^T v.   R3 (mode 1): v -= Q h; npart = |v|^2 (+ v32).
-__global__ void __launch_bounds__(SL_THREADS) k_r23(const rbf_dev_state* __restrict__ stt, int64_t n,
-                                                    double* __restrict__ v,
-                                                    const double* __restrict__ Q, int64_t ldq,
-                                                    int mcount, const double* __restrict__ h,
-                                                    int mode, double* __restrict__ hpart,
-                                                    double* __restrict__ npart,
-                                                    float* __restrict__ v32) {
-    if (stt->info[IN_DONE]) return;
-    __shared__ double vs[SL_MAX_ROWS];
-    __shared__ double hs[1024];
-    __shared__ double red[UPD_GROUPS * UPD_ROWS];
-    const Slab s = slab_of(n);
-    const int64_t rows = s.r1 - s.r0;
-    for (int m = threadIdx.x; m < mcount; m += SL_THREADS) hs[m] = h[m];
-    for (int64_t i = threadIdx.x; i < rows; i += SL_THREADS) vs[i] = v[s.r0 + i];
+__device__ bool grid_sync(rbf_dev_state* __restrict__ stt, unsigned* __restrict__ bar, int group,
+                          long long budget) {
+    __shared__ int ok;
     __syncthreads();
-    if (mcount > 0) slab_update(Q, ldq, mcount, hs, vs, s, red);
-    for (int64_t i = threadIdx.x; i < rows; i += SL_THREADS) {
-        v[s.r0 + i] = vs[i];
-        if (mode == 1 && v32) v32[s.r0 + i] = (float)vs[i];
-    }
-    __syncthreads();
-    if (mode == 0) {
-        slab_dot(Q, ldq, mcount, vs, s, hpart);
-    } else {
-        double acc = 0.0;
-        for (int64_t i = threadIdx.x; i < rows; i += SL_THREADS) acc = fma(vs[i], vs[i], acc);
-        acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < SL_WARPS; ++w) t += red[w];
-            npart[blockIdx.x] = t;
+    if (threadIdx.x == 0) {
+        const int G = gridDim.x;
+        const int K = (G + group - 1) / group;
+        const int grp = blockIdx.x / group;
+        const int members = min(group, G - grp * group);
+        unsigned* sub = bar + (size_t)grp * BAR_STRIDE;
+        unsigned* top = bar + (size_t)K * BAR_STRIDE;
+        volatile unsigned* gen = bar + (size_t)(K + 1) * BAR_STRIDE;
+        const unsigned g0 = *gen;
+        __threadfence();
+        int good = 1;
+        if (atomicAdd(sub, 1u) == (unsigned)members - 1) {
+            atomicExch(sub, 0u);
+            if (atomicAdd(top, 1u) == (unsigned)K - 1) {
+                atomicExch(top, 0u);
+                __threadfence();
+                atomicAdd((unsigned*)gen, 1u);
+            }
         }
+        long long it = 0;
+        while (*gen == g0) {
+            if (++it > budget) {
+                good = 0;
+                atomicExch(&stt->info[IN_ERR], (int)RBF_ERR_TIMEOUT);
+                atomicExch(&stt->info[IN_DONE], 1);
+                break;
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ void cp_async8(double* smem_dst, const double* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+struct HalfArgs {
+    rbf_dev_state* stt;
+    int64_t n;
+    int chunks;
+    const double* part;   // product partials [chunks][n]
+    int side;             // 0: r-side (beta_j), 1: p-side (alpha_j)
+    int j;                // 1-based step
+    int resume;           // first r-side of a resumed run: scalars are preset
+    double factor;        // breakdown factor
+    double* alpha;
+    double* beta;
+    const double* u;      // z_{j-1} (r-side, j >= 2) or w_j (p-side)
+    const double* q_raw;  // vector whose norm is finalised here
+    double* basis_out;    // w_j (r-side) or z_j (p-side) = q_raw / nrm
+    double* v;            // new vector
+    float* v32;           // FP32 copy of v (mixed precision) or null
+    const double* Q;      // basis to reorthogonalize against (Z or W)
+    int64_t ldq;
+    int mcount;
+    double* hpart;        // [mcount][G] dot partials
+    double* h;            // [mcount] reduced dots
+    double* npart;        // in: |q_raw|^2 partials; out: |v|^2 partials
+    int rmax;             // max slab rows (shared-memory stride)
+    unsigned* bar;        // barrier counters (see grid_sync)
+    int bar_group;        // CTAs per barrier group
+    long long budget;
+};
+
+// One half-step of Algorithm 1 after the product: finalize the norm of q_raw
+// (alpha_j or beta_j, breakdown test), form v, and reorthogonalize it twice
+// against Q (classical Gram-Schmidt), ending with the |v|^2 partials.
+// STAGE: the CTA's slab of Q is copied to shared memory once (cp.async,
+// overlapped with the norm finalisation) and all four passes over Q read it
+// there; otherwise they read Q from L2.  The product partials of the slab are
+// always staged.
+template <bool STAGE>
+__global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
+    extern __shared__ double dsm[];
+    __shared__ double red[UPD_GROUPS * UPD_ROWS];
+    __shared__ double nrm_s, inv_s;
+    __shared__ int brk_s;
+    rbf_dev_state* stt = a.stt;
+    if (*(volatile int*)&stt->info[IN_DONE]) return;
+    const Slab s = slab_of(a.n);
+    const int R = (int)(s.r1 - s.r0);
+    const int RM = a.rmax;
+    const int M = a.mcount;
+    double* Qs = dsm;                                 // [M][RM]   (STAGE)
+    double* ps = Qs + (STAGE ? (size_t)M * RM : 0);   // [chunks][RM]
+    double* vs = ps + (size_t)a.chunks * RM;          // [RM]
+    double* hs = vs + RM;                             // [M]
+    // ---- stage the slab's product partials and (STAGE) its rows of Q
+    for (int q = threadIdx.x / 32; q < a.chunks; q += SL_WARPS)
+        for (int i = threadIdx.x & 31; i < R; i += 32)
+            cp_async8(ps + (size_t)q * RM + i, a.part + (int64_t)q * a.n + s.r0 + i);
+    if (STAGE)
+        for (int m = threadIdx.x / 32; m < M; m += SL_WARPS)
+            for (int i = threadIdx.x & 31; i < R; i += 32)
+                cp_async8(Qs + (size_t)m * RM + i, a.Q + (int64_t)m * a.ldq + s.r0 + i);
+    // ---- finalize the norm (every CTA computes the same value in the same order)
+    if (threadIdx.x < 32) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) acc += a.npart[b];
+        acc = warp_sum(acc);
+        if (threadIdx.x == 0) {
+            double* sc = stt->scal;
+            const double eps = DBL_EPSILON;
+            double nrm = sqrt(acc);
+            int brk = 0;
+            // c_hat double buffer: the r-side of step j reads slot j&1, writes (j+1)&1;
+            // the p-side of step j reads slot (j+1)&1
+            const int rd = a.side == 0 ? (a.j & 1) : ((a.j + 1) & 1);
+            const double ch_old = sc[SC_CHAT0 + rd];
+            double ch_new = ch_old;
+            if (a.resume) {
+                nrm = sc[SC_BETA];
+            } else if (a.side == 1) {
+                brk = nrm <= a.factor * (double)a.n * eps * fmax(ch_old, nrm) ? 1 : 0;
+            } else if (a.j == 1) {
+                brk = nrm > 0.0 ? 0 : 1;
+            } else {
+                ch_new = fmax(ch_old, hypot(a.alpha[a.j - 2], nrm));
+                brk = nrm <= a.factor * (double)a.n * eps * ch_new ? 2 : 0;
+            }
+            nrm_s = nrm;
+            inv_s = a.resume ? 1.0 : 1.0 / nrm;
+            brk_s = brk;
+            if (blockIdx.x == 0) {
+                if (a.side == 0 && !a.resume) sc[SC_CHAT0 + ((a.j + 1) & 1)] = ch_new;
+                if (brk) {
+                    stt->info[IN_STEPS] = a.j - 1;
+                    stt->info[IN_BREAK] = brk;
+                    if (brk == 2) a.beta[a.j - 1] = 0.0;
+                    stt->info[IN_DONE] = 1;
+                } else if (a.side == 1) {
+                    a.alpha[a.j - 1] = nrm;
+                    sc[SC_ALPHA] = nrm;
+                } else {
+                    a.beta[a.j - 1] = nrm;
+                    sc[SC_BETA] = nrm;
+                    stt->info[IN_STEPS] = a.j - 1;
+                }
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (brk_s) {
+        if (brk_s == 2 && a.basis_out)  // w_j = 0 after a beta breakdown
+            for (int64_t i = s.r0 + threadIdx.x; i < s.r1; i += SL_THREADS) a.basis_out[i] = 0.0;
+        return;
+    }
+    const double nrm = nrm_s, inv = inv_s;
+    // ---- R1: v = (sum of partials) / nrm - nrm u; store q_raw / nrm
+    for (int i = threadIdx.x; i < R; i += SL_THREADS) {
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+        int q = 0;
+        for (; q + 3 < a.chunks; q += 4) {
+            p0 += ps[(size_t)q * RM + i];
+            p1 += ps[(size_t)(q + 1) * RM + i];
+            p2 += ps[(size_t)(q + 2) * RM + i];
+            p3 += ps[(size_t)(q + 3) * RM + i];
+        }
+        for (; q < a.chunks; ++q) p0 += ps[(size_t)q * RM + i];
+        double v = ((p0 + p1) + (p2 + p3)) * inv;
+        if (a.u) v = fma(-nrm, a.u[s.r0 + i], v);
+        vs[i] = v;
+        a.basis_out[s.r0 + i] = a.q_raw[s.r0 + i] * inv;
+    }
+    __syncthreads();
+    const double* qb = STAGE ? (const double*)Qs : a.Q + s.r0;
+    const int64_t qld = STAGE ? (int64_t)RM : a.ldq;
+    for (int pass = 0; pass < 2; ++pass) {
+        // per-slab partials of Q^T v: one thread per basis vector, 4 chains
+        for (int m = threadIdx.x; m < M; m += SL_THREADS) {
+            const double* q = qb + (int64_t)m * qld;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            int i = 0;
+            for (; i + 3 < R; i += 4) {
+                a0 = fma(q[i], vs[i], a0);
+                a1 = fma(q[i + 1], vs[i + 1], a1);
+                a2 = fma(q[i + 2], vs[i + 2], a2);
+                a3 = fma(q[i + 3], vs[i + 3], a3);
+            }
+            for (; i < R; ++i) a0 = fma(q[i], vs[i], a0);
+            a.hpart[(int64_t)m * gridDim.x + blockIdx.x] = (a0 + a1) + (a2 + a3);
+        }
+        if (!grid_sync(stt, a.bar, a.bar_group, a.budget)) return;
+        // distributed reduction: CTA b sums the partials of the vectors m = b, b+G, ...
+        if (threadIdx.x < 32) {
+            const int G = gridDim.x;
+            for (int m = blockIdx.x; m < M; m += G) {
+                double acc = 0.0;
+                for (int b = threadIdx.x; b < G; b += 32) acc += __ldcg(a.hpart + (int64_t)m * G + b);
+                acc = warp_sum(acc);
+                if (threadIdx.x == 0) a.h[m] = acc;
+            }
+        }
+        if (!grid_sync(stt, a.bar, a.bar_group, a.budget)) return;
+        for (int m = threadIdx.x; m < M; m += SL_THREADS) hs[m] = __ldcg(a.h + m);
+        __syncthreads();
+        // v -= Q h: thread (row, group of basis vectors), two chains each
+        const int row = threadIdx.x % UPD_ROWS;
+        const int grp = threadIdx.x / UPD_ROWS;
+        for (int base = 0; base < R; base += UPD_ROWS) {
+            const int i = base + row;
+            double c0 = 0.0, c1 = 0.0;
+            if (i < R) {
+                const double* q = qb + i;
+                int m = grp;
+                for (; m + UPD_GROUPS < M; m += 2 * UPD_GROUPS) {
+                    c0 = fma(q[(int64_t)m * qld], hs[m], c0);
+                    c1 = fma(q[(int64_t)(m + UPD_GROUPS) * qld], hs[m + UPD_GROUPS], c1);
+                }
+                for (; m < M; m += UPD_GROUPS) c0 = fma(q[(int64_t)m * qld], hs[m], c0);
+            }
+            red[grp * UPD_ROWS + row] = c0 + c1;
+            __syncthreads();
+            if (grp == 0 && i < R) {
+                double t = 0.0;
+#pragma unroll
+                for (int gq = 0; gq < UPD_GROUPS; ++gq) t += red[gq * UPD_ROWS + row];
+                vs[i] -= t;
+            }
+            __syncthreads();
+        }
+    }
+    // ---- store v (+ FP32 copy) and the |v|^2 partials
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < R; i += SL_THREADS) {
+        const double t = vs[i];
+        a.v[s.r0 + i] = t;
+        if (a.v32) a.v32[s.r0 + i] = (float)t;
+        acc = fma(t, t, acc);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < SL_WARPS; ++w) t += red[w];
+        a.npart[blockIdx.x] = t;
     }
 }
 
@@ -290,6 +427,7 @@ __global__ void k_reset_state(rbf_dev_state* stt, int steps_done, double beta_no
         for (int t = 0; t < 8; ++t) stt->info[t] = 0;
         stt->info[IN_STEPS] = steps_done;
         stt->scal[SC_CHAT0] = c_hat;
+        stt->scal[SC_CHAT1] = c_hat;
         if (resume) {
             stt->scal[SC_BETA] = beta_now;
             stt->scal[SC_INV_BETA] = 1.0;  // q_raw is the stored, already normalised w
@@ -298,6 +436,12 @@ __global__ void k_reset_state(rbf_dev_state* stt, int steps_done, double beta_no
 }
 
 }  // namespace
+
+constexpr size_t HALF_SMEM_STAGE_MAX = 200 * 1024;
+
+static size_t half_smem_bytes(bool stage, int mcount, int chunks, int rmax) {
+    return ((stage ? (size_t)mcount * rmax : 0) + (size_t)chunks * rmax + rmax + (size_t)mcount) * sizeof(double);
+}
 
 static int slab_grid(const rbf_ctx* ctx, int64_t n) {
     int64_t g = ctx->sm_count;
@@ -332,6 +476,7 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
     b += 2 * ws_align((size_t)n * 4);                 // vr32, vp32
     b += ws_align((size_t)(steps + 2) * G * 8);       // hpart
     b += ws_align((size_t)(steps + 2) * 8);           // h
+    b += ws_align((size_t)(G + 2) * BAR_STRIDE * 4);  // barrier counters
     b += ws_align((size_t)G * 8);                     // npart
     return b + 4096;
 }
@@ -364,6 +509,24 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
     float* vp32 = wc.take<float>((size_t)n);
     double* hpart = wc.take<double>((size_t)(st->capacity + 2) * G);
     double* h = wc.take<double>((size_t)(st->capacity + 2));
+    int bar_group = 1;
+    while (bar_group * bar_group < G) ++bar_group;
+    const int bar_k = (G + bar_group - 1) / bar_group;
+    unsigned* bar = wc.take<unsigned>((size_t)(bar_k + 2) * BAR_STRIDE);
+    RBF_CUDA(ctx, cudaMemsetAsync(bar, 0, (size_t)(bar_k + 2) * BAR_STRIDE * sizeof(unsigned), ctx->stream));
+    // shared-memory plan of the half-step kernel: stage the Q slab when it fits
+    const int rmax = (int)((n + G - 1) / G);
+    const int chmax = chT > chN ? chT : chN;
+    const bool stage = half_smem_bytes(true, st->capacity + 1, chmax, rmax) <= HALF_SMEM_STAGE_MAX;
+    {
+        const size_t need = half_smem_bytes(stage, st->capacity + 1, chmax, rmax);
+        if (need > 48 * 1024) {
+            RBF_CUDA(ctx, cudaFuncSetAttribute(stage ? (const void*)k_half<true> : (const void*)k_half<false>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+        }
+        if (need > HALF_SMEM_STAGE_MAX + 64 * 1024)
+            return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "half-step shared memory too large (%zu bytes)", need);
+    }
     double* npart = wc.take<double>((size_t)G);
     rbf_dev_state* dst = ctx->d_state;
     const int* done = &dst->info[IN_DONE];
@@ -394,48 +557,52 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
         RBF_LAUNCHED(ctx, "k_norm_partials");
         q_raw = vp;
     }
-    const unsigned red_grid = (unsigned)((st->capacity + 2 + 7) / 8);
+    auto half = [&](int side, int j, int resume, const double* u, const double* qr, double* bout,
+                    double* v, float* v32, const double* Q, int64_t ldq, int mcount, int chunks) -> rbf_status {
+        HalfArgs a;
+        a.stt = dst;
+        a.n = n;
+        a.chunks = chunks;
+        a.part = part;
+        a.side = side;
+        a.j = j;
+        a.resume = resume;
+        a.factor = factor;
+        a.alpha = st->d_alpha;
+        a.beta = st->d_beta;
+        a.u = u;
+        a.q_raw = qr;
+        a.basis_out = bout;
+        a.v = v;
+        a.v32 = v32;
+        a.Q = Q;
+        a.ldq = ldq;
+        a.mcount = mcount;
+        a.hpart = hpart;
+        a.h = h;
+        a.npart = npart;
+        a.rmax = rmax;
+        a.bar = bar;
+        a.bar_group = bar_group;
+        a.budget = 1LL << 23;
+        void* args[] = {&a};
+        const size_t smem = half_smem_bytes(stage, mcount, chunks, rmax);
+        cudaError_t e = cudaLaunchCooperativeKernel(stage ? (const void*)k_half<true> : (const void*)k_half<false>,
+                                                    dim3(G), dim3(SL_THREADS), args, smem, s);
+        ctx->launches++;
+        if (e != cudaSuccess)
+            return rbf_fail(ctx, RBF_ERR_CUDA, "cooperative launch of k_half failed: %s", cudaGetErrorString(e));
+        return RBF_OK;
+    };
     for (int j = j_begin; j <= j_end; ++j) {
         // ---------------- r-side: r = A^T w_j - beta_j z_{j-1} ----------------
-        if (!(j == j_begin && j_begin > 1)) {
-            k_finalize<<<1, 256, 0, s>>>(dst, npart, G, 0, j, n, factor, st->d_alpha, st->d_beta,
-                                         W + (int64_t)(j - 1) * ldw, 0);
-            RBF_LAUNCHED(ctx, "k_finalize");
-        }
         RBF_TRY(gkb_product(ctx, op, 1, q_raw, vp32, part, done));
-        const int mz = j - 1;
-        k_r1<<<G, SL_THREADS, 0, s>>>(dst, n, chT, part, SC_INV_BETA, SC_BETA,
-                                      j >= 2 ? Z + (int64_t)(j - 2) * ldz : nullptr, q_raw,
-                                      W + (int64_t)(j - 1) * ldw, vr, Z, ldz, mz, hpart);
-        RBF_LAUNCHED(ctx, "k_r1");
-        k_reduce_h<<<red_grid, 256, 0, s>>>(dst, hpart, G, mz, h);
-        RBF_LAUNCHED(ctx, "k_reduce_h");
-        k_r23<<<G, SL_THREADS, 0, s>>>(dst, n, vr, Z, ldz, mz, h, 0, hpart, npart, nullptr);
-        RBF_LAUNCHED(ctx, "k_r23");
-        k_reduce_h<<<red_grid, 256, 0, s>>>(dst, hpart, G, mz, h);
-        RBF_LAUNCHED(ctx, "k_reduce_h");
-        k_r23<<<G, SL_THREADS, 0, s>>>(dst, n, vr, Z, ldz, mz, h, 1, hpart, npart,
-                                       mixed ? vr32 : nullptr);
-        RBF_LAUNCHED(ctx, "k_r23");
+        RBF_TRY(half(0, j, (j == j_begin && j_begin > 1) ? 1 : 0, j >= 2 ? Z + (int64_t)(j - 2) * ldz : nullptr,
+                     q_raw, W + (int64_t)(j - 1) * ldw, vr, mixed ? vr32 : nullptr, Z, ldz, j - 1, chT));
         // ---------------- p-side: p = A z_j - alpha_j w_j ----------------
-        k_finalize<<<1, 256, 0, s>>>(dst, npart, G, 1, j, n, factor, st->d_alpha, st->d_beta,
-                                     nullptr, 0);
-        RBF_LAUNCHED(ctx, "k_finalize");
         RBF_TRY(gkb_product(ctx, op, 0, vr, vr32, part, done));
-        const int mw = j;
-        k_r1<<<G, SL_THREADS, 0, s>>>(dst, n, chN, part, SC_INV_ALPHA, SC_ALPHA,
-                                      W + (int64_t)(j - 1) * ldw, vr, Z + (int64_t)(j - 1) * ldz, vp,
-                                      W, ldw, mw, hpart);
-        RBF_LAUNCHED(ctx, "k_r1");
-        k_reduce_h<<<red_grid, 256, 0, s>>>(dst, hpart, G, mw, h);
-        RBF_LAUNCHED(ctx, "k_reduce_h");
-        k_r23<<<G, SL_THREADS, 0, s>>>(dst, n, vp, W, ldw, mw, h, 0, hpart, npart, nullptr);
-        RBF_LAUNCHED(ctx, "k_r23");
-        k_reduce_h<<<red_grid, 256, 0, s>>>(dst, hpart, G, mw, h);
-        RBF_LAUNCHED(ctx, "k_reduce_h");
-        k_r23<<<G, SL_THREADS, 0, s>>>(dst, n, vp, W, ldw, mw, h, 1, hpart, npart,
-                                       mixed ? vp32 : nullptr);
-        RBF_LAUNCHED(ctx, "k_r23");
+        RBF_TRY(half(1, j, 0, W + (int64_t)(j - 1) * ldw, vr, Z + (int64_t)(j - 1) * ldz, vp,
+                     mixed ? vp32 : nullptr, W, ldw, j, chN));
         q_raw = vp;
     }
     // beta_{l+1} and w_{l+1}
@@ -468,7 +635,11 @@ static rbf_status read_back(rbf_ctx* ctx, rbf_gkb_state* st) {
     RBF_CUDA(ctx, cudaGetLastError());
     st->steps_done = ctx->h_state->info[IN_STEPS];
     st->breakdown = ctx->h_state->info[IN_BREAK];
-    st->c_hat = ctx->h_state->scal[SC_CHAT0];
+    st->c_hat = ctx->h_state->scal[SC_CHAT0] > ctx->h_state->scal[SC_CHAT1] ? ctx->h_state->scal[SC_CHAT0]
+                                                                           : ctx->h_state->scal[SC_CHAT1];
+    if (ctx->h_state->info[IN_ERR] != 0)
+        return rbf_fail(ctx, (rbf_status)ctx->h_state->info[IN_ERR],
+                        "a bounded device-side wait gave up (grid barrier of the GKB half-step)");
     return RBF_OK;
 }
 

@@ -46,7 +46,9 @@ struct rbf_ctx {
     cudaEvent_t* pev = nullptr;   // [2][PMAX][2] product start/stop events
     int pcount[2] = {0, 0};       // recorded pairs per product kind
     int64_t ptotal[2] = {0, 0};   // launches per product kind
+    void* batch_state = nullptr;  // batched GKB: tuning choice, captured graph, stream
 };
+void rbf_batch_state_free(rbf_ctx* ctx);
 
 // ---- error helpers ---------------------------------------------------------
 rbf_status rbf_fail(rbf_ctx* ctx, rbf_status st, const char* fmt, ...);
@@ -125,9 +127,35 @@ rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, co
 rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_begin, int j_end,
                    rbf_gkb_state* st);
 size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision);
-// svd.cu
+// svd.cu: batched projected problem (blockIdx.y / blockIdx.x = instance b; buffers
+// strided by the capacity L: alpha [B][L], beta [B][L+1], sigma [B][L],
+// ftil [B][L+1], V [B][L][ldv]); l per instance from l_arr (device) or l.
+struct ProjDims {
+    int B;
+    int L;
+    int l;
+    const int* l_arr;
+};
 size_t svd_ws_bytes(int l);
+size_t svd_ws_bytes_batch(int L, int B);
+rbf_status launch_projected_svd_batch(rbf_ctx* ctx, ProjDims d, const double* alpha, const double* beta,
+                                      double* sigma, double* ftil, double* V, int64_t ldv, void* ws,
+                                      double* sigma1_out, double* ftil_last_out);
 rbf_status launch_projected_svd(rbf_ctx* ctx, const double* alpha, const double* beta, int l,
                                 double* sigma, double* ftil, double* V, int64_t ldv, void* ws);
 // select.cu
+struct LiftDims {           // lift coef = Z y per instance
+    const int64_t* n_arr;   // device [B] sizes (batched) or null
+    const int64_t* zoff;    // device [B] offsets of Z_b (batched, ld = n_b) or null
+    const int64_t* coff;    // device [B] offsets of coef_b or null
+    int64_t n;              // single instance: n
+    int64_t ldz;            // single instance: ld of Z
+    int64_t nmax;           // max n (grid size)
+};
 size_t select_ws_bytes(const rbf_ctx* ctx, int l);
+size_t select_ws_bytes_batch(const rbf_ctx* ctx, int L, int B);
+// method 0: HKT with `rule`; 1: Ine-TSVD with `rank` (0 = GCV).
+rbf_status launch_select_batch(rbf_ctx* ctx, ProjDims d, int method, int rule, double lambda_in, int rank,
+                               const double* alpha, const double* beta, const double* Z, LiftDims ld,
+                               double* coef, double* curve, void* ws, double* lam_out, int* idx_out,
+                               int* rank_out, bool single);

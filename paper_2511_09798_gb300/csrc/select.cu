@@ -29,11 +29,17 @@ __device__ __forceinline__ double grid_t(int idx, int J, double t_lo, double t_h
     return __dadd_rn(__dmul_rn((double)idx, step), t_lo);
 }
 
-__global__ void k_grid_terms(const double* __restrict__ sigma, const double* __restrict__ ftil, int l,
-                             int J, double t_lo, double t_hi, double* __restrict__ gcv,
-                             double* __restrict__ xr, double* __restrict__ ye) {
+__device__ __forceinline__ int sel_l(const ProjDims& d, int b) { return d.l_arr ? d.l_arr[b] : d.l; }
+
+__global__ void k_grid_terms(ProjDims d, const double* __restrict__ sigma_all, const double* __restrict__ ftil_all,
+                             int J, double t_lo, double t_hi, double* __restrict__ gcv_all,
+                             double* __restrict__ xr_all, double* __restrict__ ye_all) {
+    const int b = blockIdx.y;
+    const int l = sel_l(d, b);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= J) return;
+    if (t >= J || l < 1) return;
+    const double* sigma = sigma_all + (size_t)b * d.L;
+    const double* ftil = ftil_all + (size_t)b * (d.L + 1);
     const double lam = sigma[0] * exp10(grid_t(t, J, t_lo, t_hi));
     const double lam2 = lam * lam;
     double rho2 = 0.0, eta2 = 0.0, den = 1.0;
@@ -47,21 +53,33 @@ __global__ void k_grid_terms(const double* __restrict__ sigma, const double* __r
         den += q;
     }
     rho2 = fma(ftil[l], ftil[l], rho2);
-    gcv[t] = rho2 / (den * den);
-    xr[t] = 0.5 * log(rho2);
-    ye[t] = 0.5 * log(eta2);
+    gcv_all[(size_t)b * J + t] = rho2 / (den * den);
+    xr_all[(size_t)b * J + t] = 0.5 * log(rho2);
+    ye_all[(size_t)b * J + t] = 0.5 * log(eta2);
 }
 
 // Choose lambda (rule 0 GCV, 1 L-curve, 2 fixed) and form the coefficient
-// vector cvec_i = s_i f_i / (s_i^2 + lambda^2).  One block.
-__global__ void k_choose_lambda(const double* __restrict__ sigma, const double* __restrict__ ftil, int l,
-                                int J, double t_lo, double t_hi, int rule, double lambda_in,
-                                const double* __restrict__ gcv, const double* __restrict__ xr,
-                                const double* __restrict__ ye, double* __restrict__ curve,
-                                double* __restrict__ cvec, rbf_dev_state* __restrict__ stt) {
+// vector cvec_i = s_i f_i / (s_i^2 + lambda^2).  One block per instance.
+__global__ void k_choose_lambda(ProjDims d, const double* __restrict__ sigma_all,
+                                const double* __restrict__ ftil_all, int J, double t_lo, double t_hi,
+                                int rule, double lambda_in, const double* __restrict__ gcv_all,
+                                const double* __restrict__ xr_all, const double* __restrict__ ye_all,
+                                double* __restrict__ curve_all, double* __restrict__ cvec_all,
+                                double* __restrict__ lam_out, int* __restrict__ idx_out,
+                                rbf_dev_state* __restrict__ stt) {
     __shared__ double bv[1024];
     __shared__ int bi[1024];
     __shared__ double lam_s;
+    const int b = blockIdx.x;
+    const int l = sel_l(d, b);
+    if (l < 1) return;
+    const double* sigma = sigma_all + (size_t)b * d.L;
+    const double* ftil = ftil_all + (size_t)b * (d.L + 1);
+    const double* gcv = gcv_all + (size_t)b * J;
+    const double* xr = xr_all + (size_t)b * J;
+    const double* ye = ye_all + (size_t)b * J;
+    double* curve = curve_all ? curve_all + (size_t)b * J : nullptr;
+    double* cvec = cvec_all + (size_t)b * d.L;
     const double h = (t_hi - t_lo) / (double)(J - 1);
     // per-thread best over a strided subset, then a tree with lowest-index tie-break
     double best = rule == 1 ? -INFINITY : INFINITY;
@@ -120,9 +138,13 @@ __global__ void k_choose_lambda(const double* __restrict__ sigma, const double* 
             lam = sigma[0] * exp10(grid_t(idx, J, t_lo, t_hi));
         }
         lam_s = lam;
-        stt->scal[SC_LAMBDA] = lam;
-        stt->scal[SC_SIGMA1] = sigma[0];
-        stt->info[IN_INDEX] = idx;
+        if (lam_out) lam_out[b] = lam;
+        if (idx_out) idx_out[b] = idx;
+        if (stt && b == 0) {
+            stt->scal[SC_LAMBDA] = lam;
+            stt->scal[SC_SIGMA1] = sigma[0];
+            stt->info[IN_INDEX] = idx;
+        }
     }
     __syncthreads();
     const double lam2 = lam_s * lam_s;
@@ -133,10 +155,19 @@ __global__ void k_choose_lambda(const double* __restrict__ sigma, const double* 
 }
 
 // Ine-TSVD rank by GCV_l(k) (or the given rank) and cvec_i = f_i / s_i, i <= k.
-__global__ void k_choose_rank(const double* __restrict__ sigma, const double* __restrict__ ftil, int l,
-                              int rank_in, double* __restrict__ curve, double* __restrict__ cvec,
-                              double* __restrict__ work, rbf_dev_state* __restrict__ stt) {
+__global__ void k_choose_rank(ProjDims d, const double* __restrict__ sigma_all,
+                              const double* __restrict__ ftil_all, int rank_in, double* __restrict__ curve_all,
+                              double* __restrict__ cvec_all, double* __restrict__ work_all,
+                              int* __restrict__ rank_out, rbf_dev_state* __restrict__ stt) {
     __shared__ int k_s;
+    const int b = blockIdx.x;
+    const int l = sel_l(d, b);
+    if (l < 1) return;
+    const double* sigma = sigma_all + (size_t)b * d.L;
+    const double* ftil = ftil_all + (size_t)b * (d.L + 1);
+    double* curve = curve_all ? curve_all + (size_t)b * d.L : nullptr;
+    double* cvec = cvec_all + (size_t)b * d.L;
+    double* work = work_all + (size_t)b * (d.L + 2);
     if (threadIdx.x == 0) {
         const double s1 = sigma[0];
         int r = 0;
@@ -152,11 +183,11 @@ __global__ void k_choose_rank(const double* __restrict__ sigma, const double* __
             double best = INFINITY;
             k = 1;
             for (int kk = 1; kk <= r; ++kk) {
-                const double d = (double)(l + 1 - kk);
-                const double g = work[kk] / (d * d);
-                if (curve) curve[kk - 1] = g;
-                if (g < best) {
-                    best = g;
+                const double dd = (double)(l + 1 - kk);
+                const double gv = work[kk] / (dd * dd);
+                if (curve) curve[kk - 1] = gv;
+                if (gv < best) {
+                    best = gv;
                     k = kk;
                 }
             }
@@ -164,29 +195,45 @@ __global__ void k_choose_rank(const double* __restrict__ sigma, const double* __
         }
         if (k > l) k = l;
         k_s = k;
-        stt->info[IN_RANK] = k;
-        stt->scal[SC_SIGMA1] = s1;
+        if (rank_out) rank_out[b] = k;
+        if (stt && b == 0) {
+            stt->info[IN_RANK] = k;
+            stt->scal[SC_SIGMA1] = s1;
+        }
     }
     __syncthreads();
     const int k = k_s;
     for (int i = threadIdx.x; i < l; i += blockDim.x) cvec[i] = i < k ? ftil[i] / sigma[i] : 0.0;
 }
 
-// y = V cvec (V column-major l x l, ld ldv)
-__global__ void k_vmul(const double* __restrict__ V, int64_t ldv, int l, const double* __restrict__ cvec,
-                       double* __restrict__ y) {
+// y = V cvec (V column-major l x l, ld ldv), per instance
+__global__ void k_vmul(ProjDims d, const double* __restrict__ V_all, int64_t ldv,
+                       const double* __restrict__ cvec_all, double* __restrict__ y_all) {
+    const int b = blockIdx.y;
+    const int l = sel_l(d, b);
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= l) return;
+    const double* V = V_all + (size_t)b * d.L * ldv;
+    const double* cvec = cvec_all + (size_t)b * d.L;
     double acc = 0.0;
     for (int i = 0; i < l; ++i) acc = fma(V[(int64_t)i * ldv + r], cvec[i], acc);
-    y[r] = acc;
+    y_all[(size_t)b * d.L + r] = acc;
 }
 
-// coef = Z y (Z column-major n x l): 32 rows x 4 column groups per CTA
-__global__ void __launch_bounds__(128) k_lift(const double* __restrict__ Z, int64_t ldz, int64_t n, int l,
-                                              const double* __restrict__ y, double* __restrict__ coef) {
+// coef = Z y (Z column-major n x l, ld ldz): 32 rows x 4 column groups per CTA.
+// Batched: instance b = blockIdx.y with n, Z offset, ld and coef offset from tables.
+__global__ void __launch_bounds__(128) k_lift(ProjDims d, const double* __restrict__ Z_all, LiftDims ld,
+                                              const double* __restrict__ y_all, double* __restrict__ coef_all) {
     __shared__ double red[4][32];
     __shared__ double ys[1024];
+    const int b = blockIdx.y;
+    const int l = sel_l(d, b);
+    const int64_t n = ld.n_arr ? ld.n_arr[b] : ld.n;
+    if ((int64_t)blockIdx.x * 32 >= n) return;
+    const int64_t ldz = ld.n_arr ? n : ld.ldz;
+    const double* Z = Z_all + (ld.zoff ? ld.zoff[b] : 0);
+    double* coef = coef_all + (ld.coff ? ld.coff[b] : 0);
+    const double* y = y_all + (size_t)b * d.L;
     for (int m = threadIdx.x; m < l; m += 128) ys[m] = y[m];
     __syncthreads();
     const int row = threadIdx.x & 31, grp = threadIdx.x >> 5;
@@ -201,41 +248,64 @@ __global__ void __launch_bounds__(128) k_lift(const double* __restrict__ Z, int6
 
 }  // namespace
 
-size_t select_ws_bytes(const rbf_ctx* ctx, int l) {
+size_t select_ws_bytes(const rbf_ctx* ctx, int l) { return select_ws_bytes_batch(ctx, l, 1); }
+
+rbf_status launch_select_batch(rbf_ctx* ctx, ProjDims d, int method, int rule, double lambda_in, int rank,
+                               const double* alpha, const double* beta, const double* Z, LiftDims ld,
+                               double* coef, double* curve, void* ws, double* lam_out, int* idx_out,
+                               int* rank_out, bool single) {
+    const int L = d.L, B = d.B, J = ctx->opt.grid_j;
+    const double tlo = ctx->opt.grid_t_lo, thi = ctx->opt.grid_t_hi;
+    WsCarve wc(ws);
+    double* sigma = wc.take<double>((size_t)L * B);
+    double* ftil = wc.take<double>((size_t)(L + 1) * B);
+    double* V = wc.take<double>((size_t)L * L * B);
+    double* gcv = wc.take<double>((size_t)J * B);
+    double* xr = wc.take<double>((size_t)J * B);
+    double* ye = wc.take<double>((size_t)J * B);
+    double* cvec = wc.take<double>((size_t)L * B);
+    double* y = wc.take<double>((size_t)L * B);
+    double* work = wc.take<double>((size_t)(L + 2) * B);
+    void* svd = (void*)wc.take<char>(svd_ws_bytes_batch(L, B));
+    cudaStream_t s = ctx->stream;
+    rbf_dev_state* stt = single ? ctx->d_state : nullptr;
+    rbf_timer_start(ctx);
+    RBF_TRY(launch_projected_svd_batch(ctx, d, alpha, beta, sigma, ftil, V, L, svd, nullptr, nullptr));
+    ctx->tim.svd_ms = rbf_timer_stop(ctx);
+    rbf_timer_start(ctx);
+    if (method == 0) {
+        if (rule != RBF_FIXED) {
+            k_grid_terms<<<dim3((J + 31) / 32, B), 32, 0, s>>>(d, sigma, ftil, J, tlo, thi, gcv, xr, ye);
+            RBF_LAUNCHED(ctx, "k_grid_terms");
+        }
+        k_choose_lambda<<<B, 1024, 0, s>>>(d, sigma, ftil, J, tlo, thi, rule, lambda_in, gcv, xr, ye, curve, cvec,
+                                           lam_out, idx_out, stt);
+        RBF_LAUNCHED(ctx, "k_choose_lambda");
+    } else {
+        k_choose_rank<<<B, 256, 0, s>>>(d, sigma, ftil, rank, curve, cvec, work, rank_out, stt);
+        RBF_LAUNCHED(ctx, "k_choose_rank");
+    }
+    k_vmul<<<dim3((L + 127) / 128, B), 128, 0, s>>>(d, V, L, cvec, y);
+    RBF_LAUNCHED(ctx, "k_vmul");
+    ctx->tim.select_ms = rbf_timer_stop(ctx);
+    rbf_timer_start(ctx);
+    const int64_t nmax = ld.nmax;
+    k_lift<<<dim3((unsigned)((nmax + 31) / 32), B), 128, 0, s>>>(d, Z, ld, y, coef);
+    RBF_LAUNCHED(ctx, "k_lift");
+    ctx->tim.lift_ms = rbf_timer_stop(ctx);
+    return RBF_OK;
+}
+
+size_t select_ws_bytes_batch(const rbf_ctx* ctx, int L, int B) {
     const int J = ctx->opt.grid_j;
     size_t b = 0;
-    b += ws_align((size_t)l * 8) + ws_align((size_t)(l + 1) * 8) + ws_align((size_t)l * l * 8);  // sigma, ftil, V
-    b += 3 * ws_align((size_t)J * 8);                                                           // gcv, x, y
-    b += 3 * ws_align((size_t)(l + 2) * 8);                                                     // cvec, y, work
-    return b + 4096;
+    b += ws_align((size_t)L * 8 * B) + ws_align((size_t)(L + 1) * 8 * B) + ws_align((size_t)L * L * 8 * B);
+    b += 3 * ws_align((size_t)J * 8 * B);
+    b += 3 * ws_align((size_t)(L + 2) * 8 * B);
+    return b + svd_ws_bytes_batch(L, B) + 4096;
 }
 
 namespace {
-
-struct ProjWs {
-    double *sigma, *ftil, *V, *gcv, *xr, *ye, *cvec, *y, *work;
-    void* svd;
-};
-
-rbf_status proj_prepare(rbf_ctx* ctx, const rbf_gkb_state* st, ProjWs* w) {
-    const int l = st->steps_done;
-    if (l < 1) return rbf_fail(ctx, RBF_ERR_INVALID, "state has no completed step");
-    if (l > 1023) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "projected dimension above 1023");
-    const int J = ctx->opt.grid_j;
-    RBF_TRY(rbf_ws_reserve(ctx, select_ws_bytes(ctx, l) + svd_ws_bytes(l)));
-    WsCarve wc(ctx->ws);
-    w->sigma = wc.take<double>(l);
-    w->ftil = wc.take<double>(l + 1);
-    w->V = wc.take<double>((size_t)l * l);
-    w->gcv = wc.take<double>(J);
-    w->xr = wc.take<double>(J);
-    w->ye = wc.take<double>(J);
-    w->cvec = wc.take<double>(l + 2);
-    w->y = wc.take<double>(l + 2);
-    w->work = wc.take<double>(l + 2);
-    w->svd = (void*)wc.take<char>(svd_ws_bytes(l));
-    return RBF_OK;
-}
 
 rbf_status read_info(rbf_ctx* ctx, rbf_solve_info* info, int l) {
     RBF_CUDA(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(rbf_dev_state),
@@ -252,6 +322,19 @@ rbf_status read_info(rbf_ctx* ctx, rbf_solve_info* info, int l) {
     return RBF_OK;
 }
 
+rbf_status single_solve(rbf_ctx* ctx, const rbf_gkb_state* st, int method, int rule, double lambda_in, int rank,
+                        double* d_coef, double* d_curve, rbf_solve_info* info) {
+    const int l = st->steps_done;
+    if (l < 1) return rbf_fail(ctx, RBF_ERR_INVALID, "state has no completed step");
+    if (l > 1023) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "projected dimension above 1023");
+    RBF_TRY(rbf_ws_reserve(ctx, select_ws_bytes_batch(ctx, l, 1)));
+    ProjDims d{1, l, l, nullptr};
+    LiftDims ld{nullptr, nullptr, nullptr, st->n, st->ldz, st->n};
+    RBF_TRY(launch_select_batch(ctx, d, method, rule, lambda_in, rank, st->d_alpha, st->d_beta, st->d_Z, ld,
+                                d_coef, d_curve, ctx->ws, nullptr, nullptr, nullptr, true));
+    return read_info(ctx, info, l);
+}
+
 }  // namespace
 
 extern "C" rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in,
@@ -262,31 +345,7 @@ extern "C" rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, d
         return rbf_fail(ctx, RBF_ERR_INVALID, "unknown rule %d", rule);
     if (rule == RBF_FIXED && !(lambda_in >= 0.0))
         return rbf_fail(ctx, RBF_ERR_INVALID, "fixed lambda must be >= 0");
-    const int l = st->steps_done;
-    ProjWs w;
-    RBF_TRY(proj_prepare(ctx, st, &w));
-    cudaStream_t s = ctx->stream;
-    const int J = ctx->opt.grid_j;
-    const double tlo = ctx->opt.grid_t_lo, thi = ctx->opt.grid_t_hi;
-    rbf_timer_start(ctx);
-    RBF_TRY(launch_projected_svd(ctx, st->d_alpha, st->d_beta, l, w.sigma, w.ftil, w.V, l, w.svd));
-    ctx->tim.svd_ms = rbf_timer_stop(ctx);
-    rbf_timer_start(ctx);
-    if (rule != RBF_FIXED) {
-        k_grid_terms<<<(J + 31) / 32, 32, 0, s>>>(w.sigma, w.ftil, l, J, tlo, thi, w.gcv, w.xr, w.ye);
-        RBF_LAUNCHED(ctx, "k_grid_terms");
-    }
-    k_choose_lambda<<<1, 1024, 0, s>>>(w.sigma, w.ftil, l, J, tlo, thi, rule, lambda_in, w.gcv, w.xr,
-                                       w.ye, d_curve, w.cvec, ctx->d_state);
-    RBF_LAUNCHED(ctx, "k_choose_lambda");
-    k_vmul<<<(l + 127) / 128, 128, 0, s>>>(w.V, l, l, w.cvec, w.y);
-    RBF_LAUNCHED(ctx, "k_vmul");
-    ctx->tim.select_ms = rbf_timer_stop(ctx);
-    rbf_timer_start(ctx);
-    k_lift<<<(unsigned)((st->n + 31) / 32), 128, 0, s>>>(st->d_Z, st->ldz, st->n, l, w.y, d_coef);
-    RBF_LAUNCHED(ctx, "k_lift");
-    ctx->tim.lift_ms = rbf_timer_stop(ctx);
-    return read_info(ctx, info, l);
+    return single_solve(ctx, st, 0, rule, lambda_in, 0, d_coef, d_curve, info);
 }
 
 extern "C" rbf_status rbf_ine_tsvd(rbf_ctx* ctx, const rbf_gkb_state* st, int rank, double* d_coef,
@@ -295,21 +354,5 @@ extern "C" rbf_status rbf_ine_tsvd(rbf_ctx* ctx, const rbf_gkb_state* st, int ra
     if (!st || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_ine_tsvd: NULL argument");
     const int l = st->steps_done;
     if (rank < 0 || rank > l) return rbf_fail(ctx, RBF_ERR_INVALID, "rank %d outside [0, l=%d]", rank, l);
-    ProjWs w;
-    RBF_TRY(proj_prepare(ctx, st, &w));
-    cudaStream_t s = ctx->stream;
-    rbf_timer_start(ctx);
-    RBF_TRY(launch_projected_svd(ctx, st->d_alpha, st->d_beta, l, w.sigma, w.ftil, w.V, l, w.svd));
-    ctx->tim.svd_ms = rbf_timer_stop(ctx);
-    rbf_timer_start(ctx);
-    k_choose_rank<<<1, 256, 0, s>>>(w.sigma, w.ftil, l, rank, d_curve, w.cvec, w.work, ctx->d_state);
-    RBF_LAUNCHED(ctx, "k_choose_rank");
-    k_vmul<<<(l + 127) / 128, 128, 0, s>>>(w.V, l, l, w.cvec, w.y);
-    RBF_LAUNCHED(ctx, "k_vmul");
-    ctx->tim.select_ms = rbf_timer_stop(ctx);
-    rbf_timer_start(ctx);
-    k_lift<<<(unsigned)((st->n + 31) / 32), 128, 0, s>>>(st->d_Z, st->ldz, st->n, l, w.y, d_coef);
-    RBF_LAUNCHED(ctx, "k_lift");
-    ctx->tim.lift_ms = rbf_timer_stop(ctx);
-    return read_info(ctx, info, l);
+    return single_solve(ctx, st, 1, RBF_GCV, 0.0, rank, d_coef, d_curve, info);
 }

@@ -33,6 +33,8 @@ namespace {
 
 constexpr int BS_WARPS = 4;
 
+__device__ __forceinline__ int proj_l(const ProjDims& d, int b) { return d.l_arr ? d.l_arr[b] : d.l; }
+
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }
 
@@ -94,16 +96,23 @@ __device__ int sturm_count(const double* __restrict__ e2, int nt, double x) {
     return neg;
 }
 
-__global__ void k_tgk_bisect(const double* __restrict__ alpha, const double* __restrict__ beta, int l,
-                             double* __restrict__ sigma, double* __restrict__ bound_out) {
+__global__ void k_tgk_bisect(ProjDims d, const double* __restrict__ alpha_all,
+                             const double* __restrict__ beta_all, double* __restrict__ sigma_all,
+                             double* __restrict__ bound_all) {
     extern __shared__ double sh[];
+    const int b = blockIdx.y;
+    const int l = proj_l(d, b);
+    if (l < 1) return;
+    const double* alpha = alpha_all + (size_t)b * d.L;
+    const double* beta = beta_all + (size_t)b * (d.L + 1);
+    double* sigma = sigma_all + (size_t)b * d.L;
     double* e = sh;           // 2l
     double* e2 = sh + 2 * l;  // 2l
     double bound;
     load_e(alpha, beta, l, e, &bound);
     for (int k = threadIdx.x; k < 2 * l; k += blockDim.x) e2[k] = e[k] * e[k];
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) *bound_out = bound;
+    if (blockIdx.x == 0 && threadIdx.x == 0) bound_all[b] = bound;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * BS_WARPS + warp;  // descending index
     if (i >= l) return;
@@ -111,10 +120,10 @@ __global__ void k_tgk_bisect(const double* __restrict__ alpha, const double* __r
     const int nt = 2 * l + 1;
     long long lo = 0, hi = dbits(1.0 + 1.0 / 1024.0);
     for (int round = 0; round < 24 && hi - lo > 1; ++round) {
-        const long long d = hi - lo;
+        const long long dd = hi - lo;
         long long xb;
-        if (d >= 33) xb = lo + (d / 33) * (lane + 1);
-        else xb = lo + min((long long)(lane + 1), d - 1);
+        if (dd >= 33) xb = lo + (dd / 33) * (lane + 1);
+        else xb = lo + min((long long)(lane + 1), dd - 1);
         const int cnt = sturm_count(e2, nt, bitsd(xb)) - (l + 1);
         const unsigned above = __ballot_sync(RBF_FULL_MASK, cnt > m);
         const long long x_prev = __shfl_up_sync(RBF_FULL_MASK, xb, 1);
@@ -132,54 +141,64 @@ __global__ void k_tgk_bisect(const double* __restrict__ alpha, const double* __r
 }
 
 // Twisted factorization eigenvector of the normalised T for s = sigma_i / bound.
-// Scratch (k-major, stride l): invdp[k][i] = 1/d+_k, rp[k][i] = e_k / d+_k,
-// rm[k][i] = e_{k-1} / d-_k.  Output X[i * nt + k].
-__global__ void k_tgk_vectors(const double* __restrict__ alpha, const double* __restrict__ beta, int l,
-                              const double* __restrict__ sigma, const double* __restrict__ bound_p,
-                              double* __restrict__ invdp, double* __restrict__ rp,
-                              double* __restrict__ rm, double* __restrict__ X) {
+// Scratch per instance (k-major, stride L): invdp[k][i] = 1/d+_k,
+// rp[k][i] = e_k / d+_k, rm[k][i] = e_{k-1} / d-_k.  Output X[i * NT + k].
+__global__ void k_tgk_vectors(ProjDims d, const double* __restrict__ alpha_all,
+                              const double* __restrict__ beta_all, const double* __restrict__ sigma_all,
+                              const double* __restrict__ bound_all, double* __restrict__ invdp_all,
+                              double* __restrict__ rp_all, double* __restrict__ rm_all,
+                              double* __restrict__ X_all) {
     extern __shared__ double e[];
+    const int b = blockIdx.y;
+    const int l = proj_l(d, b);
+    if (l < 1) return;
+    const int L = d.L, NT = 2 * d.L + 1;
+    const size_t sc = (size_t)b * NT * L;
+    double* invdp = invdp_all + sc;
+    double* rp = rp_all + sc;
+    double* rm = rm_all + sc;
+    double* X = X_all + sc;
     double bound;
-    load_e(alpha, beta, l, e, &bound);
+    load_e(alpha_all + (size_t)b * L, beta_all + (size_t)b * (L + 1), l, e, &bound);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= l) return;
     const int nt = 2 * l + 1;
-    const double s = sigma[i] / bound;
+    const double s = sigma_all[(size_t)b * L + i] / bound;
     const double pivmin = -DBL_MIN;
     // top-down: d+_0 = -s, d+_k = -s - e_{k-1} rp_{k-1}
-    double d = -s;
+    double dd = -s;
     for (int k = 0; k < nt; ++k) {
-        if (k > 0) d = fma(-e[k - 1], rp[(size_t)(k - 1) * l + i], -s);
-        if (d == 0.0) d = pivmin;
-        const double inv = 1.0 / d;
-        invdp[(size_t)k * l + i] = inv;
-        if (k < nt - 1) rp[(size_t)k * l + i] = e[k] * inv;
-        X[(size_t)i * nt + k] = d;  // keep d+ for gamma
+        if (k > 0) dd = fma(-e[k - 1], rp[(size_t)(k - 1) * L + i], -s);
+        if (dd == 0.0) dd = pivmin;
+        const double inv = 1.0 / dd;
+        invdp[(size_t)k * L + i] = inv;
+        if (k < nt - 1) rp[(size_t)k * L + i] = e[k] * inv;
+        X[(size_t)i * NT + k] = dd;  // keep d+ for gamma
     }
     // bottom-up: d-_{nt-1} = -s, d-_k = -s - e_k rm_{k+1}; gamma_k = d+_k + d-_k + s
     double dm = -s;
     double best = 1e308;
     int r = nt - 1;
     for (int k = nt - 1; k >= 0; --k) {
-        if (k < nt - 1) dm = fma(-e[k], rm[(size_t)(k + 1) * l + i], -s);
+        if (k < nt - 1) dm = fma(-e[k], rm[(size_t)(k + 1) * L + i], -s);
         if (dm == 0.0) dm = pivmin;
-        if (k > 0) rm[(size_t)k * l + i] = e[k - 1] / dm;
-        const double g = fabs(X[(size_t)i * nt + k] + dm + s);
-        if (g < best) {
-            best = g;
+        if (k > 0) rm[(size_t)k * L + i] = e[k - 1] / dm;
+        const double gm = fabs(X[(size_t)i * NT + k] + dm + s);
+        if (gm < best) {
+            best = gm;
             r = k;
         }
     }
     // x_r = 1; upward x_k = -rp_k x_{k+1}; downward x_k = -rm_k x_{k-1}
-    double* x = X + (size_t)i * nt;
+    double* x = X + (size_t)i * NT;
     x[r] = 1.0;
     double nrm2 = 1.0;
     for (int k = r - 1; k >= 0; --k) {
-        x[k] = -rp[(size_t)k * l + i] * x[k + 1];
+        x[k] = -rp[(size_t)k * L + i] * x[k + 1];
         nrm2 = fma(x[k], x[k], nrm2);
     }
     for (int k = r + 1; k < nt; ++k) {
-        x[k] = -rm[(size_t)k * l + i] * x[k - 1];
+        x[k] = -rm[(size_t)k * L + i] * x[k - 1];
         nrm2 = fma(x[k], x[k], nrm2);
     }
     const double inv = rsqrt(nrm2);
@@ -188,15 +207,25 @@ __global__ void k_tgk_vectors(const double* __restrict__ alpha, const double* __
 
 // Clusters of close singular values: inverse iteration (3 steps) with the
 // stored LDL^T factors of T - s_a I, all members in parallel lanes, then
-// modified Gram-Schmidt in order.  One warp per cluster.
+// modified Gram-Schmidt in order.  One block per instance, one warp per cluster.
 constexpr int CL_WARPS = 8;
 constexpr int CL_MAX = 32;
 
-__global__ void k_tgk_clusters(const double* __restrict__ sigma, int l, double tol,
-                               const double* __restrict__ invdp, const double* __restrict__ rp,
-                               double* __restrict__ X, double* __restrict__ tmp /* [CL_WARPS][32][nt] */) {
+__global__ void k_tgk_clusters(ProjDims d, const double* __restrict__ sigma_all, double tol,
+                               const double* __restrict__ invdp_all, const double* __restrict__ rp_all,
+                               double* __restrict__ X_all, double* __restrict__ tmp_all) {
     __shared__ int cl_start[512], cl_end[512];
     __shared__ int ncl;
+    const int b = blockIdx.x;
+    const int l = proj_l(d, b);
+    if (l < 1) return;
+    const int L = d.L, NT = 2 * d.L + 1;
+    const size_t sc = (size_t)b * NT * L;
+    const double* sigma = sigma_all + (size_t)b * L;
+    const double* invdp = invdp_all + sc;
+    const double* rp = rp_all + sc;
+    double* X = X_all + sc;
+    double* tmp = tmp_all + (size_t)b * CL_WARPS * CL_MAX * NT;
     if (threadIdx.x == 0) {
         int c = 0;
         int i = 0;
@@ -215,29 +244,29 @@ __global__ void k_tgk_clusters(const double* __restrict__ sigma, int l, double t
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nt = 2 * l + 1;
-    double* y = tmp + (size_t)warp * CL_MAX * nt;  // member vectors of this warp's cluster
+    double* y = tmp + (size_t)warp * CL_MAX * NT;  // member vectors of this warp's cluster
     for (int c = warp; c < ncl; c += CL_WARPS) {
         const int a0 = cl_start[c], a1 = cl_end[c];
         const int mcnt = a1 - a0 + 1;
         // deterministic start vectors
         for (int a = 0; a < mcnt; ++a)
-            for (int k = lane; k < nt; k += 32) y[(size_t)a * nt + k] = sin(0.7 * (double)(k + 1) * (a + 1) + 0.3);
+            for (int k = lane; k < nt; k += 32) y[(size_t)a * NT + k] = sin(0.7 * (double)(k + 1) * (a + 1) + 0.3);
         __syncwarp();
         for (int it = 0; it < 3; ++it) {
             // lane a solves (T - s_a I) x = y_a:  L D L^T with L_{k+1,k} = rp_k
             if (lane < mcnt) {
                 const int ia = a0 + lane;
-                double* v = y + (size_t)lane * nt;
-                for (int k = 1; k < nt; ++k) v[k] = fma(-rp[(size_t)(k - 1) * l + ia], v[k - 1], v[k]);
-                for (int k = 0; k < nt; ++k) v[k] *= invdp[(size_t)k * l + ia];
-                for (int k = nt - 2; k >= 0; --k) v[k] = fma(-rp[(size_t)k * l + ia], v[k + 1], v[k]);
+                double* v = y + (size_t)lane * NT;
+                for (int k = 1; k < nt; ++k) v[k] = fma(-rp[(size_t)(k - 1) * L + ia], v[k - 1], v[k]);
+                for (int k = 0; k < nt; ++k) v[k] *= invdp[(size_t)k * L + ia];
+                for (int k = nt - 2; k >= 0; --k) v[k] = fma(-rp[(size_t)k * L + ia], v[k + 1], v[k]);
             }
             __syncwarp();
             // modified Gram-Schmidt in member order
             for (int a = 0; a < mcnt; ++a) {
-                double* va = y + (size_t)a * nt;
-                for (int b = 0; b < a; ++b) {
-                    const double* vb = y + (size_t)b * nt;
+                double* va = y + (size_t)a * NT;
+                for (int bb = 0; bb < a; ++bb) {
+                    const double* vb = y + (size_t)bb * NT;
                     double dot = 0.0;
                     for (int k = lane; k < nt; k += 32) dot = fma(vb[k], va[k], dot);
                     dot = warp_sum(dot);
@@ -253,23 +282,33 @@ __global__ void k_tgk_clusters(const double* __restrict__ sigma, int l, double t
             }
         }
         for (int a = 0; a < mcnt; ++a)
-            for (int k = lane; k < nt; k += 32) X[(size_t)(a0 + a) * nt + k] = y[(size_t)a * nt + k];
+            for (int k = lane; k < nt; k += 32) X[(size_t)(a0 + a) * NT + k] = y[(size_t)a * NT + k];
         __syncwarp();
     }
 }
 
-// Split the eigenvectors into u~, v~ (normalised), write V~ and f~.
-__global__ void k_tgk_finalize(const double* __restrict__ alpha, const double* __restrict__ beta, int l,
-                               const double* __restrict__ X, double* __restrict__ ftil,
-                               double* __restrict__ V, int64_t ldv, rbf_dev_state* __restrict__ stt,
-                               const double* __restrict__ sigma) {
+// Split the eigenvectors into u~, v~ (normalised), write V~ and f~.  One block per instance.
+__global__ void k_tgk_finalize(ProjDims d, const double* __restrict__ alpha_all,
+                               const double* __restrict__ beta_all, const double* __restrict__ X_all,
+                               double* __restrict__ ftil_all, double* __restrict__ V_all, int64_t ldv,
+                               rbf_dev_state* __restrict__ stt, const double* __restrict__ sigma_all,
+                               double* __restrict__ sigma1_out, double* __restrict__ ftil_last_out) {
     __shared__ double Ls[1024];
     __shared__ double red[32];
+    const int b = blockIdx.x;
+    const int l = proj_l(d, b);
+    if (l < 1) return;
+    const int L = d.L, NT = 2 * d.L + 1;
+    const double* alpha = alpha_all + (size_t)b * L;
+    const double* beta = beta_all + (size_t)b * (L + 1);
+    const double* X = X_all + (size_t)b * NT * L;
+    double* ftil = ftil_all + (size_t)b * (L + 1);
+    double* V = V_all + (size_t)b * L * ldv;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int nt = 2 * l + 1;
     const double beta1 = beta[0];
     for (int i = warp; i < l; i += nw) {
-        const double* x = X + (size_t)i * nt;
+        const double* x = X + (size_t)i * NT;
         double nu = 0.0, nv = 0.0;
         for (int k = lane; k < nt; k += 32) {
             double t = x[k] * x[k];
@@ -310,45 +349,61 @@ __global__ void k_tgk_finalize(const double* __restrict__ alpha, const double* _
         for (int w = 0; w < nw; ++w) s += red[w];
         double ft = zero_tail ? 0.0 : beta1 * exp(-mx) / sqrt(s);
         ftil[l] = ft;
-        stt->scal[SC_FTIL_LAST] = ft;
-        stt->scal[SC_SIGMA1] = sigma[0];
+        if (sigma1_out) sigma1_out[b] = sigma_all[(size_t)b * L];
+        if (ftil_last_out) ftil_last_out[b] = ft;
+        if (stt && b == 0) {
+            stt->scal[SC_FTIL_LAST] = ft;
+            stt->scal[SC_SIGMA1] = sigma_all[0];
+        }
     }
 }
 
 }  // namespace
 
-size_t svd_ws_bytes(int l) {
-    const size_t nt = 2 * (size_t)l + 1;
+size_t svd_ws_bytes(int l) { return svd_ws_bytes_batch(l, 1); }
+
+size_t svd_ws_bytes_batch(int L, int B) {
+    const size_t NT = 2 * (size_t)L + 1;
     size_t b = 0;
-    b += 4 * ws_align(nt * l * 8);             // X, invdp, rp, rm
-    b += ws_align((size_t)CL_WARPS * CL_MAX * nt * 8);
-    b += ws_align(64);
+    b += 4 * ws_align(NT * L * 8 * B);            // X, invdp, rp, rm
+    b += ws_align((size_t)CL_WARPS * CL_MAX * NT * 8 * B);
+    b += ws_align((size_t)8 * B);
     return b + 4096;
+}
+
+rbf_status launch_projected_svd_batch(rbf_ctx* ctx, ProjDims d, const double* alpha, const double* beta,
+                                      double* sigma, double* ftil, double* V, int64_t ldv, void* ws,
+                                      double* sigma1_out, double* ftil_last_out) {
+    const int L = d.L, B = d.B;
+    if (L < 1 || L > 1023) return rbf_fail(ctx, RBF_ERR_INVALID, "projected dimension %d outside [1, 1023]", L);
+    const size_t NT = 2 * (size_t)L + 1;
+    WsCarve wc(ws);
+    double* X = wc.take<double>(NT * L * B);
+    double* invdp = wc.take<double>(NT * L * B);
+    double* rp = wc.take<double>(NT * L * B);
+    double* rm = wc.take<double>(NT * L * B);
+    double* tmp = wc.take<double>((size_t)CL_WARPS * CL_MAX * NT * B);
+    double* bound = wc.take<double>((size_t)B);
+    cudaStream_t s = ctx->stream;
+    const size_t sh_b = 4 * (size_t)L * sizeof(double);
+    k_tgk_bisect<<<dim3((L + BS_WARPS - 1) / BS_WARPS, B), BS_WARPS * 32, sh_b, s>>>(d, alpha, beta, sigma, bound);
+    RBF_LAUNCHED(ctx, "k_tgk_bisect");
+    const size_t sh_v = 2 * (size_t)L * sizeof(double);
+    k_tgk_vectors<<<dim3((L + 31) / 32, B), 32, sh_v, s>>>(d, alpha, beta, sigma, bound, invdp, rp, rm, X);
+    RBF_LAUNCHED(ctx, "k_tgk_vectors");
+    k_tgk_clusters<<<B, CL_WARPS * 32, 0, s>>>(d, sigma, ctx->opt.cluster_tol, invdp, rp, X, tmp);
+    RBF_LAUNCHED(ctx, "k_tgk_clusters");
+    k_tgk_finalize<<<B, 256, 0, s>>>(d, alpha, beta, X, ftil, V, ldv, B == 1 ? ctx->d_state : nullptr, sigma,
+                                     sigma1_out, ftil_last_out);
+    RBF_LAUNCHED(ctx, "k_tgk_finalize");
+    return RBF_OK;
 }
 
 rbf_status launch_projected_svd(rbf_ctx* ctx, const double* alpha, const double* beta, int l,
                                 double* sigma, double* ftil, double* V, int64_t ldv, void* ws) {
     if (l < 1 || l > 1023) return rbf_fail(ctx, RBF_ERR_INVALID, "projected dimension %d outside [1, 1023]", l);
-    const size_t nt = 2 * (size_t)l + 1;
-    WsCarve wc(ws);
-    double* X = wc.take<double>(nt * l);
-    double* invdp = wc.take<double>(nt * l);
-    double* rp = wc.take<double>(nt * l);
-    double* rm = wc.take<double>(nt * l);
-    double* tmp = wc.take<double>((size_t)CL_WARPS * CL_MAX * nt);
-    double* bound = wc.take<double>(8);
-    cudaStream_t s = ctx->stream;
-    const size_t sh_b = 4 * (size_t)l * sizeof(double);
-    k_tgk_bisect<<<(l + BS_WARPS - 1) / BS_WARPS, BS_WARPS * 32, sh_b, s>>>(alpha, beta, l, sigma, bound);
-    RBF_LAUNCHED(ctx, "k_tgk_bisect");
-    const size_t sh_v = 2 * (size_t)l * sizeof(double);
-    k_tgk_vectors<<<(l + 31) / 32, 32, sh_v, s>>>(alpha, beta, l, sigma, bound, invdp, rp, rm, X);
-    RBF_LAUNCHED(ctx, "k_tgk_vectors");
-    k_tgk_clusters<<<1, CL_WARPS * 32, 0, s>>>(sigma, l, ctx->opt.cluster_tol, invdp, rp, X, tmp);
-    RBF_LAUNCHED(ctx, "k_tgk_clusters");
-    k_tgk_finalize<<<1, 256, 0, s>>>(alpha, beta, l, X, ftil, V, ldv, ctx->d_state, sigma);
-    RBF_LAUNCHED(ctx, "k_tgk_finalize");
-    return RBF_OK;
+    ProjDims d{1, l, l, nullptr};
+    return launch_projected_svd_batch(ctx, d, alpha, beta, sigma, ftil, V, ldv, ws, nullptr, nullptr);
 }
 
 extern "C" rbf_status rbf_projected_svd(rbf_ctx* ctx, const rbf_gkb_state* st, double* d_sigma,

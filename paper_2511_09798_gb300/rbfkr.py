@@ -59,6 +59,19 @@ class Counters(C.Structure):
                 ("product_ms", C.c_double * 2)]
 
 
+class Batch(C.Structure):
+    _fields_ = [("count", C.c_int), ("n", C.POINTER(C.c_int64)), ("n_interior", C.POINTER(C.c_int64)),
+                ("c", C.POINTER(C.c_double)), ("k", C.POINTER(C.c_double)), ("d_nodes", C.c_void_p),
+                ("d_f", C.c_void_p), ("capacity", C.c_int), ("d_W", C.c_void_p), ("d_Z", C.c_void_p),
+                ("d_alpha", C.c_void_p), ("d_beta", C.c_void_p), ("steps_done", C.POINTER(C.c_int)),
+                ("breakdown", C.POINTER(C.c_int))]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("mf_outputs_per_thread", C.c_int), ("mf_threads", C.c_int), ("candidates", C.c_int),
+                ("best_ms", C.c_double), ("graph_kernels", C.c_int)]
+
+
 class Timings(C.Structure):
     _fields_ = [("assemble_ms", C.c_double), ("gkb_ms", C.c_double), ("svd_ms", C.c_double),
                 ("select_ms", C.c_double), ("lift_ms", C.c_double), ("evaluate_ms", C.c_double),
@@ -89,6 +102,11 @@ EXPORTS = {
                                C.c_void_p, C.POINTER(SolveInfo)]),
     "rbf_evaluate": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_void_p, C.c_int64,
                                C.c_void_p]),
+    "rbf_batch_gkb": (C.c_int, [C.c_void_p, C.POINTER(Batch), C.c_int, C.c_int]),
+    "rbf_batch_hkt": (C.c_int, [C.c_void_p, C.POINTER(Batch), C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
+    "rbf_batch_evaluate": (C.c_int, [C.c_void_p, C.POINTER(Batch), C.c_int, C.c_void_p, C.c_void_p,
+                                     C.POINTER(C.c_int64), C.c_void_p]),
+    "rbf_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(Tuning)]),
     "rbf_matvec_t_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
 }
@@ -235,6 +253,24 @@ class Context:
                                           _ptr(coef), C.byref(info)))
         return info
 
+    def rbf_batch_gkb(self, batch, steps, form=RBF_FORM_C):
+        self._check(self.lib.rbf_batch_gkb(self.h, C.byref(batch), steps, form))
+
+    def rbf_batch_hkt(self, batch, rule, coef):
+        lam = (C.c_double * batch.count)()
+        self._check(self.lib.rbf_batch_hkt(self.h, C.byref(batch), rule, _ptr(coef), lam))
+        return list(lam)
+
+    def rbf_batch_evaluate(self, batch, coef, points, m, u, form=RBF_FORM_C):
+        arr = (C.c_int64 * batch.count)(*m)
+        self._check(self.lib.rbf_batch_evaluate(self.h, C.byref(batch), form, _ptr(coef), _ptr(points), arr,
+                                                _ptr(u)))
+
+    def rbf_get_tuning(self):
+        t = Tuning()
+        self._check(self.lib.rbf_get_tuning(self.h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
     def rbf_evaluate(self, op, coef, points, m, u):
         self._check(self.lib.rbf_evaluate(self.h, C.byref(op), _ptr(coef), _ptr(points), m, _ptr(u)))
 
@@ -259,3 +295,42 @@ def make_state(torch, n, capacity, device="cuda"):
 def padded_lda(n, precision):
     """Leading dimension used for assembled matrices: a multiple of 32 elements."""
     return ((n + 31) // 32) * 32
+
+
+def make_batch(torch, node_sets, cs, ks, fs, capacity, device="cuda"):
+    """Concatenate instances into the rbf_batch layout (caller-owned torch buffers).
+
+    node_sets: objects with .X (n x 3 float64) and .n_interior; fs: list of f_b.
+    Returns (Batch, dict of tensors and host arrays); keep the dict alive.
+    """
+    import numpy as np
+    B = len(node_sets)
+    ns = [int(s.X.shape[0]) for s in node_sets]
+    T = int(sum(ns))
+    nodes = np.concatenate([np.ascontiguousarray(s.X.T).ravel() for s in node_sets])
+    f = np.concatenate([np.asarray(x, dtype=np.float64) for x in fs])
+    keep = {
+        "nodes": torch.as_tensor(nodes, dtype=torch.float64, device=device),
+        "f": torch.as_tensor(f, dtype=torch.float64, device=device),
+        "W": torch.zeros((capacity + 1) * T, dtype=torch.float64, device=device),
+        "Z": torch.zeros(capacity * T, dtype=torch.float64, device=device),
+        "alpha": torch.zeros(B * capacity, dtype=torch.float64, device=device),
+        "beta": torch.zeros(B * (capacity + 1), dtype=torch.float64, device=device),
+        "n": (C.c_int64 * B)(*ns),
+        "ni": (C.c_int64 * B)(*[int(s.n_interior) for s in node_sets]),
+        "c": (C.c_double * B)(*[float(x) for x in cs]),
+        "k": (C.c_double * B)(*[float(x) for x in ks]),
+        "steps_done": (C.c_int * B)(),
+        "breakdown": (C.c_int * B)(),
+        "offsets": np.concatenate([[0], np.cumsum(ns)]).astype(np.int64),
+    }
+    bt = Batch()
+    bt.count = B
+    bt.n, bt.n_interior = keep["n"], keep["ni"]
+    bt.c, bt.k = keep["c"], keep["k"]
+    bt.d_nodes, bt.d_f = keep["nodes"].data_ptr(), keep["f"].data_ptr()
+    bt.capacity = capacity
+    bt.d_W, bt.d_Z = keep["W"].data_ptr(), keep["Z"].data_ptr()
+    bt.d_alpha, bt.d_beta = keep["alpha"].data_ptr(), keep["beta"].data_ptr()
+    bt.steps_done, bt.breakdown = keep["steps_done"], keep["breakdown"]
+    return bt, keep
