@@ -65,7 +65,8 @@ typedef enum {
 typedef enum {
     RBF_GCV = 0,     /* argmin of the projected GCV on the lambda grid (eq. gcv_proj) */
     RBF_LCURVE = 1,  /* max discrete curvature of (ln rho_l, ln eta_l) on the grid */
-    RBF_FIXED = 2    /* lambda supplied by the caller */
+    RBF_FIXED = 2,   /* lambda supplied by the caller */
+    RBF_FIXED_T = 3  /* lambda = s~_1 10^t with t = lambda_in supplied by the caller */
 } rbf_rule;
 
 typedef enum {
@@ -130,6 +131,8 @@ typedef struct {
     int rank;        /* truncation rank (Ine-TSVD) */
     int steps;       /* l, the projected dimension used */
     double sigma1;   /* largest Ritz value s~_1 */
+    double eta;      /* |y| = |alpha| (Z_l has orthonormal columns), eq. eta_proj */
+    double rho;      /* projected residual |C_l y - beta_1 e_1|, eq. rho_proj */
 } rbf_solve_info;
 
 /* Per-phase device time of the last calls, milliseconds (timing option). */
@@ -221,10 +224,11 @@ rbf_status rbf_projected_svd(rbf_ctx* ctx, const rbf_gkb_state* st, double* d_si
                              double* d_V, int64_t ldv);
 
 /* Hybrid Krylov-Tikhonov (Algorithm 4): choose lambda by `rule` on the grid
- * lambda = s~_1 10^t (or take lambda_in for RBF_FIXED), solve the projected
- * Tikhonov problem and lift: d_coef[n] = Z_l y_lambda.  d_curve (optional,
- * length J) receives GCV_l on the grid (RBF_GCV) or the curvature (RBF_LCURVE,
- * end points = -inf).  Synchronises; fills *info. */
+ * lambda = s~_1 10^t (or take lambda_in for RBF_FIXED, or s~_1 10^lambda_in
+ * for RBF_FIXED_T), solve the projected Tikhonov problem and lift: d_coef[n] =
+ * Z_l y_lambda.  d_curve (optional, length J) receives GCV_l on the grid
+ * (RBF_GCV) or the curvature (RBF_LCURVE, end points = -inf).  Synchronises;
+ * fills *info (eta and rho at the chosen lambda). */
 rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in,
                    double* d_coef, double* d_curve, rbf_solve_info* info);
 
@@ -306,6 +310,119 @@ rbf_status rbf_batch_evaluate(rbf_ctx* ctx, const rbf_batch* batch, int form, co
 
 /* The autotuner's last choice. */
 rbf_status rbf_get_tuning(const rbf_ctx* ctx, rbf_tuning* out);
+
+/* ---- learned stopping index and lambda -----------------------------------
+ *
+ * The paper stops GKB at a fixed l and picks lambda by GCV or the L-curve
+ * (Sec. 3.2-3.4); its closing discussion leaves cheaper stopping as future
+ * work.  These entry points carry a small regressor that predicts, from the
+ * first 10 GKB steps, the stopping index l and log10 lambda, so that GKB can
+ * end early and the selection sweep is skipped.  The network is not in the
+ * paper: a 20 -> 128 -> 128 -> 2 perceptron with exact (erf) GELU after both
+ * hidden layers, FP32 parameters and arithmetic (gradients accumulated in
+ * FP64).  Parameters are one FP32 vector of RBF_MLP_PARAMS elements laid out
+ * as W1 [20][128] (row-major, input index first), b1 [128], W2 [128][128],
+ * b2 [128], W3 [128][2], b3 [2]; the layer computes h_out = h_in W + b.
+ * Inputs d_x are [batch][20] row-major, outputs and targets [batch][2]. */
+#define RBF_MLP_IN 20
+#define RBF_MLP_HIDDEN 128
+#define RBF_MLP_OUT 2
+#define RBF_MLP_PARAMS (20 * 128 + 128 + 128 * 128 + 128 + 128 * 2 + 2)
+
+/* d_y = network(d_x).  Does not synchronise.  RBF_ERR_INVALID on NULL
+ * pointers or batch < 1. */
+rbf_status rbf_mlp_forward(rbf_ctx* ctx, const float* d_params, const float* d_x, int batch, float* d_y);
+
+/* Gradient of the loss sum_(s,o) (y_so - t_so)^2 / (2 batch) with respect to
+ * the parameters, written to d_grad (RBF_MLP_PARAMS floats, same layout as the
+ * parameters; each element summed over the batch in sample order, so the
+ * result is deterministic).  When h_loss is not NULL the loss is written there
+ * and the stream is synchronised.  Uses the context workspace (about
+ * 4 KiB per sample). */
+rbf_status rbf_mlp_grad(rbf_ctx* ctx, const float* d_params, const float* d_x, const float* d_t, int batch,
+                        float* d_grad, float* h_loss);
+
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8, bias correction for step
+ * t >= 1) of d_params with moments d_m, d_v (RBF_MLP_PARAMS floats each,
+ * zero before step 1). */
+rbf_status rbf_mlp_adam(rbf_ctx* ctx, float* d_params, float* d_m, float* d_v, const float* d_grad, int t,
+                        float lr);
+
+/* rbf_mlp_grad followed by rbf_mlp_adam (d_grad receives the gradient). */
+rbf_status rbf_mlp_train_step(rbf_ctx* ctx, float* d_params, float* d_m, float* d_v, int t, float lr,
+                              const float* d_x, const float* d_t, int batch, float* d_grad, float* h_loss);
+
+/* The 20 network inputs after j (1 <= j <= 10) completed GKB steps of `st`,
+ * from the projected problem C_j (Sec. 3.2): log10 s~_1, log10(s~_i / s~_1)
+ * for i = 2..10, and log10(rho_i / beta_1) for i = 1..10, where rho_i is the
+ * least-squares residual min_y |C_i y - beta_1 e_1| after i steps.  Entries
+ * past j repeat the last available value (singular values: -300); a zero
+ * residual is written as -300.  When d_mean and d_std (20 floats each) are
+ * given the features are standardised, (f - mean) / std.  d_feat receives 20
+ * floats.  Does not synchronise.  RBF_ERR_INVALID when j is out of range or
+ * the state has fewer than j steps. */
+rbf_status rbf_stop_features(rbf_ctx* ctx, const rbf_gkb_state* st, int j, const float* d_mean,
+                             const float* d_std, float* d_feat);
+
+/* Reconstruction (eq. u_reconstruction) for ncoef coefficient vectors at
+ * once: d_u[c][t] = sum_j d_coefs[c][j] Phi(|P_t - X_j|) (times 1/c in the
+ * eps form), FP64, with d_coefs [ncoef][ldc] (ldc >= n), d_points SoA [3][m]
+ * and d_u [ncoef][m].  Used to score many candidate solutions against a known
+ * field (training labels for the learned stop).  Does not synchronise. */
+rbf_status rbf_evaluate_many(rbf_ctx* ctx, const rbf_operator* op, const double* d_coefs, int64_t ldc,
+                             int ncoef, const double* d_points, int64_t m, double* d_u);
+
+/* Error table for labelling: for each l in h_ells (host, n_ell values, each
+ * 1 <= l <= st->steps_done <= 1023) and each lambda of the context grid whose
+ * index is a multiple of t_stride (Jp = (J - 1) / t_stride + 1 values,
+ * lambda = s~_1(l) 10^t), the relative max-norm error
+ * max_t |u_t - uref_t| / max_t |uref_t| of the HKT reconstruction u = G_l y_lambda
+ * (Algorithm 4 step 9 in SVD form, eq. u_reconstruction).  d_G is column-major
+ * m x l_max with ld ldg >= m, column i = Phi(P, X) z_{i+1} (rbf_evaluate_many on
+ * the columns of Z); d_uref [m]; d_err receives [n_ell][Jp] doubles.
+ * Synchronises. */
+rbf_status rbf_hkt_error_table(rbf_ctx* ctx, const rbf_gkb_state* st, const double* d_G, int64_t ldg,
+                               int64_t m, const double* d_uref, int n_ell, const int* h_ells, int t_stride,
+                               double* d_err);
+
+/* A trained stop network and the rules around it (all host fields). */
+typedef struct {
+    const float* d_params;     /* RBF_MLP_PARAMS floats (device) */
+    const float* d_feat_mean;  /* 20 floats (device) or NULL: feature standardisation */
+    const float* d_feat_std;   /* 20 floats (device) or NULL */
+    float out_mean[2];         /* outputs are standardised ln l and t = log10(lambda / s~_1): */
+    float out_std[2];          /*   value = output * out_std + out_mean */
+    int feat_steps;            /* GKB steps before the prediction, 1..10 */
+    int l_min, l_max;          /* predicted l is clamped to [l_min, l_max]; l_max is the fallback's l */
+    int window;                /* acceptance: eta at t compared with l - window steps ... */
+    double accept_tol;         /* ... relative change at most accept_tol */
+    double t_min, t_max;       /* acceptance: predicted t must lie in [t_min, t_max] */
+    int fallback_rule;         /* RBF_GCV or RBF_LCURVE */
+    double z_max;              /* acceptance: every standardised feature within [-z_max, z_max]
+                                  (inputs like the training set's); 0 = no bound */
+} rbf_stopnet;
+
+typedef struct {
+    int l_pred;          /* predicted stopping index after clamping (0 when no prediction was made) */
+    double t_pred;       /* predicted log10(lambda / s~_1) */
+    int accepted;        /* 1: the learned (l, lambda) solution is returned; 0: fallback HKT */
+    int in_distribution; /* 1: finite features within z_max of the training set */
+    double eta_change;   /* |eta_l - eta_{l-window}| / eta_l at t_pred (NaN when accept_tol is inf) */
+    int steps;           /* GKB steps held by the state at return */
+    rbf_solve_info solve;/* the returned projected solve */
+} rbf_learned_info;
+
+/* Learned-stop HKT: GKB for net->feat_steps steps from f, the stop features,
+ * one network forward, GKB resumed to the predicted l (Algorithm 1), then the
+ * projected Tikhonov solve at lambda = s~_1 10^t (Algorithm 4 steps 2-10).
+ * The prediction is accepted when the standardised features lie within
+ * z_max, t lies in [t_min, t_max] and the solution norm eta at that t changed
+ * by at most accept_tol relative over the last `window` steps (a test skipped
+ * when accept_tol is +inf); otherwise GKB
+ * continues to l_max and lambda comes from fallback_rule.  st must hold
+ * capacity >= l_max; d_coef[n] receives Z_l y.  Synchronises; fills *info. */
+rbf_status rbf_learned_hkt(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, const rbf_stopnet* net,
+                           rbf_gkb_state* st, double* d_coef, rbf_learned_info* info);
 
 /* ---- allocation-free product (no counterpart in the paper) ------------- */
 

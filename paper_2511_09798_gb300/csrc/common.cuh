@@ -38,3 +38,12 @@ __device__ __forceinline__ unsigned sign_bit(double v) {
 __device__ __forceinline__ bool gkb_done(const int* done) {
     return done != nullptr && *(volatile const int*)done != 0;
 }
+
+// Lambda grid coordinate t_idx = t_lo + idx * step, step = (t_hi - t_lo) /
+// (J - 1), rounded as two separate operations (no contraction); the last
+// point is exactly t_hi.
+__device__ __forceinline__ double grid_t(int idx, int J, double t_lo, double t_hi) {
+    if (idx == J - 1) return t_hi;
+    const double step = __ddiv_rn(t_hi - t_lo, (double)(J - 1));
+    return __dadd_rn(__dmul_rn((double)idx, step), t_lo);
+}

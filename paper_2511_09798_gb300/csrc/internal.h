@@ -14,6 +14,7 @@
 struct rbf_dev_state {
     int info[8];      // 0 steps_done, 1 breakdown, 2 done flag, 3 error code, 4 cur step
     double scal[16];  // see SC_* below
+    float mlp[64];    // learned stop: features [0, 20), network output [32, 34)
 };
 enum {
     SC_CHAT0 = 0,   // c_hat double buffer slot 0
@@ -25,6 +26,8 @@ enum {
     SC_LAMBDA = 6,  // chosen lambda
     SC_SIGMA1 = 7,
     SC_FTIL_LAST = 8,
+    SC_ETA = 9,     // |y| of the last projected solve
+    SC_RHO = 10,    // projected residual of the last projected solve
 };
 enum { IN_STEPS = 0, IN_BREAK = 1, IN_DONE = 2, IN_ERR = 3, IN_INDEX = 4, IN_RANK = 5 };
 
@@ -153,6 +156,10 @@ struct LiftDims {           // lift coef = Z y per instance
     int64_t nmax;           // max n (grid size)
 };
 size_t select_ws_bytes(const rbf_ctx* ctx, int l);
+// Single-instance HKT (rule incl. RBF_FIXED_T) on the first st->steps_done
+// steps; d_coef may be NULL (no lift: only *info, with eta and rho).
+rbf_status hkt_single(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in, double* d_coef,
+                      rbf_solve_info* info, double* d_curve = nullptr);
 size_t select_ws_bytes_batch(const rbf_ctx* ctx, int L, int B);
 // method 0: HKT with `rule`; 1: Ine-TSVD with `rank` (0 = GCV).
 rbf_status launch_select_batch(rbf_ctx* ctx, ProjDims d, int method, int rule, double lambda_in, int rank,

@@ -21,14 +21,6 @@
 
 namespace {
 
-// t_idx = t_lo + idx * step with step = (t_hi - t_lo) / (J - 1) rounded as two
-// separate operations (no contraction), and the last point exactly t_hi.
-__device__ __forceinline__ double grid_t(int idx, int J, double t_lo, double t_hi) {
-    if (idx == J - 1) return t_hi;
-    const double step = __ddiv_rn(t_hi - t_lo, (double)(J - 1));
-    return __dadd_rn(__dmul_rn((double)idx, step), t_lo);
-}
-
 __device__ __forceinline__ int sel_l(const ProjDims& d, int b) { return d.l_arr ? d.l_arr[b] : d.l; }
 
 __global__ void k_grid_terms(ProjDims d, const double* __restrict__ sigma_all, const double* __restrict__ ftil_all,
@@ -58,8 +50,10 @@ __global__ void k_grid_terms(ProjDims d, const double* __restrict__ sigma_all, c
     ye_all[(size_t)b * J + t] = 0.5 * log(eta2);
 }
 
-// Choose lambda (rule 0 GCV, 1 L-curve, 2 fixed) and form the coefficient
-// vector cvec_i = s_i f_i / (s_i^2 + lambda^2).  One block per instance.
+// Choose lambda (rule 0 GCV, 1 L-curve, 2 fixed, 3 fixed t: lambda = s~_1
+// 10^lambda_in) and form the coefficient vector cvec_i = s_i f_i / (s_i^2 +
+// lambda^2); eta = |cvec| and rho (eq. rho_proj) at that lambda go to the
+// state (instance 0).  One block per instance.
 __global__ void k_choose_lambda(ProjDims d, const double* __restrict__ sigma_all,
                                 const double* __restrict__ ftil_all, int J, double t_lo, double t_hi,
                                 int rule, double lambda_in, const double* __restrict__ gcv_all,
@@ -68,6 +62,7 @@ __global__ void k_choose_lambda(ProjDims d, const double* __restrict__ sigma_all
                                 double* __restrict__ lam_out, int* __restrict__ idx_out,
                                 rbf_dev_state* __restrict__ stt) {
     __shared__ double bv[1024];
+    __shared__ double gcv_red[1024];
     __shared__ int bi[1024];
     __shared__ double lam_s;
     const int b = blockIdx.x;
@@ -84,7 +79,7 @@ __global__ void k_choose_lambda(ProjDims d, const double* __restrict__ sigma_all
     // per-thread best over a strided subset, then a tree with lowest-index tie-break
     double best = rule == 1 ? -INFINITY : INFINITY;
     int besti = 0x7fffffff;
-    if (rule != 2) {
+    if (rule < 2) {
         for (int t = threadIdx.x; t < J; t += blockDim.x) {
             double v;
             if (rule == 0) {
@@ -132,6 +127,9 @@ __global__ void k_choose_lambda(ProjDims d, const double* __restrict__ sigma_all
         if (rule == 2) {
             lam = lambda_in;
             idx = -1;
+        } else if (rule == 3) {
+            lam = sigma[0] * exp10(lambda_in);
+            idx = -1;
         } else {
             idx = bi[0];
             if (idx < 0 || idx >= J) idx = 0;
@@ -148,9 +146,32 @@ __global__ void k_choose_lambda(ProjDims d, const double* __restrict__ sigma_all
     }
     __syncthreads();
     const double lam2 = lam_s * lam_s;
+    double e2 = 0.0, r2 = 0.0;
     for (int i = threadIdx.x; i < l; i += blockDim.x) {
         const double s = sigma[i];
-        cvec[i] = s * ftil[i] / fma(s, s, lam2);
+        const double inv = 1.0 / fma(s, s, lam2);
+        const double cv = s * ftil[i] * inv;
+        const double q = lam2 * inv * ftil[i];
+        cvec[i] = cv;
+        e2 = fma(cv, cv, e2);
+        r2 = fma(q, q, r2);
+    }
+    if (stt && b == 0) {
+        __syncthreads();
+        bv[threadIdx.x] = e2;
+        gcv_red[threadIdx.x] = r2;
+        __syncthreads();
+        for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+            if ((int)threadIdx.x < off) {
+                bv[threadIdx.x] += bv[threadIdx.x + off];
+                gcv_red[threadIdx.x] += gcv_red[threadIdx.x + off];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            stt->scal[SC_ETA] = sqrt(bv[0]);
+            stt->scal[SC_RHO] = sqrt(fma(ftil[l], ftil[l], gcv_red[0]));
+        }
     }
 }
 
@@ -197,8 +218,19 @@ __global__ void k_choose_rank(ProjDims d, const double* __restrict__ sigma_all,
         k_s = k;
         if (rank_out) rank_out[b] = k;
         if (stt && b == 0) {
+            double e2 = 0.0, r2 = ftil[l] * ftil[l];
+            for (int i = 0; i < l; ++i) {
+                if (i < k) {
+                    const double cv = ftil[i] / sigma[i];
+                    e2 = fma(cv, cv, e2);
+                } else {
+                    r2 = fma(ftil[i], ftil[i], r2);
+                }
+            }
             stt->info[IN_RANK] = k;
             stt->scal[SC_SIGMA1] = s1;
+            stt->scal[SC_ETA] = sqrt(e2);
+            stt->scal[SC_RHO] = sqrt(r2);
         }
     }
     __syncthreads();
@@ -274,7 +306,7 @@ rbf_status launch_select_batch(rbf_ctx* ctx, ProjDims d, int method, int rule, d
     ctx->tim.svd_ms = rbf_timer_stop(ctx);
     rbf_timer_start(ctx);
     if (method == 0) {
-        if (rule != RBF_FIXED) {
+        if (rule == RBF_GCV || rule == RBF_LCURVE) {
             k_grid_terms<<<dim3((J + 31) / 32, B), 32, 0, s>>>(d, sigma, ftil, J, tlo, thi, gcv, xr, ye);
             RBF_LAUNCHED(ctx, "k_grid_terms");
         }
@@ -290,8 +322,10 @@ rbf_status launch_select_batch(rbf_ctx* ctx, ProjDims d, int method, int rule, d
     ctx->tim.select_ms = rbf_timer_stop(ctx);
     rbf_timer_start(ctx);
     const int64_t nmax = ld.nmax;
-    k_lift<<<dim3((unsigned)((nmax + 31) / 32), B), 128, 0, s>>>(d, Z, ld, y, coef);
-    RBF_LAUNCHED(ctx, "k_lift");
+    if (coef) {
+        k_lift<<<dim3((unsigned)((nmax + 31) / 32), B), 128, 0, s>>>(d, Z, ld, y, coef);
+        RBF_LAUNCHED(ctx, "k_lift");
+    }
     ctx->tim.lift_ms = rbf_timer_stop(ctx);
     return RBF_OK;
 }
@@ -318,6 +352,8 @@ rbf_status read_info(rbf_ctx* ctx, rbf_solve_info* info, int l) {
         info->rank = ctx->h_state->info[IN_RANK];
         info->steps = l;
         info->sigma1 = ctx->h_state->scal[SC_SIGMA1];
+        info->eta = ctx->h_state->scal[SC_ETA];
+        info->rho = ctx->h_state->scal[SC_RHO];
     }
     return RBF_OK;
 }
@@ -341,10 +377,17 @@ extern "C" rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, d
                               double* d_coef, double* d_curve, rbf_solve_info* info) {
     if (!ctx) return RBF_ERR_INVALID;
     if (!st || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_hkt: NULL argument");
-    if (rule != RBF_GCV && rule != RBF_LCURVE && rule != RBF_FIXED)
+    return hkt_single(ctx, st, rule, lambda_in, d_coef, info, d_curve);
+}
+
+rbf_status hkt_single(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in, double* d_coef,
+                      rbf_solve_info* info, double* d_curve) {
+    if (rule != RBF_GCV && rule != RBF_LCURVE && rule != RBF_FIXED && rule != RBF_FIXED_T)
         return rbf_fail(ctx, RBF_ERR_INVALID, "unknown rule %d", rule);
     if (rule == RBF_FIXED && !(lambda_in >= 0.0))
         return rbf_fail(ctx, RBF_ERR_INVALID, "fixed lambda must be >= 0");
+    if (rule == RBF_FIXED_T && !(lambda_in >= -300.0 && lambda_in <= 300.0))
+        return rbf_fail(ctx, RBF_ERR_INVALID, "fixed t must be finite and within [-300, 300]");
     return single_solve(ctx, st, 0, rule, lambda_in, 0, d_coef, d_curve, info);
 }
 

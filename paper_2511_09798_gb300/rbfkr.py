@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "librbfkr.so")
 RBF_OK, RBF_ERR_INVALID, RBF_ERR_OOM, RBF_ERR_CUDA, RBF_ERR_TIMEOUT, RBF_ERR_UNSUPPORTED, RBF_ERR_INTERNAL = range(7)
 RBF_FP64, RBF_MIXED = 0, 1
 RBF_ASSEMBLED, RBF_MATRIX_FREE = 0, 1
-RBF_GCV, RBF_LCURVE, RBF_FIXED = 0, 1, 2
+RBF_GCV, RBF_LCURVE, RBF_FIXED, RBF_FIXED_T = 0, 1, 2, 3
 RBF_FORM_C, RBF_FORM_EPS = 0, 1
 
 STATUS_NAMES = {0: "RBF_OK", 1: "RBF_ERR_INVALID", 2: "RBF_ERR_OOM", 3: "RBF_ERR_CUDA",
@@ -51,7 +51,12 @@ class GkbState(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("index", C.c_int), ("rank", C.c_int), ("steps", C.c_int),
-                ("sigma1", C.c_double)]
+                ("sigma1", C.c_double), ("eta", C.c_double), ("rho", C.c_double)]
+
+
+class LearnedInfo(C.Structure):
+    _fields_ = [("l_pred", C.c_int), ("t_pred", C.c_double), ("accepted", C.c_int), ("in_distribution", C.c_int),
+                ("eta_change", C.c_double), ("steps", C.c_int), ("solve", SolveInfo)]
 
 
 class Counters(C.Structure):
@@ -70,6 +75,14 @@ class Batch(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("mf_outputs_per_thread", C.c_int), ("mf_threads", C.c_int), ("candidates", C.c_int),
                 ("best_ms", C.c_double), ("graph_kernels", C.c_int)]
+
+
+class StopNet(C.Structure):
+    _fields_ = [("d_params", C.c_void_p), ("d_feat_mean", C.c_void_p), ("d_feat_std", C.c_void_p),
+                ("out_mean", C.c_float * 2), ("out_std", C.c_float * 2), ("feat_steps", C.c_int),
+                ("l_min", C.c_int), ("l_max", C.c_int), ("window", C.c_int), ("accept_tol", C.c_double),
+                ("t_min", C.c_double), ("t_max", C.c_double), ("fallback_rule", C.c_int),
+                ("z_max", C.c_double)]
 
 
 class Timings(C.Structure):
@@ -107,9 +120,27 @@ EXPORTS = {
     "rbf_batch_evaluate": (C.c_int, [C.c_void_p, C.POINTER(Batch), C.c_int, C.c_void_p, C.c_void_p,
                                      C.POINTER(C.c_int64), C.c_void_p]),
     "rbf_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(Tuning)]),
+    "rbf_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "rbf_mlp_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                               C.POINTER(C.c_float)]),
+    "rbf_mlp_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                               C.c_float]),
+    "rbf_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_float,
+                                     C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_float)]),
+    "rbf_stop_features": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_int, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "rbf_evaluate_many": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_int64, C.c_int,
+                                    C.c_void_p, C.c_int64, C.c_void_p]),
+    "rbf_hkt_error_table": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_void_p, C.c_int64, C.c_int64,
+                                      C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p]),
+    "rbf_learned_hkt": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.POINTER(StopNet),
+                                  C.POINTER(GkbState), C.c_void_p, C.c_void_p]),
     "rbf_matvec_t_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
 }
+
+RBF_MLP_IN, RBF_MLP_HIDDEN, RBF_MLP_OUT = 20, 128, 2
+RBF_MLP_PARAMS = 20 * 128 + 128 + 128 * 128 + 128 + 128 * 2 + 2
 
 RBF_NOALLOC_SCRATCH_DOUBLES = 1 << 20
 
@@ -166,6 +197,9 @@ class Context:
         for k, v in opts.items():
             setattr(o, k, v)
         o.timing = int(timing)
+        self.grid_j = o.grid_j if o.grid_j >= 3 else 321
+        self.grid_t_lo, self.grid_t_hi = ((o.grid_t_lo, o.grid_t_hi) if o.grid_t_lo < o.grid_t_hi
+                                          else (-16.0, 0.0))
         h = C.c_void_p()
         s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         st = self.lib.rbf_create(C.byref(h), device, s, C.byref(o))
@@ -273,6 +307,44 @@ class Context:
 
     def rbf_evaluate(self, op, coef, points, m, u):
         self._check(self.lib.rbf_evaluate(self.h, C.byref(op), _ptr(coef), _ptr(points), m, _ptr(u)))
+
+    # --- learned stopping index and lambda --------------------------------
+    def rbf_mlp_forward(self, params, x, batch, y):
+        self._check(self.lib.rbf_mlp_forward(self.h, _ptr(params), _ptr(x), batch, _ptr(y)))
+
+    def rbf_mlp_grad(self, params, x, t, batch, grad, want_loss=True):
+        loss = C.c_float(0.0)
+        self._check(self.lib.rbf_mlp_grad(self.h, _ptr(params), _ptr(x), _ptr(t), batch, _ptr(grad),
+                                          C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def rbf_mlp_adam(self, params, m, v, grad, t, lr):
+        self._check(self.lib.rbf_mlp_adam(self.h, _ptr(params), _ptr(m), _ptr(v), _ptr(grad), t, float(lr)))
+
+    def rbf_mlp_train_step(self, params, m, v, t, lr, x, target, batch, grad, want_loss=False):
+        loss = C.c_float(0.0)
+        self._check(self.lib.rbf_mlp_train_step(self.h, _ptr(params), _ptr(m), _ptr(v), t, float(lr), _ptr(x),
+                                                _ptr(target), batch, _ptr(grad),
+                                                C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def rbf_stop_features(self, state, j, feat, mean=None, std=None):
+        self._check(self.lib.rbf_stop_features(self.h, C.byref(state), j, _ptr(mean), _ptr(std), _ptr(feat)))
+
+    def rbf_hkt_error_table(self, state, G, ldg, m, uref, ells, t_stride, err):
+        arr = (C.c_int * len(ells))(*[int(x) for x in ells])
+        self._check(self.lib.rbf_hkt_error_table(self.h, C.byref(state), _ptr(G), ldg, m, _ptr(uref), len(ells),
+                                                 arr, t_stride, _ptr(err)))
+
+    def rbf_learned_hkt(self, op, f, net, state, coef):
+        info = LearnedInfo()
+        self._check(self.lib.rbf_learned_hkt(self.h, C.byref(op), _ptr(f), C.byref(net), C.byref(state),
+                                             _ptr(coef), C.byref(info)))
+        return info
+
+    def rbf_evaluate_many(self, op, coefs, ldc, ncoef, points, m, u):
+        self._check(self.lib.rbf_evaluate_many(self.h, C.byref(op), _ptr(coefs), ldc, ncoef, _ptr(points), m,
+                                               _ptr(u)))
 
 
 def make_state(torch, n, capacity, device="cuda"):

@@ -1,0 +1,51 @@
+"""GPU: what the trained stop network gains over the method without it.
+
+A small network is trained on the GPU (the library's forward, backward and
+Adam kernels) on GKB runs the method generates, then compared on held-out
+runs with GCV-driven HKT at the full step count -- the fallback and the judge
+of its error -- and with L-curve HKT.  The learned stop must use fewer GKB
+steps and less time, with an error no worse than GCV-HKT's on most runs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as w
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_09798_gb300 import rbfkr
+    return rbfkr
+
+
+def test_learned_stop_beats_gcv_hkt(R):
+    from paper_2511_09798_gb300 import learned, train_stopnet
+    ctx = R.Context(0)
+    try:
+        L = 60
+        ells = list(range(10, L + 1, 10))
+        tr = w.stop_instances(640, 400, 1200, seed0=w.nodes.BASE_SEED + 700)
+        F, E = train_stopnet.generate(ctx, torch, tr, L, ells, m=300)
+        tgrid = learned.grid_t(ctx.grid_j, ctx.grid_t_lo, ctx.grid_t_hi, 4)
+        Y = learned.make_labels(E, ells, tgrid, 0.25)
+        net, losses = learned.train(ctx, torch, F, Y, steps=3000, lr=1e-3, batch=256, log_every=1000,
+                                    l_min=10, l_max=L, window=5, accept_tol=math.inf, t_min=-16.0, t_max=0.0,
+                                    fallback_rule=R.RBF_GCV, z_max=6.0)
+        assert losses[-1][1] < 0.6 * losses[0][1] or losses[-1][1] < 0.2, losses
+        ev = w.stop_instances(40, 400, 1200, seed0=w.nodes.BASE_SEED + 60000)
+        rows = train_stopnet.evaluate(ctx, torch, net, ev, L, m=300)
+        s = train_stopnet.summarize(rows)
+        print(s)
+        assert s["learned_steps_mean"] <= 0.75 * L
+        assert s["time_ratio_vs_gcv_mean"] < 0.9
+        assert s["err_ratio_vs_gcv_median"] <= 1.0
+        assert s["err_not_worse_than_gcv_frac"] >= 0.7
+    finally:
+        ctx.close()

@@ -13,6 +13,7 @@ from .nodes import (  # noqa: F401
     cube_faces_random,
     pump_like,
     batch_instances,
+    stop_instances,
     test_points,
     scrambled_halton,
     fibonacci_sphere,
@@ -25,4 +26,6 @@ from .problem import (  # noqa: F401
     gaussian,
     gaussian_source,
     gaussian_rhs,
+    instance_rhs,
+    instance_field,
 )

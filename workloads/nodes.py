@@ -378,6 +378,45 @@ def batch_instances(count: int = 96, n_lo: int = 2000, n_hi: int = 16000,
     return out
 
 
+def stop_instances(count: int, n_lo: int, n_hi: int, seed0: int = BASE_SEED + 600,
+                   gauss_share: float = 0.5):
+    """Training / evaluation runs for the learned stopping index.
+
+    Node sets and (c, k) are drawn like the batched sweep (cube or sphere,
+    N ~ U{n_lo..n_hi}, c log-uniform in [0.05, 1], k ~ U[1, 20]).  The exact
+    solution is a plane wave sin(k d.X) with d uniform on S^2, or, with
+    probability gauss_share, the Gaussian exp(-|X - X0|^2 / sigma) of the
+    paper's examples with sigma log-uniform in [0.05, 1] and X0 uniform in the
+    middle half of the domain.  params: c, k, seed, rhs ('plane' | 'gauss'),
+    d or (sigma, center).
+    """
+    out = []
+    for b in range(count):
+        rng = _rng(seed0 + b)
+        is_cube = rng.uniform() < 0.5
+        n = int(rng.integers(n_lo, n_hi + 1))
+        c = float(math.exp(rng.uniform(math.log(0.05), math.log(1.0))))
+        k = float(rng.uniform(1.0, 20.0))
+        if is_cube:
+            ns = cube_faces_random(n, 0.30, rng)
+            center = rng.uniform(0.25, 0.75, 3)
+        else:
+            nb = int(round(0.20 * n))
+            I = uniform_ball(n - nb, rng)
+            ns = NodeSet(np.ascontiguousarray(np.concatenate([I, fibonacci_sphere(nb)])),
+                         n - nb, "sphere", f"sphere{n}")
+            center = uniform_ball(1, rng, 0.5)[0]
+        if rng.uniform() < gauss_share:
+            sigma = float(math.exp(rng.uniform(math.log(0.05), math.log(1.0))))
+            ns.params = dict(c=c, k=k, seed=seed0 + b, rhs="gauss", sigma=sigma, center=center)
+        else:
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            ns.params = dict(c=c, k=k, seed=seed0 + b, rhs="plane", d=d)
+        out.append(ns)
+    return out
+
+
 # ----------------------------------------------------------------------------
 # named workload presets
 # ----------------------------------------------------------------------------

@@ -41,3 +41,20 @@ def gaussian_rhs(nodes, sigma: float, k: float, center=(0.0, 0.0, 0.0)) -> np.nd
     ni = nodes.n_interior
     return np.concatenate([gaussian_source(nodes.X[:ni], sigma, k, center),
                            gaussian(nodes.X[ni:], sigma, center)])
+
+
+def instance_rhs(nodes) -> np.ndarray:
+    """f for a node set whose params name its exact solution (see
+    nodes.stop_instances): 'plane' (d) or 'gauss' (sigma, center)."""
+    p = nodes.params
+    if p.get("rhs", "plane") == "gauss":
+        return gaussian_rhs(nodes, p["sigma"], p["k"], p["center"])
+    return plane_wave_rhs(nodes, p["k"], p.get("d", DIAG))
+
+
+def instance_field(nodes, P: np.ndarray) -> np.ndarray:
+    """The exact solution of that instance at the points P."""
+    p = nodes.params
+    if p.get("rhs", "plane") == "gauss":
+        return gaussian(P, p["sigma"], p["center"])
+    return plane_wave(P, p["k"], p.get("d", DIAG))
