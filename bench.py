@@ -317,9 +317,21 @@ def run_batch(args, rank, world, local_rank):
     P = torch.as_tensor(np.concatenate([p.T.ravel() for p in pts]), device=dev)
     u = torch.empty(m * len(inst), dtype=torch.float64, device=dev)
 
-    def one():
-        ctx.rbf_batch_gkb(bt, L)
-        lam = ctx.rbf_batch_hkt(bt, R.RBF_GCV, coef)
+    learned_arm = args.workload == "batch96-learned"
+    snet = None
+    if learned_arm:
+        from paper_2511_09798_gb300 import learned
+        net = learned.StopNet.load(torch, os.path.join(ROOT, "paper_2511_09798_gb300", "stopnet_weights.npz"),
+                                   device=dev)
+        snet = net.c_struct()
+
+    def one(use_learned=learned_arm):
+        if use_learned:
+            infos = ctx.rbf_batch_learned_hkt(bt, snet, coef)
+            lam = [x.solve.lambda_ for x in infos]
+        else:
+            ctx.rbf_batch_gkb(bt, L)
+            lam = ctx.rbf_batch_hkt(bt, R.RBF_GCV, coef)
         ctx.rbf_batch_evaluate(bt, coef, P, [m] * len(inst), u)
         return sum(bt.steps_done[b] for b in range(len(inst))), lam
 
@@ -333,34 +345,226 @@ def run_batch(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     steps_total = 0
+    entries = 0  # matrix entries regenerated by the products (the learned arm's first 10 steps included)
     for _ in range(args.steps):
         st, lam = one()
         steps_total += st
+        entries += sum(2 * (bt.steps_done[b] + (10 if learned_arm else 0)) * inst[b].n ** 2
+                       for b in range(len(inst)))
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clocks = sampler.stop() if sampler else None
-    uh = u.cpu().numpy().reshape(len(inst), m)
-    errs = []
-    for b, s_ in enumerate(inst):
-        ue = w.plane_wave(pts[b], s_.params["k"], s_.params["d"])
-        errs.append(float(np.max(np.abs(uh[b] - ue)) / np.max(np.abs(ue))))
+    def errors():
+        uh = u.cpu().numpy().reshape(len(inst), m)
+        out = []
+        for b, s_ in enumerate(inst):
+            ue = w.plane_wave(pts[b], s_.params["k"], s_.params["d"])
+            out.append(float(np.max(np.abs(uh[b] - ue)) / np.max(np.abs(ue))))
+        return out
+
+    errs = errors()
+    mean_steps = steps_total / (len(inst) * args.steps)
     tune = ctx.rbf_get_tuning()
+    other = None
+    if learned_arm:  # the same batch with GCV-HKT at 150 steps, once, for comparison
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record()
+        one(False)
+        g1.record()
+        torch.cuda.synchronize()
+        eg = errors()
+        other = {"gcv_hkt_ms": round(g0.elapsed_time(g1), 2),
+                 "gcv_hkt_re_vs_exact": {"median": float(np.median(eg)), "max": float(np.max(eg))},
+                 "learned_err_not_worse_frac": float(np.mean(np.array(errs) <= 1.05 * np.array(eg)))}
     ctx.close()
     if rank != 0:
         return None
     value = len(inst) * args.steps * world / (ms / 1e3)
-    entries = sum(2 * bt.steps_done[b] * inst[b].n ** 2 for b in range(len(inst))) * args.steps
-    return {"metric": "batched HKT instances/s (96 uneven instances, 150 GKB steps each)", "value": round(value, 3),
+    name = "batch96-learned" if learned_arm else "batch96"
+    return {"metric": ("batched learned-stop HKT instances/s (96 uneven instances, at most 150 GKB steps each)"
+                       if learned_arm else "batched HKT instances/s (96 uneven instances, 150 GKB steps each)"),
+            "value": round(value, 3),
             "unit": "instances/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms / args.steps, 2), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "batch96", "instances": len(inst), "rows_total": T, "gkb_steps": L,
-                       "precision": "mixed", "storage": "matrix_free", "rule": "gcv", "test_points_per_instance": m},
+            "config": {"workload": name, "instances": len(inst), "rows_total": T, "gkb_steps": L,
+                       "precision": "mixed", "storage": "matrix_free",
+                       "rule": "learned (GCV fallback)" if learned_arm else "gcv", "test_points_per_instance": m},
+            "mean_gkb_steps_per_instance": round(mean_steps, 2), "comparison": other,
             "gkb_steps_per_s": round(steps_total / (ms / 1e3), 1),
             "regenerated_entries_per_s": entries / (ms / 1e3),
             "re_vs_exact": {"median": float(np.median(errs)), "max": float(np.max(errs))},
             "tuning": tune, "clocks": clocks}
+
+
+# --------------------------------------------------------------------------- learned stop (pump casing)
+def run_learned(args, rank, world, local_rank):
+    """Pump-casing-like domain, N = 40000 (8000 surface + 32000 interior
+    nodes), c = 0.1, k = 8, u at 2000 points.  The exact solution is the
+    casing example's Gaussian exp(-|X|^2 / 10) (Sec. 5, Example 3); the plane
+    wave along (1,1,1)/sqrt 3 is reported beside it.  One bench step = one
+    learned-stop HKT solve through the C ABI: mixed precision (FP32
+    matrix-free products, FP64 elsewhere), GKB for 10 steps, network forward,
+    GKB resumed to the predicted l (at most 150), projected solve at the
+    predicted lambda (GCV-HKT at 150 steps when rejected), reconstruction.
+    Beside it, timed once per field: the learned stop, mixed GCV-HKT(150), and
+    the plain FP64 assembled HKT(150) with GCV and with the L-curve."""
+    import numpy as np
+    import torch
+
+    import workloads as w
+    from paper_2511_09798_gb300 import learned
+    from paper_2511_09798_gb300 import rbfkr as R
+
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    ns = w.preset("pump40000")
+    c, k, L = ns.params["c"], ns.params["k"], ns.params["steps"]
+    n = ns.n
+    Pn = w.test_points(ns)
+    m = Pn.shape[0]
+    fields = {
+        "gauss_sigma10": (w.gaussian_rhs(ns, 10.0, k), w.gaussian(Pn, 10.0)),
+        "plane_wave": (w.plane_wave_rhs(ns, k), w.plane_wave(Pn, k)),
+    }
+    stream = torch.cuda.current_stream()
+    ctx = R.Context(local_rank, stream=stream, timing=2)
+    net = learned.StopNet.load(torch, os.path.join(ROOT, "paper_2511_09798_gb300", "stopnet_weights.npz"),
+                               device=dev)
+    snet = net.c_struct()
+    f_np, ue = fields["gauss_sigma10"]
+    nodes_h = torch.from_numpy(ns.soa()).pin_memory()
+    pts_h = torch.from_numpy(np.ascontiguousarray(Pn.T)).pin_memory()
+    f_h = torch.from_numpy(f_np).pin_memory()
+    nodes_d, pts_d, f_d = nodes_h.to(dev), pts_h.to(dev), f_h.to(dev)
+    st, *_ = R.make_state(torch, n, L, dev)
+    coef = torch.empty(n, dtype=torch.float64, device=dev)
+    u_d = torch.empty(m, dtype=torch.float64, device=dev)
+    u_h = torch.empty(m, dtype=torch.float64).pin_memory()
+    op = ctx.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, R.RBF_MATRIX_FREE, R.RBF_MIXED)
+    infos = []
+
+    def rel_err(u_exact):
+        return float(np.max(np.abs(u_d.cpu().numpy() - u_exact)) / np.max(np.abs(u_exact)))
+
+    def one_step(f, e2e=False):
+        if e2e:
+            nodes_d.copy_(nodes_h, non_blocking=True)
+            pts_d.copy_(pts_h, non_blocking=True)
+            f_d.copy_(f_h, non_blocking=True)
+        info = ctx.rbf_learned_hkt(op, f, snet, st, coef)
+        ctx.rbf_evaluate(op, coef, pts_d, m, u_d)
+        if e2e:
+            u_h.copy_(u_d, non_blocking=True)
+        infos.append(info)
+        return info.steps
+
+    def timed(k_steps, e2e):
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        done = sum(one_step(f_d, e2e) for _ in range(k_steps))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, done
+
+    for _ in range(args.warmup):
+        one_step(f_d)
+    ctx.rbf_get_counters(reset=True)
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms, done = timed(args.steps, False)
+    clocks = sampler.stop() if sampler else None
+    cnt = ctx.rbf_get_counters(reset=True)
+    err_learned = rel_err(ue)
+    last = infos[-1]
+    ms_e2e, _ = timed(args.steps, True)
+
+    def arm(f, u_exact, prec, storage, rule):
+        A = None
+        lda = 0
+        if storage == R.RBF_ASSEMBLED:
+            lda = R.padded_lda(n, prec)
+            A = torch.empty((n, lda), dtype=torch.float64, device=dev)
+        o = ctx.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, storage, prec, R.RBF_FORM_C, A, lda)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if rule == "learned":
+            info = ctx.rbf_learned_hkt(o, f, snet, st, coef)
+            lam, s1 = info.solve.lambda_, info.solve.sigma1
+        else:
+            if A is not None:
+                ctx.rbf_assemble(o)
+            ctx.rbf_gkb(o, f, L, st)
+            info = ctx.rbf_hkt(st, rule, 0.0, coef)
+            lam, s1 = info.lambda_, info.sigma1
+        ctx.rbf_evaluate(o, coef, pts_d, m, u_d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out = {"ms": round(e0.elapsed_time(e1), 2), "max_err_vs_exact": rel_err(u_exact),
+               "gkb_steps": st.steps_done, "t": float(np.log10(lam / s1)) if lam > 0 and s1 > 0 else None}
+        if rule == "learned":
+            out.update({"accepted": info.accepted, "l_pred": info.l_pred, "t_pred": info.t_pred})
+        del A, o
+        return out
+
+    arms = {}
+    for name, (f_np2, u_ex) in fields.items():
+        f2 = torch.as_tensor(f_np2, device=dev)
+        arms[name] = {"learned_mixed_mf": arm(f2, u_ex, R.RBF_MIXED, R.RBF_MATRIX_FREE, "learned"),
+                      "mixed_mf_gcv_hkt": arm(f2, u_ex, R.RBF_MIXED, R.RBF_MATRIX_FREE, R.RBF_GCV),
+                      "fp64_assembled_gcv_hkt": arm(f2, u_ex, R.RBF_FP64, R.RBF_ASSEMBLED, R.RBF_GCV),
+                      "fp64_assembled_lcurve_hkt": arm(f2, u_ex, R.RBF_FP64, R.RBF_ASSEMBLED, R.RBF_LCURVE)}
+    ctx.close()
+    if rank != 0:
+        return None
+    p_ms, p_cnt = cnt["product_ms"], cnt["product_launches"]
+    avg_ms = (p_ms[0] + p_ms[1]) / max(1, p_cnt[0] + p_cnt[1])
+    ent = n * n / (avg_ms / 1e3)
+    tflops = ent * 12 / 1e12
+    roof = {"bound": "alu", "achieved": round(tflops, 3), "peak": round(FP32_PEAK_TFLOPS, 3), "unit": "TFLOP/s",
+            "frac": round(tflops / FP32_PEAK_TFLOPS, 4), "traffic": None, "entries_per_s": ent,
+            "kernel": "matrix-free FP32 products (p = A z, r = A^T w)", "avg_launch_ms": round(avg_ms, 5),
+            "launches_timed": int(p_cnt[0] + p_cnt[1]), "algorithmic_per_launch": f"{n * n} entries",
+            "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts)"}
+    solves = args.steps * world
+    value = solves / (ms / 1e3)
+    ms_solve = ms / args.steps
+    base = arms["gauss_sigma10"]["fp64_assembled_gcv_hkt"]
+    return {"metric": METRIC, "value": round(value, 3), "unit": "HKT solutions/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_solve, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "pump40000-learned", "n": n, "n_interior": ns.n_interior, "c": c, "k": k,
+                       "exact_solution": "exp(-|X|^2/10)", "l_max": L, "precision": "mixed",
+                       "storage": "matrix_free", "rule": "learned (GCV fallback)", "test_points": m,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (node set and Krylov bases streamed each product)"},
+            "time_to_solution_ms": round(ms_solve, 2),
+            "learned": {"gkb_steps": last.steps, "l_pred": last.l_pred, "t_pred": last.t_pred,
+                        "accepted": last.accepted, "in_distribution": last.in_distribution,
+                        "max_err_vs_exact": err_learned},
+            "comparison_single_runs": arms,
+            "speedup_vs_fp64_gcv_hkt": round(base["ms"] / ms_solve, 2),
+            "roofline": roof,
+            "e2e": {"value": round(solves / (ms_e2e / 1e3), 3), "unit": "HKT solutions/s",
+                    "h2d_bytes_per_step": (nodes_h.numel() + pts_h.numel() + f_h.numel()) * 8,
+                    "d2h_bytes_per_step": u_h.numel() * 8, "ms_per_step": round(ms_e2e / args.steps, 2)},
+            "gpu_launches": int(cnt["launches"]),
+            "cpu_baseline": None,
+            "cpu_baseline_note": "not run for this workload: the oracle would assemble a 12.8 GB FP64 matrix",
+            "clocks": clocks}
 
 
 # --------------------------------------------------------------------------- oracle
@@ -469,8 +673,10 @@ def main():
         torch.distributed.init_process_group("nccl")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
-    elif args.workload == "batch96":
+    elif args.workload in ("batch96", "batch96-learned"):
         out = run_batch(args, rank, world, local_rank)
+    elif args.workload == "pump40000-learned":
+        out = run_learned(args, rank, world, local_rank)
     else:
         out = run_ours(args, rank, world, local_rank)
         if out is not None and not args.no_cpu_baseline:

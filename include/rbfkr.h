@@ -271,6 +271,9 @@ typedef struct {
     double* d_beta;              /* device [B][L+1] */
     int* steps_done;             /* host [B], written by rbf_batch_gkb */
     int* breakdown;              /* host [B], written by rbf_batch_gkb */
+    const int* steps_limit;      /* host [B] or NULL: instance b stops after min(steps, steps_limit[b])
+                                    steps (>= 1), with beta and w of the next step written as after
+                                    a full run of that length */
 } rbf_batch;
 
 /* Autotuner choice for the batched matrix-free product (see rbf_batch_gkb). */
@@ -301,6 +304,13 @@ rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* batch, int steps, int form);
  * SVD, lambda by `rule` (RBF_GCV or RBF_LCURVE) on each instance's grid, solve
  * and lift into d_coef (device, instance b at off_b).  h_lambda: host [B] out. */
 rbf_status rbf_batch_hkt(rbf_ctx* ctx, const rbf_batch* batch, int rule, double* d_coef, double* h_lambda);
+
+/* rbf_batch_hkt with a rule per instance: h_rules[b] in {RBF_GCV, RBF_LCURVE,
+ * RBF_FIXED, RBF_FIXED_T} with h_lambda_in[b] its lambda (RBF_FIXED) or t
+ * (RBF_FIXED_T; ignored by the grid rules).  Host arrays of length B.
+ * Synchronises; h_lambda[b] receives the lambda used. */
+rbf_status rbf_batch_hkt_each(rbf_ctx* ctx, const rbf_batch* batch, const int* h_rules, const double* h_lambda_in,
+                              double* d_coef, double* h_lambda);
 
 /* Reconstruction for every instance: d_u (device, instance b at moff_b =
  * sum_{a<b} m_a) at the m_b points of d_points (device FP64 SoA [3][m_b] at
@@ -423,6 +433,18 @@ typedef struct {
  * capacity >= l_max; d_coef[n] receives Z_l y.  Synchronises; fills *info. */
 rbf_status rbf_learned_hkt(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, const rbf_stopnet* net,
                            rbf_gkb_state* st, double* d_coef, rbf_learned_info* info);
+
+/* Batched learned-stop HKT: one batched GKB run of net->feat_steps steps for
+ * all instances, their stop features and one network forward, then a second
+ * batched run (the first steps recomputed) that stops each instance at its
+ * own step count -- the predicted l when accepted (same tests as
+ * rbf_learned_hkt except the eta test, which is not run), l_max otherwise --
+ * and the projected solves with the predicted t or the fallback rule.  The
+ * batch's steps_limit is ignored.  d_coef as rbf_batch_hkt; h_info [B]
+ * receives each instance's decision (eta_change NaN; solve.lambda and
+ * solve.steps filled).  Synchronises. */
+rbf_status rbf_batch_learned_hkt(rbf_ctx* ctx, rbf_batch* batch, const rbf_stopnet* net, double* d_coef,
+                                 rbf_learned_info* h_info);
 
 /* ---- allocation-free product (no counterpart in the paper) ------------- */
 

@@ -190,7 +190,7 @@ __device__ bool grid_sync_b(rbf_dev_state* __restrict__ stt, unsigned* __restric
 }
 
 // per-instance flags, struct of arrays [6][B]
-enum { BI_STEPS = 0, BI_BREAK = 1, BI_DONE0 = 2, BI_DONE1 = 3 };
+enum { BI_STEPS = 0, BI_BREAK = 1, BI_DONE0 = 2, BI_DONE1 = 3, BI_LIMIT = 4 };
 
 struct HalfBArgs {
     const BInst* inst;
@@ -215,6 +215,7 @@ struct HalfBArgs {
     int* binfo;              // [6][B]
     const int* done_in;      // done flags before this launch
     int* done_out;           // done flags after this launch
+    const int* limit;        // [B] steps per instance (the instance stops after step limit[b])
     double* chat_all;        // [B][2]
     rbf_dev_state* stt;
     unsigned* bar;
@@ -225,7 +226,7 @@ struct HalfBArgs {
 
 __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
     extern __shared__ double dsm[];
-    __shared__ int seg_b[SEGMAX], seg_base[SEGMAX], seg_act[SEGMAX], seg_brk[SEGMAX];
+    __shared__ int seg_b[SEGMAX], seg_base[SEGMAX], seg_act[SEGMAX], seg_brk[SEGMAX], seg_stop[SEGMAX];
     __shared__ int64_t seg_i0[SEGMAX], seg_i1[SEGMAX];
     __shared__ double seg_nrm[SEGMAX], seg_inv[SEGMAX];
     __shared__ int nseg, nrows;
@@ -285,13 +286,16 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
                     brk = nrm <= a.factor * (double)I.n * eps * ch_new ? 2 : 0;
                 }
             }
-            seg_act[sx] = active && !brk;
+            // the instance's step limit: step limit[b] + 1 only finalises beta and w
+            const int stop = active && !brk && a.side == 0 && a.limit && a.j == a.limit[b] + 1;
+            seg_act[sx] = active && !brk && !stop;
             seg_brk[sx] = active ? brk : 0;
+            seg_stop[sx] = stop;
             seg_nrm[sx] = nrm;
             seg_inv[sx] = 1.0 / nrm;
             if ((int)blockIdx.x == I.cfirst) {  // the instance's first CTA writes its scalars
                 if (active && a.side == 0) ch[(a.j + 1) & 1] = ch_new;
-                a.done_out[b] = (!active || brk) ? 1 : 0;
+                a.done_out[b] = (!active || brk || stop) ? 1 : 0;
                 if (active) {
                     if (brk) {
                         a.binfo[BI_STEPS * a.B + b] = a.j - 1;
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
     // ---- R1 per segment: v = (sum of partials) / nrm - nrm u; store q_raw / nrm
     for (int sx = 0; sx < nseg; ++sx) {
         const int b = seg_b[sx];
-        if (!seg_act[sx] && seg_brk[sx] != 2) continue;
+        if (!seg_act[sx] && seg_brk[sx] != 2 && !seg_stop[sx]) continue;
         const BInst I = a.inst[b];
         const int64_t n = I.n;
         double* Wb = a.W_all + (size_t)(L + 1) * I.off;
@@ -324,6 +328,10 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
         for (int64_t i = seg_i0[sx] + threadIdx.x; i < seg_i1[sx]; i += HB_THREADS) {
             if (seg_brk[sx] == 2) {  // w_j = 0 after a beta breakdown
                 bout[i] = 0.0;
+                continue;
+            }
+            if (seg_stop[sx]) {  // last step of a limited instance: w_j only
+                bout[i] = qr[i] * inv;
                 continue;
             }
             double p0 = 0.0, p1 = 0.0;
@@ -550,15 +558,27 @@ struct BatchPlan {
 
 // Tuning and graph state lives in the context (one entry; a new batch shape
 // re-tunes and re-captures).
+constexpr int GRAPH_SLOTS = 4;  // captured step loops kept per context (e.g. a short and a full run)
+
 struct BatchTuneState {
     int64_t key_T = -1;
     int key_B = -1;
     int cand = 1;
     double best_ms = 0.0;
-    int graph_kernels = 0;
-    cudaGraphExec_t exec = nullptr;
-    uint64_t graph_key = 0;
+    int graph_kernels = 0;               // kernels in the graph used last
+    cudaGraphExec_t exec[GRAPH_SLOTS] = {};
+    uint64_t graph_key[GRAPH_SLOTS] = {};
+    int slot_kernels[GRAPH_SLOTS] = {};
+    uint64_t last_use[GRAPH_SLOTS] = {};
+    uint64_t clock = 0;
     cudaStream_t stream = nullptr;
+    void drop_graphs() {
+        for (int i = 0; i < GRAPH_SLOTS; ++i) {
+            if (exec[i]) cudaGraphExecDestroy(exec[i]);
+            exec[i] = nullptr;
+            graph_key[i] = 0;
+        }
+    }
 };
 
 static BatchTuneState& tune_state(rbf_ctx* ctx) {
@@ -569,7 +589,7 @@ static BatchTuneState& tune_state(rbf_ctx* ctx) {
 void rbf_batch_state_free(rbf_ctx* ctx) {
     if (!ctx->batch_state) return;
     BatchTuneState* ts = (BatchTuneState*)ctx->batch_state;
-    if (ts->exec) cudaGraphExecDestroy(ts->exec);
+    ts->drop_graphs();
     if (ts->stream) cudaStreamDestroy(ts->stream);
     delete ts;
     ctx->batch_state = nullptr;
@@ -745,6 +765,8 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
             !(bt->k[b] >= 0))
             return rbf_fail(ctx, RBF_ERR_INVALID, "instance %d: invalid n, n_interior, c or k", b);
         if (steps > bt->n[b]) return rbf_fail(ctx, RBF_ERR_INVALID, "instance %d: steps exceed n", b);
+        if (bt->steps_limit && bt->steps_limit[b] < 1)
+            return rbf_fail(ctx, RBF_ERR_INVALID, "instance %d: steps_limit must be >= 1", b);
     }
     BatchPlan P;
     RBF_TRY(plan_batch(ctx, bt, form, &P));
@@ -764,6 +786,10 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     RBF_CUDA(ctx, cudaMemcpyAsync(w.offs, P.offs.data(), sizeof(int64_t) * (P.B + 1), cudaMemcpyHostToDevice, s));
     RBF_CUDA(ctx, cudaMemsetAsync(w.bar, 0, (size_t)(P.bar_k + 2) * BAR_STRIDE_B * sizeof(unsigned), s));
     RBF_CUDA(ctx, cudaMemsetAsync(w.binfo, 0, sizeof(int) * 6 * P.B, s));
+    std::vector<int> lim((size_t)P.B, steps);
+    if (bt->steps_limit)
+        for (int b = 0; b < P.B; ++b) lim[b] = bt->steps_limit[b] < steps ? bt->steps_limit[b] : steps;
+    RBF_CUDA(ctx, cudaMemcpyAsync(w.binfo + BI_LIMIT * P.B, lim.data(), sizeof(int) * P.B, cudaMemcpyHostToDevice, s));
     rbf_dev_state* dst = ctx->d_state;
     RBF_CUDA(ctx, cudaMemsetAsync(&dst->info[IN_ERR], 0, sizeof(int), s));
 
@@ -792,6 +818,7 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     a.qraw_all = w.vp;
     a.v32_all = w.vp32;
     a.done_in = w.binfo + BI_DONE0 * P.B;
+    a.limit = w.binfo + BI_LIMIT * P.B;
     k_init_batch<<<P.G, HB_THREADS, 0, s>>>(a, bt->d_f, w.vp);
     RBF_LAUNCHED(ctx, "k_init_batch");
 
@@ -829,10 +856,7 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
         ts.key_B = P.B;
         ts.cand = bestc;
         ts.best_ms = best;
-        if (ts.exec) {
-            cudaGraphExecDestroy(ts.exec);
-            ts.exec = nullptr;
-        }
+        ts.drop_graphs();
     }
     const int cand = ts.cand;
     std::vector<MfItem> items = make_items(P, MF_CANDS[cand].ro * MF_CANDS[cand].th);
@@ -880,13 +904,26 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
         return cudaSuccess;
     };
     bool ran = false;
-    if (ts.exec && ts.graph_key == key) {
-        RBF_CUDA(ctx, cudaGraphLaunch(ts.exec, s));
+    int slot = -1;
+    for (int i = 0; i < GRAPH_SLOTS; ++i)
+        if (ts.exec[i] && ts.graph_key[i] == key) slot = i;
+    if (slot >= 0) {
+        ts.last_use[slot] = ++ts.clock;
+        ts.graph_kernels = ts.slot_kernels[slot];
+        RBF_CUDA(ctx, cudaGraphLaunch(ts.exec[slot], s));
         ran = true;
     } else {
-        if (ts.exec) {
-            cudaGraphExecDestroy(ts.exec);
-            ts.exec = nullptr;
+        slot = 0;  // an empty slot, else the least recently used one
+        for (int i = 0; i < GRAPH_SLOTS; ++i) {
+            if (!ts.exec[i]) {
+                slot = i;
+                break;
+            }
+            if (ts.last_use[i] < ts.last_use[slot]) slot = i;
+        }
+        if (ts.exec[slot]) {
+            cudaGraphExecDestroy(ts.exec[slot]);
+            ts.exec[slot] = nullptr;
         }
         cudaGraph_t graph = nullptr;
         int kernels = 0;
@@ -896,16 +933,18 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
             e = cudaStreamEndCapture(s, &graph);
             if (er != cudaSuccess) e = er;
         }
-        if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&ts.exec, graph, 0);
+        if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&ts.exec[slot], graph, 0);
         if (graph) cudaGraphDestroy(graph);
-        if (e == cudaSuccess && ts.exec) {
-            ts.graph_key = key;
+        if (e == cudaSuccess && ts.exec[slot]) {
+            ts.graph_key[slot] = key;
+            ts.slot_kernels[slot] = kernels;
+            ts.last_use[slot] = ++ts.clock;
             ts.graph_kernels = kernels;
-            RBF_CUDA(ctx, cudaGraphLaunch(ts.exec, s));
+            RBF_CUDA(ctx, cudaGraphLaunch(ts.exec[slot], s));
             ran = true;
         } else {
             cudaGetLastError();  // capture unsupported: launch the same sequence directly
-            ts.exec = nullptr;
+            ts.exec[slot] = nullptr;
             ts.graph_kernels = 0;
         }
     }
@@ -940,10 +979,8 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     return RBF_OK;
 }
 
-extern "C" rbf_status rbf_batch_hkt(rbf_ctx* ctx, const rbf_batch* bt, int rule, double* d_coef, double* h_lambda) {
-    if (!ctx) return RBF_ERR_INVALID;
-    if (!bt || !d_coef || !h_lambda || bt->count < 1) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_batch_hkt: NULL argument");
-    if (rule != RBF_GCV && rule != RBF_LCURVE) return rbf_fail(ctx, RBF_ERR_INVALID, "rule must be GCV or L-curve");
+static rbf_status batch_hkt_impl(rbf_ctx* ctx, const rbf_batch* bt, int rule, const int* h_rules,
+                                 const double* h_lambda_in, double* d_coef, double* h_lambda) {
     const int B = bt->count, L = bt->capacity;
     int lmax = 0;
     for (int b = 0; b < B; ++b) lmax = bt->steps_done[b] > lmax ? bt->steps_done[b] : lmax;
@@ -958,25 +995,55 @@ extern "C" rbf_status rbf_batch_hkt(rbf_ctx* ctx, const rbf_batch* bt, int rule,
         nmax = bt->n[b] > nmax ? bt->n[b] : nmax;
     }
     const size_t extra = ws_align(sizeof(int64_t) * 3 * B) + ws_align(sizeof(int) * B) + ws_align(sizeof(double) * B) +
-                         ws_align(sizeof(int) * B);
+                         ws_align(sizeof(int) * B) + ws_align(sizeof(int) * B) + ws_align(sizeof(double) * B);
     RBF_TRY(rbf_ws_reserve(ctx, extra + select_ws_bytes_batch(ctx, L, B)));
     WsCarve wc(ctx->ws);
     int64_t* dtab = wc.take<int64_t>(3 * (size_t)B);
     int* l_arr = wc.take<int>(B);
     double* lam = wc.take<double>(B);
     int* idx = wc.take<int>(B);
+    int* rules = wc.take<int>(B);
+    double* lam_in = wc.take<double>(B);
     void* rest = (void*)wc.take<char>(select_ws_bytes_batch(ctx, L, B));
     cudaStream_t s = ctx->stream;
     RBF_CUDA(ctx, cudaMemcpyAsync(dtab, tab.data(), sizeof(int64_t) * 3 * B, cudaMemcpyHostToDevice, s));
     RBF_CUDA(ctx, cudaMemcpyAsync(l_arr, bt->steps_done, sizeof(int) * B, cudaMemcpyHostToDevice, s));
+    if (h_rules) {
+        RBF_CUDA(ctx, cudaMemcpyAsync(rules, h_rules, sizeof(int) * B, cudaMemcpyHostToDevice, s));
+        RBF_CUDA(ctx, cudaMemcpyAsync(lam_in, h_lambda_in, sizeof(double) * B, cudaMemcpyHostToDevice, s));
+    }
     ProjDims d{B, L, 0, l_arr};
     LiftDims ld{dtab, dtab + B, dtab + 2 * B, 0, 0, nmax};
     RBF_TRY(launch_select_batch(ctx, d, 0, rule, 0.0, 0, bt->d_alpha, bt->d_beta, bt->d_Z, ld, d_coef, nullptr, rest,
-                                lam, idx, nullptr, false));
+                                lam, idx, nullptr, false, h_rules ? rules : nullptr, h_rules ? lam_in : nullptr));
     RBF_CUDA(ctx, cudaMemcpyAsync(h_lambda, lam, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
     RBF_CUDA(ctx, cudaStreamSynchronize(s));
     RBF_CUDA(ctx, cudaGetLastError());
     return RBF_OK;
+}
+
+extern "C" rbf_status rbf_batch_hkt(rbf_ctx* ctx, const rbf_batch* bt, int rule, double* d_coef, double* h_lambda) {
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!bt || !d_coef || !h_lambda || bt->count < 1) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_batch_hkt: NULL argument");
+    if (rule != RBF_GCV && rule != RBF_LCURVE) return rbf_fail(ctx, RBF_ERR_INVALID, "rule must be GCV or L-curve");
+    return batch_hkt_impl(ctx, bt, rule, nullptr, nullptr, d_coef, h_lambda);
+}
+
+extern "C" rbf_status rbf_batch_hkt_each(rbf_ctx* ctx, const rbf_batch* bt, const int* h_rules,
+                                         const double* h_lambda_in, double* d_coef, double* h_lambda) {
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!bt || !h_rules || !h_lambda_in || !d_coef || !h_lambda || bt->count < 1)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_batch_hkt_each: NULL argument");
+    for (int b = 0; b < bt->count; ++b) {
+        const int r = h_rules[b];
+        if (r != RBF_GCV && r != RBF_LCURVE && r != RBF_FIXED && r != RBF_FIXED_T)
+            return rbf_fail(ctx, RBF_ERR_INVALID, "instance %d: unknown rule %d", b, r);
+        if (r == RBF_FIXED && !(h_lambda_in[b] >= 0.0))
+            return rbf_fail(ctx, RBF_ERR_INVALID, "instance %d: fixed lambda must be >= 0", b);
+        if (r == RBF_FIXED_T && !(h_lambda_in[b] >= -300.0 && h_lambda_in[b] <= 300.0))
+            return rbf_fail(ctx, RBF_ERR_INVALID, "instance %d: fixed t must be finite", b);
+    }
+    return batch_hkt_impl(ctx, bt, RBF_GCV, h_rules, h_lambda_in, d_coef, h_lambda);
 }
 
 extern "C" rbf_status rbf_batch_evaluate(rbf_ctx* ctx, const rbf_batch* bt, int form, const double* d_coef,

@@ -161,8 +161,18 @@ size_t select_ws_bytes(const rbf_ctx* ctx, int l);
 rbf_status hkt_single(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in, double* d_coef,
                       rbf_solve_info* info, double* d_curve = nullptr);
 size_t select_ws_bytes_batch(const rbf_ctx* ctx, int L, int B);
-// method 0: HKT with `rule`; 1: Ine-TSVD with `rank` (0 = GCV).
+// method 0: HKT with `rule`; 1: Ine-TSVD with `rank` (0 = GCV).  rule_arr /
+// lam_arr (device [B], optional) give each instance its own HKT rule and
+// lambda_in.
 rbf_status launch_select_batch(rbf_ctx* ctx, ProjDims d, int method, int rule, double lambda_in, int rank,
                                const double* alpha, const double* beta, const double* Z, LiftDims ld,
                                double* coef, double* curve, void* ws, double* lam_out, int* idx_out,
-                               int* rank_out, bool single);
+                               int* rank_out, bool single, const int* rule_arr = nullptr,
+                               const double* lam_arr = nullptr);
+
+// mlp.cu: stop features of B batch instances after j steps (alpha [B][L],
+// beta [B][L+1], sigma [B][L] from the batched projected SVD at l = d_l[b]);
+// feat [B][20], NaN rows for instances with fewer than j steps.
+rbf_status launch_stop_features_batch(rbf_ctx* ctx, const double* alpha, const double* beta, const double* sigma,
+                                      int L, const int* d_l, int B, int j, const float* mean, const float* stdv,
+                                      float* feat);

@@ -15,6 +15,7 @@
 // u(l, lambda) = G_l V~ diag(s~ f~ / (s~^2 + lambda^2)) (Sec. 3.3).
 #include <cfloat>
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -219,5 +220,94 @@ extern "C" rbf_status rbf_learned_hkt(rbf_ctx* ctx, const rbf_operator* op, cons
     }
     out.steps = st->steps_done;
     if (info) *info = out;
+    return RBF_OK;
+}
+
+// Batched learned stop: all instances run feat_steps steps in one batched GKB,
+// their features go through one network forward, and a second batched run
+// advances every instance to its own step count (the predicted l when the
+// prediction is accepted, l_max otherwise; the first feat_steps steps are
+// recomputed there, which keeps each instance's run one uninterrupted GKB).
+// The projected solves then use per-instance rules: the predicted t, or the
+// fallback rule.
+extern "C" rbf_status rbf_batch_learned_hkt(rbf_ctx* ctx, rbf_batch* bt, const rbf_stopnet* net, double* d_coef,
+                                            rbf_learned_info* h_info) {
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!bt || !net || !d_coef || !h_info || !net->d_params || bt->count < 1)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_batch_learned_hkt: NULL argument");
+    const int j0 = net->feat_steps;
+    if (j0 < 1 || j0 > 10 || net->l_min < j0 || net->l_max < net->l_min || net->l_max > bt->capacity)
+        return rbf_fail(ctx, RBF_ERR_INVALID,
+                        "rbf_batch_learned_hkt: need 1 <= feat_steps <= 10 <= l_min <= l_max <= capacity");
+    if (net->fallback_rule != RBF_GCV && net->fallback_rule != RBF_LCURVE)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "fallback rule must be RBF_GCV or RBF_LCURVE");
+    const int B = bt->count, L = bt->capacity;
+    rbf_batch b1 = *bt;
+    b1.steps_limit = nullptr;
+    RBF_TRY(rbf_batch_gkb(ctx, &b1, j0, RBF_FORM_C));
+    // features of every instance from its first j0 steps
+    std::vector<int> larr(B);
+    for (int b = 0; b < B; ++b) larr[b] = bt->steps_done[b] < j0 ? bt->steps_done[b] : j0;
+    const size_t need = ws_align((size_t)B * 4) + ws_align((size_t)B * L * 8) + ws_align((size_t)B * (L + 1) * 8) +
+                        ws_align((size_t)B * L * L * 8) + svd_ws_bytes_batch(L, B) +
+                        ws_align((size_t)B * RBF_MLP_IN * 4) + ws_align((size_t)B * RBF_MLP_OUT * 4);
+    RBF_TRY(rbf_ws_reserve(ctx, need));
+    WsCarve wc(ctx->ws);
+    int* d_l = wc.take<int>(B);
+    double* sigma = wc.take<double>((size_t)B * L);
+    double* ftil = wc.take<double>((size_t)B * (L + 1));
+    double* V = wc.take<double>((size_t)B * L * L);
+    void* svd = (void*)wc.take<char>(svd_ws_bytes_batch(L, B));
+    float* feat = wc.take<float>((size_t)B * RBF_MLP_IN);
+    float* yout = wc.take<float>((size_t)B * RBF_MLP_OUT);
+    RBF_CUDA(ctx, cudaMemcpyAsync(d_l, larr.data(), sizeof(int) * B, cudaMemcpyHostToDevice, ctx->stream));
+    ProjDims d{B, L, 0, d_l};
+    RBF_TRY(launch_projected_svd_batch(ctx, d, bt->d_alpha, bt->d_beta, sigma, ftil, V, L, svd, nullptr, nullptr));
+    RBF_TRY(launch_stop_features_batch(ctx, bt->d_alpha, bt->d_beta, sigma, L, d_l, B, j0, net->d_feat_mean,
+                                       net->d_feat_std, feat));
+    RBF_TRY(rbf_mlp_forward(ctx, net->d_params, feat, B, yout));
+    std::vector<float> hf((size_t)B * RBF_MLP_IN), hy((size_t)B * RBF_MLP_OUT);
+    RBF_CUDA(ctx, cudaMemcpyAsync(hf.data(), feat, hf.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    RBF_CUDA(ctx, cudaMemcpyAsync(hy.data(), yout, hy.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    // per-instance decision
+    std::vector<int> limit(B), rules(B);
+    std::vector<double> lam_in(B, 0.0), lam_out(B, 0.0);
+    int lmax_run = 1;
+    for (int b = 0; b < B; ++b) {
+        rbf_learned_info out{};
+        bool in_dist = larr[b] >= j0;
+        for (int q = 0; q < RBF_MLP_IN && in_dist; ++q) {
+            const float v = hf[(size_t)b * RBF_MLP_IN + q];
+            if (!std::isfinite(v) || (net->z_max > 0.0 && std::fabs((double)v) > net->z_max)) in_dist = false;
+        }
+        const double ln_l = (double)hy[(size_t)b * 2] * net->out_std[0] + net->out_mean[0];
+        const double t = (double)hy[(size_t)b * 2 + 1] * net->out_std[1] + net->out_mean[1];
+        const double lp = std::isfinite(ln_l) ? std::exp(std::fmin(ln_l, 30.0)) : (double)net->l_max;
+        long lr = std::lround(lp);
+        if (lr < net->l_min) lr = net->l_min;
+        if (lr > net->l_max) lr = net->l_max;
+        const bool accept = in_dist && std::isfinite(t) && t >= net->t_min && t <= net->t_max;
+        out.l_pred = larr[b] >= j0 ? (int)lr : 0;
+        out.t_pred = t;
+        out.in_distribution = in_dist ? 1 : 0;
+        out.accepted = accept ? 1 : 0;
+        out.eta_change = NAN;
+        limit[b] = accept ? (int)lr : net->l_max;
+        rules[b] = accept ? RBF_FIXED_T : net->fallback_rule;
+        lam_in[b] = accept ? t : 0.0;
+        lmax_run = limit[b] > lmax_run ? limit[b] : lmax_run;
+        h_info[b] = out;
+    }
+    rbf_batch b2 = *bt;
+    b2.steps_limit = limit.data();
+    RBF_TRY(rbf_batch_gkb(ctx, &b2, lmax_run, RBF_FORM_C));
+    RBF_TRY(rbf_batch_hkt_each(ctx, bt, rules.data(), lam_in.data(), d_coef, lam_out.data()));
+    for (int b = 0; b < B; ++b) {
+        h_info[b].steps = bt->steps_done[b];
+        h_info[b].solve.lambda = lam_out[b];
+        h_info[b].solve.steps = bt->steps_done[b];
+        h_info[b].solve.index = -1;
+    }
     return RBF_OK;
 }

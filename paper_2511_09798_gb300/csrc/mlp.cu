@@ -204,10 +204,9 @@ __global__ void k_sum_parts(const double* __restrict__ parts, int n, double scal
 // least-squares residual after i steps (LSQR): rho_i = beta_1 / |u^(i)| with
 // u the null vector of C_i^T (u_1 = 1, u_{m+1} = -alpha_m u_m / beta_{m+1}).
 // Standardised with (mean, std) when given.
-__global__ void k_stop_features(const double* __restrict__ alpha, const double* __restrict__ beta,
-                                const double* __restrict__ sigma, int j, const float* __restrict__ mean,
-                                const float* __restrict__ stdv, float* __restrict__ feat) {
-    if (threadIdx.x != 0) return;
+__device__ void stop_features_one(const double* __restrict__ alpha, const double* __restrict__ beta,
+                                  const double* __restrict__ sigma, int j, const float* __restrict__ mean,
+                                  const float* __restrict__ stdv, float* __restrict__ feat) {
     double f[RBF_MLP_IN];
     const double s1 = sigma[0];
     f[0] = log10(s1);
@@ -234,6 +233,28 @@ __global__ void k_stop_features(const double* __restrict__ alpha, const double* 
         if (mean && stdv) v = (v - mean[q]) / stdv[q];
         feat[q] = v;
     }
+}
+
+__global__ void k_stop_features(const double* __restrict__ alpha, const double* __restrict__ beta,
+                                const double* __restrict__ sigma, int j, const float* __restrict__ mean,
+                                const float* __restrict__ stdv, float* __restrict__ feat) {
+    if (threadIdx.x == 0) stop_features_one(alpha, beta, sigma, j, mean, stdv, feat);
+}
+
+// Batched: instance b = blockIdx.x with alpha [B][L], beta [B][L+1], sigma
+// [B][L]; instances with fewer than j steps get NaN features.
+__global__ void k_stop_features_batch(const double* __restrict__ alpha, const double* __restrict__ beta,
+                                      const double* __restrict__ sigma, int L, const int* __restrict__ l_arr, int j,
+                                      const float* __restrict__ mean, const float* __restrict__ stdv,
+                                      float* __restrict__ feat) {
+    const int b = blockIdx.x;
+    if (threadIdx.x != 0) return;
+    float* out = feat + (size_t)b * RBF_MLP_IN;
+    if (l_arr[b] < j) {
+        for (int q = 0; q < RBF_MLP_IN; ++q) out[q] = __int_as_float(0x7fc00000);
+        return;
+    }
+    stop_features_one(alpha + (size_t)b * L, beta + (size_t)b * (L + 1), sigma + (size_t)b * L, j, mean, stdv, out);
 }
 
 // u[c][t] = sum_j coef[c][j] Phi(|P_t - X_j|) for 8 coefficient vectors per
@@ -386,6 +407,14 @@ extern "C" rbf_status rbf_stop_features(rbf_ctx* ctx, const rbf_gkb_state* st, i
     RBF_TRY(launch_projected_svd(ctx, st->d_alpha, st->d_beta, j, sigma, ftil, V, j, svd));
     k_stop_features<<<1, 32, 0, ctx->stream>>>(st->d_alpha, st->d_beta, sigma, j, d_mean, d_std, d_feat);
     RBF_LAUNCHED(ctx, "k_stop_features");
+    return RBF_OK;
+}
+
+rbf_status launch_stop_features_batch(rbf_ctx* ctx, const double* alpha, const double* beta, const double* sigma,
+                                      int L, const int* d_l, int B, int j, const float* mean, const float* stdv,
+                                      float* feat) {
+    k_stop_features_batch<<<B, 32, 0, ctx->stream>>>(alpha, beta, sigma, L, d_l, j, mean, stdv, feat);
+    RBF_LAUNCHED(ctx, "k_stop_features_batch");
     return RBF_OK;
 }
 

@@ -56,7 +56,8 @@ __global__ void k_grid_terms(ProjDims d, const double* __restrict__ sigma_all, c
 // state (instance 0).  One block per instance.
 __global__ void k_choose_lambda(ProjDims d, const double* __restrict__ sigma_all,
                                 const double* __restrict__ ftil_all, int J, double t_lo, double t_hi,
-                                int rule, double lambda_in, const double* __restrict__ gcv_all,
+                                int rule0, double lambda0, const int* __restrict__ rule_arr,
+                                const double* __restrict__ lam_arr, const double* __restrict__ gcv_all,
                                 const double* __restrict__ xr_all, const double* __restrict__ ye_all,
                                 double* __restrict__ curve_all, double* __restrict__ cvec_all,
                                 double* __restrict__ lam_out, int* __restrict__ idx_out,
@@ -68,6 +69,8 @@ __global__ void k_choose_lambda(ProjDims d, const double* __restrict__ sigma_all
     const int b = blockIdx.x;
     const int l = sel_l(d, b);
     if (l < 1) return;
+    const int rule = rule_arr ? rule_arr[b] : rule0;  // per-instance rule and lambda_in when given
+    const double lambda_in = lam_arr ? lam_arr[b] : lambda0;
     const double* sigma = sigma_all + (size_t)b * d.L;
     const double* ftil = ftil_all + (size_t)b * (d.L + 1);
     const double* gcv = gcv_all + (size_t)b * J;
@@ -285,7 +288,7 @@ size_t select_ws_bytes(const rbf_ctx* ctx, int l) { return select_ws_bytes_batch
 rbf_status launch_select_batch(rbf_ctx* ctx, ProjDims d, int method, int rule, double lambda_in, int rank,
                                const double* alpha, const double* beta, const double* Z, LiftDims ld,
                                double* coef, double* curve, void* ws, double* lam_out, int* idx_out,
-                               int* rank_out, bool single) {
+                               int* rank_out, bool single, const int* rule_arr, const double* lam_arr) {
     const int L = d.L, B = d.B, J = ctx->opt.grid_j;
     const double tlo = ctx->opt.grid_t_lo, thi = ctx->opt.grid_t_hi;
     WsCarve wc(ws);
@@ -306,12 +309,12 @@ rbf_status launch_select_batch(rbf_ctx* ctx, ProjDims d, int method, int rule, d
     ctx->tim.svd_ms = rbf_timer_stop(ctx);
     rbf_timer_start(ctx);
     if (method == 0) {
-        if (rule == RBF_GCV || rule == RBF_LCURVE) {
+        if (rule == RBF_GCV || rule == RBF_LCURVE || rule_arr) {
             k_grid_terms<<<dim3((J + 31) / 32, B), 32, 0, s>>>(d, sigma, ftil, J, tlo, thi, gcv, xr, ye);
             RBF_LAUNCHED(ctx, "k_grid_terms");
         }
-        k_choose_lambda<<<B, 1024, 0, s>>>(d, sigma, ftil, J, tlo, thi, rule, lambda_in, gcv, xr, ye, curve, cvec,
-                                           lam_out, idx_out, stt);
+        k_choose_lambda<<<B, 1024, 0, s>>>(d, sigma, ftil, J, tlo, thi, rule, lambda_in, rule_arr, lam_arr, gcv, xr,
+                                           ye, curve, cvec, lam_out, idx_out, stt);
         RBF_LAUNCHED(ctx, "k_choose_lambda");
     } else {
         k_choose_rank<<<B, 256, 0, s>>>(d, sigma, ftil, rank, curve, cvec, work, rank_out, stt);

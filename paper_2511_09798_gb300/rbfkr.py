@@ -69,7 +69,7 @@ class Batch(C.Structure):
                 ("c", C.POINTER(C.c_double)), ("k", C.POINTER(C.c_double)), ("d_nodes", C.c_void_p),
                 ("d_f", C.c_void_p), ("capacity", C.c_int), ("d_W", C.c_void_p), ("d_Z", C.c_void_p),
                 ("d_alpha", C.c_void_p), ("d_beta", C.c_void_p), ("steps_done", C.POINTER(C.c_int)),
-                ("breakdown", C.POINTER(C.c_int))]
+                ("breakdown", C.POINTER(C.c_int)), ("steps_limit", C.POINTER(C.c_int))]
 
 
 class Tuning(C.Structure):
@@ -135,6 +135,10 @@ EXPORTS = {
                                       C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_void_p]),
     "rbf_learned_hkt": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.POINTER(StopNet),
                                   C.POINTER(GkbState), C.c_void_p, C.c_void_p]),
+    "rbf_batch_hkt_each": (C.c_int, [C.c_void_p, C.POINTER(Batch), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                     C.c_void_p, C.POINTER(C.c_double)]),
+    "rbf_batch_learned_hkt": (C.c_int, [C.c_void_p, C.POINTER(Batch), C.POINTER(StopNet), C.c_void_p,
+                                        C.c_void_p]),
     "rbf_matvec_t_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
 }
@@ -299,6 +303,19 @@ class Context:
         arr = (C.c_int64 * batch.count)(*m)
         self._check(self.lib.rbf_batch_evaluate(self.h, C.byref(batch), form, _ptr(coef), _ptr(points), arr,
                                                 _ptr(u)))
+
+    def rbf_batch_hkt_each(self, batch, rules, lambda_in, coef):
+        B = batch.count
+        r = (C.c_int * B)(*[int(x) for x in rules])
+        li = (C.c_double * B)(*[float(x) for x in lambda_in])
+        lam = (C.c_double * B)()
+        self._check(self.lib.rbf_batch_hkt_each(self.h, C.byref(batch), r, li, _ptr(coef), lam))
+        return list(lam)
+
+    def rbf_batch_learned_hkt(self, batch, net, coef):
+        infos = (LearnedInfo * batch.count)()
+        self._check(self.lib.rbf_batch_learned_hkt(self.h, C.byref(batch), C.byref(net), _ptr(coef), infos))
+        return list(infos)
 
     def rbf_get_tuning(self):
         t = Tuning()

@@ -161,3 +161,90 @@ def test_batch_evaluate_matches_single(ctx, R):
         got = u[moff:moff + ms[b]].cpu().numpy()
         assert np.max(np.abs(got - ref) / (np.abs(ref) + 1e-300)) < 1e-9 or np.allclose(got, ref, rtol=1e-10, atol=1e-10)
         moff += ms[b]
+
+
+def test_batch_step_limits_match_unlimited_runs(ctx, R):
+    sets, cs, ks, fs = _instances()
+    L = 30
+    bt, keep = R.make_batch(torch, sets, cs, ks, fs, L)
+    ctx.rbf_batch_gkb(bt, L)
+    ref = {k: keep[k].clone() for k in ("alpha", "beta", "W", "Z")}
+    done_ref = [bt.steps_done[b] for b in range(len(sets))]
+    lim = [5, 30, 12, 1, 29, 17]
+    arr = (R.C.c_int * len(sets))(*lim)
+    bt.steps_limit = arr
+    for k in ("alpha", "beta", "W", "Z"):
+        keep[k].zero_()
+    ctx.rbf_batch_gkb(bt, L)
+    off = keep["offsets"]
+    for b, ns in enumerate(sets):
+        l = min(lim[b], done_ref[b])
+        assert bt.steps_done[b] == l, (b, bt.steps_done[b], l)
+        a0, a1 = b * L, b * L + l
+        assert torch.equal(keep["alpha"][a0:a1], ref["alpha"][a0:a1])
+        assert torch.equal(keep["beta"][b * (L + 1):b * (L + 1) + l + 1], ref["beta"][b * (L + 1):b * (L + 1) + l + 1])
+        n = ns.n
+        w0 = (L + 1) * int(off[b])
+        assert torch.equal(keep["W"][w0:w0 + (l + 1) * n], ref["W"][w0:w0 + (l + 1) * n])
+        z0 = L * int(off[b])
+        assert torch.equal(keep["Z"][z0:z0 + l * n], ref["Z"][z0:z0 + l * n])
+    bt.steps_limit = None
+
+
+def test_batch_hkt_each_matches_uniform_and_single(ctx, R):
+    sets, cs, ks, fs = _instances()
+    L = 25
+    bt, keep = R.make_batch(torch, sets, cs, ks, fs, L)
+    ctx.rbf_batch_gkb(bt, L)
+    T = int(keep["offsets"][-1])
+    coef_g = torch.empty(T, dtype=torch.float64, device="cuda")
+    lam_g = ctx.rbf_batch_hkt(bt, R.RBF_GCV, coef_g)
+    rules = [R.RBF_GCV, R.RBF_FIXED_T, R.RBF_LCURVE, R.RBF_GCV, R.RBF_FIXED, R.RBF_FIXED_T]
+    lam_in = [0.0, -7.5, 0.0, 0.0, 1e-6, -3.0]
+    coef = torch.empty(T, dtype=torch.float64, device="cuda")
+    lam = ctx.rbf_batch_hkt_each(bt, rules, lam_in, coef)
+    for b, ns in enumerate(sets):
+        o0, o1 = int(keep["offsets"][b]), int(keep["offsets"][b + 1])
+        st = _state_view(R, keep, bt, b, L)
+        c1 = torch.empty(ns.n, dtype=torch.float64, device="cuda")
+        if rules[b] == R.RBF_GCV:
+            assert lam[b] == lam_g[b] and torch.equal(coef[o0:o1], coef_g[o0:o1])
+        info = ctx.rbf_hkt(st, rules[b], lam_in[b], c1)
+        assert lam[b] == info.lambda_
+        assert torch.equal(coef[o0:o1], c1)
+
+
+def test_batch_learned_hkt_decisions(ctx, R):
+    import math
+    from paper_2511_09798_gb300 import learned
+    sets, cs, ks, fs = _instances()
+    L = 40
+    p = learned.init_params(9)
+    p[19200:19458] = 0.0  # output = last bias = 0 -> prediction = out_mean
+    T = None
+    # accepted: every instance stops at l = 20 and solves at t = -7
+    net = learned.StopNet(torch, p, np.zeros(20), np.ones(20), [math.log(20), -7.0], [1.0, 1.0],
+                          l_min=10, l_max=L, z_max=0.0)
+    bt, keep = R.make_batch(torch, sets, cs, ks, fs, L)
+    T = int(keep["offsets"][-1])
+    coef = torch.empty(T, dtype=torch.float64, device="cuda")
+    infos = ctx.rbf_batch_learned_hkt(bt, net.c_struct(), coef)
+    bt2, keep2 = R.make_batch(torch, sets, cs, ks, fs, L)
+    ctx.rbf_batch_gkb(bt2, 20)
+    coef2 = torch.empty(T, dtype=torch.float64, device="cuda")
+    lam2 = ctx.rbf_batch_hkt_each(bt2, [R.RBF_FIXED_T] * len(sets), [-7.0] * len(sets), coef2)
+    for b in range(len(sets)):
+        assert infos[b].accepted == 1 and infos[b].l_pred == 20
+        assert bt.steps_done[b] == bt2.steps_done[b] == min(20, bt2.steps_done[b])
+        assert infos[b].solve.lambda_ == lam2[b]
+    assert torch.equal(coef, coef2)
+    # rejected (t outside the accepted range): GCV-HKT at l_max for all
+    net_r = learned.StopNet(torch, p, np.zeros(20), np.ones(20), [math.log(20), 2.0], [1.0, 1.0],
+                            l_min=10, l_max=L, z_max=0.0)
+    infos = ctx.rbf_batch_learned_hkt(bt, net_r.c_struct(), coef)
+    ctx.rbf_batch_gkb(bt2, L)
+    lam_g = ctx.rbf_batch_hkt(bt2, R.RBF_GCV, coef2)
+    for b in range(len(sets)):
+        assert infos[b].accepted == 0 and bt.steps_done[b] == bt2.steps_done[b]
+        assert infos[b].solve.lambda_ == lam_g[b]
+    assert torch.equal(coef, coef2)

@@ -386,8 +386,8 @@ def stop_instances(count: int, n_lo: int, n_hi: int, seed0: int = BASE_SEED + 60
     N ~ U{n_lo..n_hi}, c log-uniform in [0.05, 1], k ~ U[1, 20]).  The exact
     solution is a plane wave sin(k d.X) with d uniform on S^2, or, with
     probability gauss_share, the Gaussian exp(-|X - X0|^2 / sigma) of the
-    paper's examples with sigma log-uniform in [0.05, 1] and X0 uniform in the
-    middle half of the domain.  params: c, k, seed, rhs ('plane' | 'gauss'),
+    paper's examples with sigma log-uniform in [0.05, 10] (the casing example
+    uses sigma = 10) and X0 uniform in the middle half of the domain.  params: c, k, seed, rhs ('plane' | 'gauss'),
     d or (sigma, center).
     """
     out = []
@@ -407,7 +407,7 @@ def stop_instances(count: int, n_lo: int, n_hi: int, seed0: int = BASE_SEED + 60
                          n - nb, "sphere", f"sphere{n}")
             center = uniform_ball(1, rng, 0.5)[0]
         if rng.uniform() < gauss_share:
-            sigma = float(math.exp(rng.uniform(math.log(0.05), math.log(1.0))))
+            sigma = float(math.exp(rng.uniform(math.log(0.05), math.log(10.0))))
             ns.params = dict(c=c, k=k, seed=seed0 + b, rhs="gauss", sigma=sigma, center=center)
         else:
             d = rng.normal(size=3)
