@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "mf_core.cuh"
 
 namespace {
 
@@ -53,11 +54,6 @@ constexpr int SEGMAX = 16;       // instances intersecting one slab
 constexpr int UPD_ROWS_B = 64;
 constexpr int UPD_GROUPS_B = HB_THREADS / UPD_ROWS_B;
 
-__device__ __forceinline__ float rsqrt_approx_b(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // ---------------------------------------------------------------------------
 // Batched matrix-free product (same arithmetic as the single-instance kernel).
@@ -67,7 +63,8 @@ __global__ void __launch_bounds__(TH) k_mf_batch(const MfItem* __restrict__ item
                                                  const double* __restrict__ nodes_all,
                                                  const float* __restrict__ x32_all, double* __restrict__ part_all,
                                                  const int* __restrict__ done) {
-    __shared__ float4 tile[MF_SB];
+    constexpr int NP = RO / 2;
+    __shared__ MfNode tile[MF_SB];
     const MfItem it = items[blockIdx.x];
     if (done && done[it.b]) return;
     const BInst I = inst[it.b];
@@ -76,66 +73,76 @@ __global__ void __launch_bounds__(TH) k_mf_batch(const MfItem* __restrict__ item
     const float* __restrict__ x32 = x32_all + I.off;
     const float c2 = I.c2, k2 = I.k2;
     const int64_t obase = (int64_t)it.tile * (TH * RO);
-    float ox[RO], oy[RO], oz[RO], a2[RO], a1[RO], a0[RO];
+    f2_t OX[NP], OY[NP], OZ[NP], A0[NP], A1[NP], A2[NP];
     double acc[RO];
 #pragma unroll
-    for (int r = 0; r < RO; ++r) {
-        const int64_t o = obase + threadIdx.x + r * TH;
-        const bool ok = o < n;
-        ox[r] = ok ? (float)X[o] : 0.f;
-        oy[r] = ok ? (float)X[n + o] : 0.f;
-        oz[r] = ok ? (float)X[2 * n + o] : 0.f;
-        const bool interior = TRANS == 0 && o < ni;
-        a2[r] = interior ? k2 : 1.f;
-        a1[r] = interior ? 2.f : 0.f;
-        a0[r] = interior ? c2 : 0.f;
-        acc[r] = 0.0;
+    for (int p = 0; p < NP; ++p) {
+        float cx[2], cy[2], cz[2], e0[2], e1[2], e2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t o = obase + threadIdx.x + (2 * p + h) * TH;
+            const bool ok = o < n;
+            cx[h] = ok ? (float)X[o] : 0.f;
+            cy[h] = ok ? (float)X[n + o] : 0.f;
+            cz[h] = ok ? (float)X[2 * n + o] : 0.f;
+            const bool interior = TRANS == 0 && o < ni;
+            e0[h] = interior ? c2 : 0.f;
+            e1[h] = interior ? 2.f : 0.f;
+            e2[h] = interior ? k2 : 1.f;
+        }
+        OX[p] = f2_pack(cx[0], cx[1]);
+        OY[p] = f2_pack(cy[0], cy[1]);
+        OZ[p] = f2_pack(cz[0], cz[1]);
+        A0[p] = f2_pack(e0[0], e0[1]);
+        A1[p] = f2_pack(e1[0], e1[1]);
+        A2[p] = f2_pack(e2[0], e2[1]);
+        acc[2 * p] = acc[2 * p + 1] = 0.0;
     }
+    const f2_t C2 = f2_pack(c2, c2);
     const int64_t s0 = (int64_t)it.chunk * I.chunk_len;
     const int64_t s1 = min(n, s0 + I.chunk_len);
     for (int seg = 0; seg < (TRANS ? 2 : 1); ++seg) {
         int64_t lo = s0, hi = s1;
-        float b2 = 0.f, b1 = 0.f, b0 = 0.f;
+        bool bnd = obase >= ni;  // trans = 0: every output row is a Dirichlet row
         if (TRANS) {
-            if (seg == 0) { hi = min(s1, ni); b2 = k2; b1 = 2.f; b0 = c2; }
-            else { lo = max(s0, ni); b2 = 1.f; b1 = 0.f; b0 = 0.f; }
+            if (seg == 0) {
+                hi = min(s1, ni);
+                bnd = false;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    A0[p] = C2;
+                    A1[p] = f2_pack(2.f, 2.f);
+                    A2[p] = f2_pack(k2, k2);
+                }
+            } else {
+                lo = max(s0, ni);
+                bnd = true;
+            }
             if (hi <= lo) continue;
         }
         for (int64_t tb = lo; tb < hi; tb += MF_SB) {
             __syncthreads();
             for (int q = threadIdx.x; q < MF_SB; q += TH) {
                 const int64_t s = tb + q;
-                float4 v;
-                if (s < hi) {
-                    v.x = (float)X[s];
-                    v.y = (float)X[n + s];
-                    v.z = (float)X[2 * n + s];
-                    v.w = x32[s];
-                } else {
-                    v = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                tile[q] = v;
+                tile[q] = s < hi ? mf_node((float)X[s], (float)X[n + s], (float)X[2 * n + s], x32[s])
+                                 : mf_node(0.f, 0.f, 0.f, 0.f);
             }
             __syncthreads();
             const int cnt = (int)min((int64_t)MF_SB, hi - tb);
-            float t[RO];
+            f2_t T[NP];
 #pragma unroll
-            for (int r = 0; r < RO; ++r) t[r] = 0.f;
-#pragma unroll 4
-            for (int q = 0; q < cnt; ++q) {
-                const float4 cq = tile[q];
+            for (int p = 0; p < NP; ++p) T[p] = 0ull;
+            if (bnd)
+                mf_tile<NP, true>(tile, cnt, OX, OY, OZ, A0, A1, A2, C2, T);
+            else
+                mf_tile<NP, false>(tile, cnt, OX, OY, OZ, A0, A1, A2, C2, T);
 #pragma unroll
-                for (int r = 0; r < RO; ++r) {
-                    const float dx = ox[r] - cq.x, dy = oy[r] - cq.y, dz = oz[r] - cq.z;
-                    const float s = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, c2)));
-                    const float rs = rsqrt_approx_b(s);
-                    const float P = TRANS ? fmaf(s, fmaf(b2, s, b1), b0) : fmaf(s, fmaf(a2[r], s, a1[r]), a0[r]);
-                    const float rs3 = (rs * rs) * rs;
-                    t[r] = fmaf(rs3 * P, cq.w, t[r]);
-                }
+            for (int p = 0; p < NP; ++p) {
+                float t0, t1;
+                f2_unpack(T[p], t0, t1);
+                acc[2 * p] += (double)t0;
+                acc[2 * p + 1] += (double)t1;
             }
-#pragma unroll
-            for (int r = 0; r < RO; ++r) acc[r] += (double)t[r];
         }
     }
     double* part = part_all + I.poff + (int64_t)it.chunk * n;

@@ -66,6 +66,97 @@ __global__ void __launch_bounds__(GN_THREADS) k_gemv_n_f64(
     }
 }
 
+// ---------------------------------------------------------------------------
+// part[g][i] = sum_{j in column segment g} A_ij x_j: the n x S (row, segment)
+// units are split into equal contiguous ranges, one per warp of the grid, so
+// every resident warp does the same work to within one unit (row-granular
+// work would leave a tail of warps with one row more than the others).
+// Segments start on even columns (16-byte aligned double2 loads).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(GN_THREADS) k_gemv_nseg_f64(
+    const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x, int S,
+    int64_t seglen, double* __restrict__ part, const int* __restrict__ done) {
+    if (gkb_done(done)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t W = (int64_t)gridDim.x * (GN_THREADS / 32);
+    const int64_t w = (int64_t)blockIdx.x * (GN_THREADS / 32) + warp;
+    const int64_t U = n * S;
+    const int64_t u0 = U * w / W, u1 = U * (w + 1) / W;
+    for (int64_t u = u0; u < u1; ++u) {
+        const int64_t i = u / S;
+        const int g = (int)(u - i * S);
+        const int64_t c0 = (int64_t)g * seglen;
+        const int64_t c1 = min(n, c0 + seglen);
+        const double2* __restrict__ row = reinterpret_cast<const double2*>(A + i * lda + c0);
+        const double2* __restrict__ xv = reinterpret_cast<const double2*>(x + c0);
+        const int64_t nvec = (c1 - c0) >> 1;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t v = lane;
+        for (; v + 96 < nvec; v += 128) {
+            double2 m0 = ld_stream(row + v), m1 = ld_stream(row + v + 32);
+            double2 m2 = ld_stream(row + v + 64), m3 = ld_stream(row + v + 96);
+            double2 x0 = __ldg(xv + v), x1 = __ldg(xv + v + 32);
+            double2 x2 = __ldg(xv + v + 64), x3 = __ldg(xv + v + 96);
+            a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
+            a1 = fma(m1.x, x1.x, a1); a1 = fma(m1.y, x1.y, a1);
+            a2 = fma(m2.x, x2.x, a2); a2 = fma(m2.y, x2.y, a2);
+            a3 = fma(m3.x, x3.x, a3); a3 = fma(m3.y, x3.y, a3);
+        }
+        for (; v < nvec; v += 32) {
+            double2 m0 = ld_stream(row + v), x0 = __ldg(xv + v);
+            a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
+        }
+        if (((c1 - c0) & 1) && lane == 0) a1 = fma(A[i * lda + c1 - 1], __ldg(x + c1 - 1), a1);
+        const double acc = warp_sum((a0 + a1) + (a2 + a3));
+        if (lane == 0) part[(int64_t)g * n + i] = acc;
+    }
+}
+
+// FP32 (mixed) version: products of one float4 quad group summed in FP32,
+// each group added into the FP64 accumulator; segments start on multiples of
+// 4 columns (16-byte aligned float4 loads).
+__global__ void __launch_bounds__(GN_THREADS) k_gemv_nseg_f32(
+    const float* __restrict__ A, int64_t lda, int64_t n, const float* __restrict__ x32, int S,
+    int64_t seglen, double* __restrict__ part, const int* __restrict__ done) {
+    if (gkb_done(done)) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t W = (int64_t)gridDim.x * (GN_THREADS / 32);
+    const int64_t w = (int64_t)blockIdx.x * (GN_THREADS / 32) + warp;
+    const int64_t U = n * S;
+    const int64_t u0 = U * w / W, u1 = U * (w + 1) / W;
+    for (int64_t u = u0; u < u1; ++u) {
+        const int64_t i = u / S;
+        const int g = (int)(u - i * S);
+        const int64_t c0 = (int64_t)g * seglen;
+        const int64_t c1 = min(n, c0 + seglen);
+        const float4* __restrict__ row = reinterpret_cast<const float4*>(A + i * lda + c0);
+        const float4* __restrict__ xv = reinterpret_cast<const float4*>(x32 + c0);
+        const int64_t nvec = (c1 - c0) >> 2;
+        double acc = 0.0;
+        int64_t v = lane;
+        for (; v + 96 < nvec; v += 128) {
+            float4 m0 = ld_stream(row + v), m1 = ld_stream(row + v + 32);
+            float4 m2 = ld_stream(row + v + 64), m3 = ld_stream(row + v + 96);
+            float4 x0 = __ldg(xv + v), x1 = __ldg(xv + v + 32);
+            float4 x2 = __ldg(xv + v + 64), x3 = __ldg(xv + v + 96);
+            float s0 = m0.x * x0.x, s1 = m1.x * x1.x, s2 = m2.x * x2.x, s3 = m3.x * x3.x;
+            s0 = fmaf(m0.y, x0.y, s0); s1 = fmaf(m1.y, x1.y, s1); s2 = fmaf(m2.y, x2.y, s2); s3 = fmaf(m3.y, x3.y, s3);
+            s0 = fmaf(m0.z, x0.z, s0); s1 = fmaf(m1.z, x1.z, s1); s2 = fmaf(m2.z, x2.z, s2); s3 = fmaf(m3.z, x3.z, s3);
+            s0 = fmaf(m0.w, x0.w, s0); s1 = fmaf(m1.w, x1.w, s1); s2 = fmaf(m2.w, x2.w, s2); s3 = fmaf(m3.w, x3.w, s3);
+            acc += (double)((s0 + s1) + (s2 + s3));
+        }
+        for (; v < nvec; v += 32) {
+            float4 m0 = ld_stream(row + v), x0 = __ldg(xv + v);
+            float s0 = m0.x * x0.x;
+            s0 = fmaf(m0.y, x0.y, s0); s0 = fmaf(m0.z, x0.z, s0); s0 = fmaf(m0.w, x0.w, s0);
+            acc += (double)s0;
+        }
+        for (int64_t c = c0 + nvec * 4 + lane; c < c1; c += 32) acc += (double)(A[i * lda + c] * x32[c]);
+        acc = warp_sum(acc);
+        if (lane == 0) part[(int64_t)g * n + i] = acc;
+    }
+}
+
 __global__ void __launch_bounds__(GN_THREADS) k_gemv_n_f32(
     const float* __restrict__ A, int64_t lda, int64_t n, const float* __restrict__ x32,
     const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ sc,
@@ -233,6 +324,7 @@ size_t gemv_ws_bytes(const rbf_ctx* ctx, int64_t n) {
     int pc4, pn4, ch4;
     plan_t(ctx, n, 4, &pc4, &pn4, &ch4);
     int c = ch > ch4 ? ch : ch4;
+    if (c < 8) c = 8;  // column segments of the FP64 A x
     return ws_align((size_t)c * n * sizeof(double)) + ws_align((size_t)n * sizeof(float));
 }
 
@@ -249,11 +341,72 @@ static int gemv_n_grid(const rbf_ctx* ctx, int64_t n) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// FP64 A x: grid = one wave of resident CTAs; S column segments per row chosen
+// so that the n S units divide as evenly as possible over the grid's warps
+// (efficiency x / ceil(x) with x = n S / warps), segments of >= 256 columns.
+static void gemv_nseg_plan(const rbf_ctx* ctx, int64_t n, bool fp64, int* grid, int* S, int64_t* seglen) {
+    static int occ[2][64] = {{0}};
+    const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
+    int& o = occ[fp64 ? 0 : 1][dev];
+    if (!o) {
+        int a = 0;
+        const cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_nseg_f64, GN_THREADS, 0)
+                                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_nseg_f32, GN_THREADS, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            a = 4;
+        }
+        o = a < 1 ? 1 : a;
+    }
+    int64_t g = (int64_t)ctx->sm_count * o;
+    const int64_t rows_min = (n + 7) / 8;
+    if (g > rows_min) g = rows_min;
+    if (g < 1) g = 1;
+    const double W = (double)g * (GN_THREADS / 32);
+    int best = 1;
+    double best_eff = 0.0;
+    for (int s = 1; s <= 8; ++s) {
+        if (s > 1 && n / s < 256) break;
+        const double xu = (double)n * s / W;
+        const double eff = xu / ceil(xu);
+        if (eff > best_eff + 1e-3) {
+            best_eff = eff;
+            best = s;
+        }
+    }
+    int64_t len = (n + best - 1) / best;
+    const int64_t al = fp64 ? 2 : 4;  // segments start on 16-byte boundaries
+    len = (len + al - 1) / al * al;
+    *grid = (int)g;
+    *S = (int)((n + len - 1) / len);
+    *seglen = len;
+}
+
+int gemv_n_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
+    int g, S;
+    int64_t len;
+    gemv_nseg_plan(ctx, op->n, op->precision == RBF_FP64, &g, &S, &len);
+    return S;
+}
+
 rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, const float* x32,
                          double* y, const double* sc, const double* w, double* z_out,
                          const int* done) {
     const int grid = gemv_n_grid(ctx, op->n);
-    if (op->precision == RBF_FP64) {
+    if (!sc) {  // column-segment partials [S][n] into y
+        int g, S;
+        int64_t len;
+        gemv_nseg_plan(ctx, op->n, op->precision == RBF_FP64, &g, &S, &len);
+        if (op->precision == RBF_FP64) {
+            k_gemv_nseg_f64<<<g, GN_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x, S, len,
+                                                               y, done);
+            RBF_LAUNCHED(ctx, "k_gemv_nseg_f64");
+        } else {
+            k_gemv_nseg_f32<<<g, GN_THREADS, 0, ctx->stream>>>((const float*)op->d_A, op->lda, op->n, x32, S, len,
+                                                               y, done);
+            RBF_LAUNCHED(ctx, "k_gemv_nseg_f32");
+        }
+    } else if (op->precision == RBF_FP64) {
         k_gemv_n_f64<<<grid, GN_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x,
                                                            y, sc, w, z_out, done);
         RBF_LAUNCHED(ctx, "k_gemv_n_f64");
@@ -314,7 +467,12 @@ extern "C" rbf_status rbf_matvec(rbf_ctx* ctx, const rbf_operator* op, int trans
     double* part = wc.take<double>((size_t)ch * n);
     float* x32 = wc.take<float>((size_t)n);
     if (op->precision == RBF_MIXED) RBF_TRY(launch_to_f32(ctx, n, d_x, x32));
-    if (trans == 0) return launch_gemv_n(ctx, op, d_x, x32, d_y, nullptr, nullptr, nullptr, nullptr);
+    if (trans == 0) {
+        const int S = gemv_n_chunks(ctx, op);
+        if (S == 1) return launch_gemv_n(ctx, op, d_x, x32, d_y, nullptr, nullptr, nullptr, nullptr);
+        RBF_TRY(launch_gemv_n(ctx, op, d_x, x32, part, nullptr, nullptr, nullptr, nullptr));
+        return launch_reduce_partials(ctx, n, S, part, d_y);
+    }
     RBF_TRY(launch_gemv_t_partial(ctx, op, d_x, x32, part, nullptr));
     return launch_reduce_partials(ctx, n, ch, part, d_y);
 }
