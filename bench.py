@@ -72,7 +72,11 @@ def workload(name):
     import numpy as np
 
     import workloads as w
-    if name == "cube8000":
+    if name == "cube1000":
+        ns = w.preset("cube1000")
+        cases = [(0.3, 2.0)]
+        steps, prec, storage = 40, "fp64", "assembled"
+    elif name == "cube8000":
         ns = w.preset("cube8000")
         cases = [(c, k) for c in (0.1, 0.2, 0.5) for k in (2.0, 5.0)]
         steps, prec, storage = 100, "fp64", "assembled"
@@ -249,6 +253,8 @@ def run_ours(args, rank, world, local_rank):
         ctx_ph.rbf_evaluate(op, coef, pts_d, m, u_d[ci])
         phases = ctx_ph.rbf_get_timings()
     ctx_ph.close()
+    methods = all_methods(ctx, wl, nodes_d, pts_d, f_d, A, lda, storage, prec, st, coef, stream) \
+        if wl["name"] == "cube1000" else None
     if rank != 0:
         return None
     peaks = measured_peaks()
@@ -303,9 +309,58 @@ def run_ours(args, rank, world, local_rank):
                 "ms_per_step": round(ms_e2e / args.steps, 3)},
         "gpu_launches": int(cnt["launches"]),
         "phase_ms_one_solve": {k: round(v, 3) for k, v in phases.items() if k.endswith("_ms")},
+        "methods": methods,
         "clocks": clocks,
     }
     ctx.close()
+    return out
+
+
+def all_methods(ctx, wl, nodes_d, pts_d, f_d, A, lda, storage, prec, st, coef, stream):
+    """Every method of the paper on the first (c, k) case, each timed once on the
+    device (after the timed region) with its max error against the exact plane
+    wave: full-SVD Tikhonov and TSVD (Algorithm 3, GCV), Ine-TSVD and HKT on
+    l GKB steps (Algorithms 2 and 4, GCV and L-curve), LSQR early stopping."""
+    import numpy as np
+    import torch
+
+    import workloads as w
+    from paper_2511_09798_gb300 import rbfkr as R
+    ns, (c, k), L = wl["ns"], wl["cases"][0], wl["steps"]
+    n, m = ns.n, wl["points"].shape[0]
+    ue = w.plane_wave(wl["points"], k)
+    u = torch.empty(m, dtype=torch.float64, device=nodes_d.device)
+    op = ctx.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, storage, prec, R.RBF_FORM_C, A,
+                               lda if A is not None else 0)
+    if A is not None:
+        ctx.rbf_assemble(op)
+    out = {}
+
+    def timed(name, fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = fn()
+        ctx.rbf_evaluate(op, coef, pts_d, m, u)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        err = float(np.max(np.abs(u.cpu().numpy() - ue)) / np.max(np.abs(ue)))
+        out[name] = {"ms": round(e0.elapsed_time(e1), 3), "max_err_vs_exact": err}
+        if info is not None:
+            out[name].update({"lambda": info.lambda_, "rank": info.rank, "steps": info.steps})
+
+    f = f_d[k]
+    timed("tikhonov_full_gcv", lambda: ctx.rbf_tikhonov(op, f, R.RBF_GCV, 0.0, coef))
+    timed("tsvd_full_gcv", lambda: ctx.rbf_tsvd(op, f, 0, coef))
+
+    def gkb_then(solve):
+        ctx.rbf_gkb(op, f, L, st)
+        return solve()
+    timed("hkt_gcv", lambda: gkb_then(lambda: ctx.rbf_hkt(st, R.RBF_GCV, 0.0, coef)))
+    timed("hkt_lcurve", lambda: gkb_then(lambda: ctx.rbf_hkt(st, R.RBF_LCURVE, 0.0, coef)))
+    timed("ine_tsvd_gcv", lambda: gkb_then(lambda: ctx.rbf_ine_tsvd(st, 0, coef)))
+    timed("lsqr_lcurve", lambda: gkb_then(lambda: ctx.rbf_lsqr(st, R.RBF_LCURVE, 0, coef)))
+    timed("lsqr_gcv", lambda: gkb_then(lambda: ctx.rbf_lsqr(st, R.RBF_GCV, 0, coef)))
     return out
 
 

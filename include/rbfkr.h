@@ -238,10 +238,41 @@ rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambd
 rbf_status rbf_ine_tsvd(rbf_ctx* ctx, const rbf_gkb_state* st, int rank, double* d_coef,
                         double* d_curve, rbf_solve_info* info);
 
-/* Full-SVD Tikhonov / TSVD (Algorithm 3, eq. tsvd_solution): not implemented
- * on the GPU; returns RBF_ERR_UNSUPPORTED. */
+/* LSQR as iterative regularization (Sec. 3.4) on a finished GKB run: the k-th
+ * iterate x_k = Z_k y_k, y_k the least-squares solution of C_k y = beta_1 e_1,
+ * with k chosen from the sequence (rho_k, eta_k) = (|A x_k - f|, |x_k|),
+ * k = 1..l: RBF_LCURVE = the corner (maximum signed curvature of
+ * (ln rho_k, ln eta_k) by central differences along decreasing k, stationary
+ * points excluded), RBF_GCV = argmin rho_k^2 / ((l+1) - k)^2, RBF_FIXED =
+ * k_fixed (1..l).  d_coef[n] = x_k; d_curve (optional, length l) receives the
+ * rule's values.  l <= 511.  Synchronises; info->rank = k, eta and rho at k. */
+rbf_status rbf_lsqr(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, int k_fixed, double* d_coef,
+                    double* d_curve, rbf_solve_info* info);
+
+/* Full SVD of an assembled FP64 operator (Algorithm 3 step 1), 2 <= n <=
+ * 8192, by one-sided Jacobi: d_sigma[n] receives the singular values in
+ * descending order; with d_f given, d_fhat[n] receives f^ = U^T f; d_V
+ * (optional, n x n column-major) the right singular vectors in the same order.
+ * *sweeps (optional) receives the number of Jacobi sweeps.  Uses 2 n^2 doubles
+ * of workspace.  Synchronises.  RBF_ERR_UNSUPPORTED for other operators. */
+rbf_status rbf_svd_full(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, double* d_sigma,
+                        double* d_fhat, double* d_V, int* sweeps);
+
+/* Full-SVD Tikhonov (Algorithm 3): lambda by GCV on the grid lambda = s_1 10^t
+ * (eq. gcv_svd, denominator (N - r) + sum_{i<=r} (1 - phi_i), numerical rank
+ * r = #{s_i > N eps s_1}, s_perp = sum_{i>r} f^_i^2) or fixed (RBF_FIXED);
+ * d_coef[n] = sum_{i<=r} phi_i / s_i f^_i v_i (eq. tikh_svd_solution).
+ * Assembled FP64 operators, n <= 8192.  Synchronises; info: lambda, index,
+ * rank = r, steps = Jacobi sweeps, sigma1. */
 rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int rule,
                         double lambda_in, double* d_coef, rbf_solve_info* info);
+
+/* Full TSVD (eq. tsvd_solution): d_coef[n] = sum_{i<=k} f^_i / s_i v_i with
+ * k = rank (1..n) or, for rank = 0, the GCV choice over k = 1..min(r, N-1):
+ * GCV(k) = (sum_{k<i<=r} f^_i^2 + s_perp) / (N - k)^2.  Same operators and
+ * synchronisation as rbf_tikhonov; info->rank = k. */
+rbf_status rbf_tsvd(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int rank, double* d_coef,
+                    rbf_solve_info* info);
 
 /* ---- reconstruction (eq. u_reconstruction) --------------------------- */
 

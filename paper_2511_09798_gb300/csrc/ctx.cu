@@ -226,12 +226,4 @@ rbf_status rbf_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* d_co
     return RBF_OK;
 }
 
-rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int rule,
-                        double lambda_in, double* d_coef, rbf_solve_info* info) {
-    (void)op; (void)d_f; (void)rule; (void)lambda_in; (void)d_coef; (void)info;
-    if (!ctx) return RBF_ERR_INVALID;
-    return rbf_fail(ctx, RBF_ERR_UNSUPPORTED,
-                    "full-SVD Tikhonov (Algorithm 3) is not implemented on the GPU");
-}
-
 }  // extern "C"

@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "grid_sync.cuh"
 
 namespace {
 
@@ -124,56 +125,6 @@ __global__ void k_finalize(rbf_dev_state* __restrict__ stt, const double* __rest
     __syncthreads();
     if (bd == 2 && wzero)
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) wzero[i] = 0.0;
-}
-
-// ---------------------------------------------------------------------------
-// Grid barrier for the cooperative half-step kernel: two levels so that no
-// L2 address sees more than ~sqrt(G) atomics (one address with all G CTAs
-// serialises ~14 ns per atomic).  bar[0..K) are group counters, bar[K] the top
-// counter, bar[K+1] the generation; each on its own 128-byte line (stride 32).
-// Bounded: after `budget` polls it records RBF_ERR_TIMEOUT in the device state,
-// stops the run and returns false; the caller's CTA then exits without further
-// barriers.
-// ---------------------------------------------------------------------------
-constexpr int BAR_STRIDE = 32;
-
-__device__ bool grid_sync(rbf_dev_state* __restrict__ stt, unsigned* __restrict__ bar, int group,
-                          long long budget) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int G = gridDim.x;
-        const int K = (G + group - 1) / group;
-        const int grp = blockIdx.x / group;
-        const int members = min(group, G - grp * group);
-        unsigned* sub = bar + (size_t)grp * BAR_STRIDE;
-        unsigned* top = bar + (size_t)K * BAR_STRIDE;
-        volatile unsigned* gen = bar + (size_t)(K + 1) * BAR_STRIDE;
-        const unsigned g0 = *gen;
-        __threadfence();
-        int good = 1;
-        if (atomicAdd(sub, 1u) == (unsigned)members - 1) {
-            atomicExch(sub, 0u);
-            if (atomicAdd(top, 1u) == (unsigned)K - 1) {
-                atomicExch(top, 0u);
-                __threadfence();
-                atomicAdd((unsigned*)gen, 1u);
-            }
-        }
-        long long it = 0;
-        while (*gen == g0) {
-            if (++it > budget) {
-                good = 0;
-                atomicExch(&stt->info[IN_ERR], (int)RBF_ERR_TIMEOUT);
-                atomicExch(&stt->info[IN_DONE], 1);
-                break;
-            }
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
 }
 
 __device__ __forceinline__ void cp_async8(double* smem_dst, const double* gsrc) {

@@ -111,8 +111,14 @@ EXPORTS = {
                           C.c_void_p, C.POINTER(SolveInfo)]),
     "rbf_ine_tsvd": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_int, C.c_void_p, C.c_void_p,
                                C.POINTER(SolveInfo)]),
+    "rbf_lsqr": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                           C.POINTER(SolveInfo)]),
     "rbf_tikhonov": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_int, C.c_double,
                                C.c_void_p, C.POINTER(SolveInfo)]),
+    "rbf_svd_full": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(C.c_int)]),
+    "rbf_tsvd": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_int, C.c_void_p,
+                           C.POINTER(SolveInfo)]),
     "rbf_evaluate": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_void_p, C.c_int64,
                                C.c_void_p]),
     "rbf_batch_gkb": (C.c_int, [C.c_void_p, C.POINTER(Batch), C.c_int, C.c_int]),
@@ -283,6 +289,23 @@ class Context:
         info = SolveInfo()
         self._check(self.lib.rbf_ine_tsvd(self.h, C.byref(state), rank, _ptr(coef), _ptr(curve),
                                           C.byref(info)))
+        return info
+
+    def rbf_lsqr(self, state, rule, k_fixed, coef, curve=None):
+        info = SolveInfo()
+        self._check(self.lib.rbf_lsqr(self.h, C.byref(state), rule, int(k_fixed), _ptr(coef), _ptr(curve),
+                                      C.byref(info)))
+        return info
+
+    def rbf_svd_full(self, op, sigma, f=None, fhat=None, V=None):
+        sw = C.c_int(0)
+        self._check(self.lib.rbf_svd_full(self.h, C.byref(op), _ptr(f), _ptr(sigma), _ptr(fhat), _ptr(V),
+                                          C.byref(sw)))
+        return sw.value
+
+    def rbf_tsvd(self, op, f, rank, coef):
+        info = SolveInfo()
+        self._check(self.lib.rbf_tsvd(self.h, C.byref(op), _ptr(f), int(rank), _ptr(coef), C.byref(info)))
         return info
 
     def rbf_tikhonov(self, op, f, rule, lambda_in, coef):
