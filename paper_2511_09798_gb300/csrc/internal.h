@@ -145,7 +145,8 @@ size_t svd_ws_bytes(int l);
 size_t svd_ws_bytes_batch(int L, int B);
 rbf_status launch_projected_svd_batch(rbf_ctx* ctx, ProjDims d, const double* alpha, const double* beta,
                                       double* sigma, double* ftil, double* V, int64_t ldv, void* ws,
-                                      double* sigma1_out, double* ftil_last_out);
+                                      double* sigma1_out, double* ftil_last_out, double* U = nullptr,
+                                      int64_t ldu = 0);
 rbf_status launch_projected_svd(rbf_ctx* ctx, const double* alpha, const double* beta, int l,
                                 double* sigma, double* ftil, double* V, int64_t ldv, void* ws);
 // select.cu

@@ -287,12 +287,14 @@ __global__ void k_tgk_clusters(ProjDims d, const double* __restrict__ sigma_all,
     }
 }
 
-// Split the eigenvectors into u~, v~ (normalised), write V~ and f~.  One block per instance.
+// Split the eigenvectors into u~, v~ (normalised), write V~ (and U~ when
+// asked: column i = u~_i, l+1 entries, ld ldu) and f~.  One block per instance.
 __global__ void k_tgk_finalize(ProjDims d, const double* __restrict__ alpha_all,
                                const double* __restrict__ beta_all, const double* __restrict__ X_all,
                                double* __restrict__ ftil_all, double* __restrict__ V_all, int64_t ldv,
                                rbf_dev_state* __restrict__ stt, const double* __restrict__ sigma_all,
-                               double* __restrict__ sigma1_out, double* __restrict__ ftil_last_out) {
+                               double* __restrict__ sigma1_out, double* __restrict__ ftil_last_out,
+                               double* __restrict__ U_all, int64_t ldu) {
     __shared__ double Ls[1024];
     __shared__ double red[32];
     const int b = blockIdx.x;
@@ -318,6 +320,11 @@ __global__ void k_tgk_finalize(ProjDims d, const double* __restrict__ alpha_all,
         nv = warp_sum(nv);
         const double iv = rsqrt(nv);
         for (int k = 2 * lane + 1; k < nt; k += 64) V[(int64_t)i * ldv + (k >> 1)] = x[k] * iv;
+        if (U_all) {
+            const double iu = rsqrt(nu);
+            double* U = U_all + (size_t)b * L * ldu;
+            for (int k = 2 * lane; k < nt; k += 64) U[(int64_t)i * ldu + (k >> 1)] = x[k] * iu;
+        }
         if (lane == 0) ftil[i] = beta1 * x[0] * rsqrt(nu);
     }
     // f~_{l+1} = beta_1 / |u|, u_1 = 1, log|u_{j+1}| = log|u_j| + log(alpha_j / beta_{j+1})
@@ -373,7 +380,7 @@ size_t svd_ws_bytes_batch(int L, int B) {
 
 rbf_status launch_projected_svd_batch(rbf_ctx* ctx, ProjDims d, const double* alpha, const double* beta,
                                       double* sigma, double* ftil, double* V, int64_t ldv, void* ws,
-                                      double* sigma1_out, double* ftil_last_out) {
+                                      double* sigma1_out, double* ftil_last_out, double* U, int64_t ldu) {
     const int L = d.L, B = d.B;
     if (L < 1 || L > 1023) return rbf_fail(ctx, RBF_ERR_INVALID, "projected dimension %d outside [1, 1023]", L);
     const size_t NT = 2 * (size_t)L + 1;
@@ -394,7 +401,7 @@ rbf_status launch_projected_svd_batch(rbf_ctx* ctx, ProjDims d, const double* al
     k_tgk_clusters<<<B, CL_WARPS * 32, 0, s>>>(d, sigma, ctx->opt.cluster_tol, invdp, rp, X, tmp);
     RBF_LAUNCHED(ctx, "k_tgk_clusters");
     k_tgk_finalize<<<B, 256, 0, s>>>(d, alpha, beta, X, ftil, V, ldv, B == 1 ? ctx->d_state : nullptr, sigma,
-                                     sigma1_out, ftil_last_out);
+                                     sigma1_out, ftil_last_out, U, ldu);
     RBF_LAUNCHED(ctx, "k_tgk_finalize");
     return RBF_OK;
 }

@@ -2,17 +2,27 @@
 // the full-SVD methods on top of it: Tikhonov with GCV (Algorithm 3, eqs.
 // gcv_svd and tikh_svd_solution) and TSVD (eq. tsvd_solution).
 //
-// SVD by one-sided (Hestenes) Jacobi: the columns of W = A are rotated in
+// n <= 1023: Householder bidiagonalization A = Q_L B Q_R^T in one cooperative
+// kernel (per step a left reflector on column k applied to the trailing
+// columns and to f, which rides along as an extra column so that g = Q_L^T f
+// comes out of the same pass, then a right reflector on row k applied to the
+// trailing rows; bounded grid barriers between the phases), then the SVD of
+// the bidiagonal through the Golub-Kahan tridiagonal (the projected-SVD
+// kernels with C = [B^T; 0]: sigma, V~ = U_B and U~ = V_B), f^ = V~^T g and
+// alpha = Q_R (U~ d).
+//
+// Larger n: one-sided (Hestenes) Jacobi: the columns of W = A are rotated in
 // pairs until they are mutually orthogonal (W = U Sigma, V = product of the
-// rotations), which keeps the small singular values of these very
-// ill-conditioned matrices accurate.  One cooperative kernel per sweep: each
-// round pairs the columns by the circle method (n/2 disjoint pairs), one CTA
-// per pair: the three dot products |w_i|^2, |w_j|^2, w_i.w_j in one pass, the
-// rotation that zeroes w_i.w_j applied to w_i, w_j and v_i, v_j; a bounded
-// grid barrier separates the rounds.  Sweeps repeat until no pair needed a
-// rotation (|w_i.w_j| <= tol |w_i| |w_j|).  Then sigma_j = |w_j| sorted
-// descending, f^ = U^T f = W^T f / sigma, numerical rank r = #{sigma_i >
-// N eps sigma_1}, and the solution alpha = V d.
+// rotations).  One cooperative kernel per sweep: each round pairs the columns
+// by the circle method (n/2 disjoint pairs), one CTA per pair: the three dot
+// products |w_i|^2, |w_j|^2, w_i.w_j in one pass, the rotation that zeroes
+// w_i.w_j applied to w_i, w_j and v_i, v_j; a bounded grid barrier separates
+// the rounds.  Sweeps repeat until no pair needed a rotation (|w_i.w_j| <=
+// sqrt(n) eps |w_i| |w_j|).  Then sigma_j = |w_j| sorted descending and
+// f^ = W^T f / sigma.
+//
+// Both: numerical rank r = #{sigma_i > N eps sigma_1}, s_perp = sum_{i>r}
+// f^_i^2, the GCV grid (Tikhonov) or rank curve (TSVD), the solution alpha.
 #include <cfloat>
 #include <vector>
 
@@ -277,6 +287,199 @@ __global__ void k_fsvd_lift(const double* __restrict__ V, int64_t n, const int* 
     coef[row] = acc;
 }
 
+// ---------------------------------------------------------------------------
+// Householder bidiagonalization path (n <= 1023)
+// ---------------------------------------------------------------------------
+constexpr int BT = 256;
+constexpr int BW = BT / 32;
+
+__device__ __forceinline__ double block_sum1(double v, double* red) {
+    v = warp_sum(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < BW; ++w) t += red[w];
+    return t;
+}
+
+// Reflector H = I - tau v v^T with v = [1; x_rest * scale] and H x = beta e_1,
+// from x_0 and ss = |x_rest|^2 (tau = 0: no reflection needed).
+__device__ __forceinline__ void reflector(double x0, double ss, double* sc) {
+    if (ss == 0.0) {
+        sc[0] = 0.0;
+        sc[1] = 0.0;
+        sc[2] = x0;
+        return;
+    }
+    const double nrm = sqrt(fma(x0, x0, ss));
+    const double beta = x0 >= 0.0 ? -nrm : nrm;
+    sc[0] = (beta - x0) / beta;
+    sc[1] = 1.0 / (x0 - beta);
+    sc[2] = beta;
+}
+
+// W column-major n x (n+1) (ld n), the last column f.  On return: dg = diag
+// of B, eg = superdiagonal, column n = Q_L^T f, the right reflectors in rows
+// k (entries k+2..n-1, unscaled) with taur / scaler.
+__global__ void __launch_bounds__(BT) k_bidiag(double* __restrict__ W, int64_t n, double* __restrict__ dg,
+                                               double* __restrict__ eg, double* __restrict__ taur,
+                                               double* __restrict__ scaler, rbf_dev_state* __restrict__ stt,
+                                               unsigned* __restrict__ bar, int group, long long budget) {
+    __shared__ double red[BW];
+    __shared__ double sc[3];
+    __shared__ double rp[BW][32];
+    __shared__ double rw[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t GW = (int64_t)gridDim.x * BW, gw = (int64_t)blockIdx.x * BW + warp;
+    for (int64_t k = 0; k < n; ++k) {
+        // left reflector of column k (rows k..n-1), every CTA computes it
+        const double* xk = W + k * n + k;
+        const int64_t m = n - k;
+        double ss = 0.0;
+        for (int64_t i = 1 + threadIdx.x; i < m; i += BT) ss = fma(xk[i], xk[i], ss);
+        ss = block_sum1(ss, red);
+        if (threadIdx.x == 0) reflector(xk[0], ss, sc);
+        __syncthreads();
+        const double tau = sc[0], scale = sc[1];
+        if (tau != 0.0) {
+            for (int64_t j = k + 1 + gw; j <= n; j += GW) {  // warp per trailing column, f included
+                double* wj = W + j * n + k;
+                const double w0 = wj[0];
+                double sd = 0.0, sd1 = 0.0;
+                int64_t i = 1 + lane;
+                for (; i + 32 < m; i += 64) {
+                    sd = fma(xk[i], wj[i], sd);
+                    sd1 = fma(xk[i + 32], wj[i + 32], sd1);
+                }
+                if (i < m) sd = fma(xk[i], wj[i], sd);
+                sd = warp_sum(sd + sd1);
+                const double t = tau * fma(scale, sd, w0);
+                const double ts = t * scale;
+                for (int64_t i = 1 + lane; i < m; i += 32) wj[i] = fma(-ts, xk[i], wj[i]);
+                if (lane == 0) wj[0] = w0 - t;
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) dg[k] = sc[2];
+        if (!grid_sync(stt, bar, group, budget)) return;
+        if (k == n - 1) break;
+        // right reflector of row k (columns k+1..n-1)
+        const int64_t m2 = n - k - 1;
+        double ss2 = 0.0;
+        for (int64_t c = 1 + threadIdx.x; c < m2; c += BT) {
+            const double y = W[(k + 1 + c) * n + k];
+            ss2 = fma(y, y, ss2);
+        }
+        ss2 = block_sum1(ss2, red);
+        if (threadIdx.x == 0) reflector(W[(k + 1) * n + k], ss2, sc);
+        __syncthreads();
+        const double tau2 = sc[0], scale2 = sc[1];
+        if (tau2 != 0.0) {
+            // 32-row blocks over the CTAs; warp q takes the columns c = q, q+8, ...
+            // (coalesced along the rows), partial dots combined in shared memory
+            const int64_t rows = n - k - 1;
+            const int64_t nblk = (rows + 31) / 32;
+            for (int64_t rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
+                const int64_t i = k + 1 + rb * 32 + lane;
+                const bool ok = i < n;
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                int64_t c = 1 + warp;
+                for (; c + 3 * BW < m2; c += 4 * BW) {
+                    if (ok) {
+                        a0 = fma(W[(k + 1 + c) * n + i], W[(k + 1 + c) * n + k], a0);
+                        a1 = fma(W[(k + 1 + c + BW) * n + i], W[(k + 1 + c + BW) * n + k], a1);
+                        a2 = fma(W[(k + 1 + c + 2 * BW) * n + i], W[(k + 1 + c + 2 * BW) * n + k], a2);
+                        a3 = fma(W[(k + 1 + c + 3 * BW) * n + i], W[(k + 1 + c + 3 * BW) * n + k], a3);
+                    }
+                }
+                for (; c < m2; c += BW)
+                    if (ok) a0 = fma(W[(k + 1 + c) * n + i], W[(k + 1 + c) * n + k], a0);
+                rp[warp][lane] = (a0 + a1) + (a2 + a3);
+                __syncthreads();
+                if (warp == 0) {
+                    double t = 0.0;
+#pragma unroll
+                    for (int q = 0; q < BW; ++q) t += rp[q][lane];
+                    const double x0 = ok ? W[(k + 1) * n + i] : 0.0;
+                    rw[lane] = tau2 * fma(scale2, t, x0);  // t_i = tau (u . w_i)
+                }
+                __syncthreads();
+                const double ti = rw[lane];
+                if (ok) {
+                    if (warp == 0) W[(k + 1) * n + i] -= ti;
+                    const double tsi = ti * scale2;
+                    for (int64_t cc = 1 + warp; cc < m2; cc += BW)
+                        W[(k + 1 + cc) * n + i] = fma(-tsi, W[(k + 1 + cc) * n + k], W[(k + 1 + cc) * n + i]);
+                }
+                __syncthreads();
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            eg[k] = sc[2];
+            taur[k] = tau2;
+            scaler[k] = scale2;
+        }
+        if (!grid_sync(stt, bar, group, budget)) return;
+    }
+}
+
+// alpha / beta of C = [B^T; 0] for the tridiagonal SVD: alpha = dg, beta =
+// (1, eg, 0); beta_1 only scales f~, which is not used here.
+__global__ void k_bidiag_ab(const double* __restrict__ dg, const double* __restrict__ eg, int64_t n,
+                            double* __restrict__ alpha, double* __restrict__ beta) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) alpha[i] = dg[i];
+    if (i <= n) beta[i] = i == 0 ? 1.0 : (i < n ? eg[i - 1] : 0.0);
+}
+
+// fhat[i] = V~_i . g  (V~ column-major, ld n; one CTA per i)
+__global__ void __launch_bounds__(BT) k_vt_g(const double* __restrict__ Vt, int64_t n, const double* __restrict__ g,
+                                             double* __restrict__ fhat) {
+    __shared__ double red[BW];
+    const double* v = Vt + (int64_t)blockIdx.x * n;
+    double a = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += BT) a = fma(v[k], g[k], a);
+    a = block_sum1(a, red);
+    if (threadIdx.x == 0) fhat[blockIdx.x] = a;
+}
+
+// x[row] = sum_i U~[row][i] d_i over the first n rows of U~ (ld n+1)
+__global__ void k_u_d(const double* __restrict__ Ut, int64_t n, const double* __restrict__ d, double* __restrict__ x) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    double acc = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double di = d[i];
+        if (di != 0.0) acc = fma(Ut[i * (n + 1) + row], di, acc);
+    }
+    x[row] = acc;
+}
+
+// Z <- Q_R Z, one CTA per column (ld ldz): the right reflectors in reverse order.
+__global__ void __launch_bounds__(BT) k_apply_qr(const double* __restrict__ W, int64_t n,
+                                                 const double* __restrict__ taur, const double* __restrict__ scaler,
+                                                 double* __restrict__ Z, int64_t ldz) {
+    __shared__ double red[BW];
+    double* z = Z + (int64_t)blockIdx.x * ldz;
+    for (int64_t k = n - 2; k >= 0; --k) {
+        const double tau = taur[k];
+        if (tau == 0.0) continue;
+        const double scale = scaler[k];
+        const int64_t m2 = n - k - 1;
+        const double z0 = z[k + 1];
+        double sd = 0.0;
+        for (int64_t c = 1 + threadIdx.x; c < m2; c += BT) sd = fma(W[(k + 1 + c) * n + k], z[k + 1 + c], sd);
+        sd = block_sum1(sd, red);
+        const double t = tau * fma(scale, sd, z0);
+        const double ts = t * scale;
+        for (int64_t c = 1 + threadIdx.x; c < m2; c += BT) z[k + 1 + c] = fma(-ts, W[(k + 1 + c) * n + k], z[k + 1 + c]);
+        if (threadIdx.x == 0) z[k + 1] = z0 - t;
+        __syncthreads();
+    }
+}
+
 // out[:, k] = V[:, perm k] (column-major)
 __global__ void k_gather_cols(const double* __restrict__ V, int64_t n, const int* __restrict__ perm,
                               double* __restrict__ out) {
@@ -285,75 +488,104 @@ __global__ void k_gather_cols(const double* __restrict__ V, int64_t n, const int
     if (i < n) out[k * n + i] = V[(int64_t)perm[k] * n + i];
 }
 
-struct FsvdWs {
-    double *W, *V, *sig, *sig_sorted, *fhat, *curve, *d, *sperp;
-    int *perm, *r, *rot;
-    unsigned* bar;
-};
-
-size_t fsvd_ws_bytes(int64_t n, int G, int bar_k, int J) {
-    return 2 * ws_align((size_t)n * n * 8) + 5 * ws_align((size_t)n * 8) + ws_align((size_t)(J > n ? J : n) * 8) +
-           ws_align(8) + ws_align((size_t)n * 4) + ws_align(4) + ws_align((size_t)G * 4) +
-           ws_align((size_t)(bar_k + 2) * BAR_STRIDE * 4) + 4096;
+// out[:, k] = U~[0..n-1, k] (drop the last row of U~, ld n+1 -> n)
+__global__ void k_copy_ut(const double* __restrict__ Ut, int64_t n, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = blockIdx.y;
+    if (i < n) out[k * n + i] = Ut[k * (n + 1) + i];
 }
 
-// The SVD itself: W, V, sig_sorted, perm, fhat (when f given), r, s_perp.
-rbf_status fsvd_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, FsvdWs* out, int* sweeps_out) {
-    const int64_t n = op->n;
-    if (op->storage != RBF_ASSEMBLED || op->precision != RBF_FP64 || !op->d_A)
-        return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "the full SVD needs an assembled FP64 operator");
-    if (n < 2 || n > 8192) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "full SVD for 2 <= n <= 8192 (n = %lld)",
-                                           (long long)n);
+constexpr int64_t TGK_MAX_N = 1023;
+
+// Result of either path.
+struct Fsvd {
+    bool tgk;
+    int64_t n;
+    double *sig, *fhat, *d, *curve, *sperp;
+    int* r;
+    // Jacobi
+    double *W, *V;
+    int* perm;
+    // bidiagonalization
+    double *Wb, *taur, *scaler, *Vt, *Ut;
+    int sweeps;
+};
+
+int coop_grid(rbf_ctx* ctx, const void* kernel, int threads, int cap, int* group, int* bar_k) {
     int occ = 0;
-    RBF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jacobi_sweep, JT, 0));
-    const int np = (int)(n + (n & 1));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 1;
+    }
     int G = ctx->sm_count * (occ < 1 ? 1 : occ);
-    if (G > np / 2) G = np / 2;
-    int group = 1;
-    while (group * group < G) ++group;
-    const int bar_k = (G + group - 1) / group;
-    const int J = ctx->opt.grid_j;
-    RBF_TRY(rbf_ws_reserve(ctx, fsvd_ws_bytes(n, G, bar_k, J)));
-    WsCarve wc(ctx->ws);
-    FsvdWs w;
-    w.W = wc.take<double>((size_t)n * n);
-    w.V = wc.take<double>((size_t)n * n);
-    w.sig = wc.take<double>((size_t)n);
-    w.sig_sorted = wc.take<double>((size_t)n);
-    w.fhat = wc.take<double>((size_t)n);
-    w.d = wc.take<double>((size_t)n);
-    w.curve = wc.take<double>((size_t)(J > n ? J : n));
-    w.sperp = wc.take<double>(1);
-    w.perm = wc.take<int>((size_t)n);
-    w.r = wc.take<int>(1);
-    w.rot = wc.take<int>((size_t)G);
-    w.bar = wc.take<unsigned>((size_t)(bar_k + 2) * BAR_STRIDE);
+    if (G > cap) G = cap;
+    if (G < 1) G = 1;
+    int gr = 1;
+    while (gr * gr < G) ++gr;
+    *group = gr;
+    *bar_k = (G + gr - 1) / gr;
+    return G;
+}
+
+rbf_status fsvd_common_tail(rbf_ctx* ctx, Fsvd* F, const double* f) {
     cudaStream_t s = ctx->stream;
-    RBF_CUDA(ctx, cudaMemsetAsync(w.bar, 0, (size_t)(bar_k + 2) * BAR_STRIDE * sizeof(unsigned), s));
-    RBF_CUDA(ctx, cudaMemsetAsync(&ctx->d_state->info[IN_ERR], 0, sizeof(int), s));
-    RBF_CUDA(ctx, cudaMemsetAsync(&ctx->d_state->info[IN_DONE], 0, sizeof(int), s));
+    if (f) {
+        k_fsvd_rank<<<1, 32, 0, s>>>(F->sig, F->fhat, F->n, F->r, F->sperp);
+        RBF_LAUNCHED(ctx, "k_fsvd_rank");
+    }
+    return RBF_OK;
+}
+
+// Jacobi path (any 2 <= n <= 8192)
+rbf_status fsvd_jacobi(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fsvd* F) {
+    const int64_t n = op->n;
+    const int np = (int)(n + (n & 1));
+    int group, bar_k;
+    const int G = coop_grid(ctx, (const void*)k_jacobi_sweep, JT, np / 2, &group, &bar_k);
+    const int J = ctx->opt.grid_j;
+    const size_t need = 2 * ws_align((size_t)n * n * 8) + 5 * ws_align((size_t)n * 8) +
+                        ws_align((size_t)(J > n ? J : n) * 8) + ws_align(8) + ws_align((size_t)n * 4) + ws_align(4) +
+                        ws_align((size_t)G * 4) + ws_align((size_t)(bar_k + 2) * BAR_STRIDE * 4) + 4096;
+    RBF_TRY(rbf_ws_reserve(ctx, need));
+    WsCarve wc(ctx->ws);
+    F->tgk = false;
+    F->n = n;
+    F->W = wc.take<double>((size_t)n * n);
+    F->V = wc.take<double>((size_t)n * n);
+    double* sig_raw = wc.take<double>((size_t)n);
+    F->sig = wc.take<double>((size_t)n);
+    F->fhat = wc.take<double>((size_t)n);
+    F->d = wc.take<double>((size_t)n);
+    F->curve = wc.take<double>((size_t)(J > n ? J : n));
+    F->sperp = wc.take<double>(1);
+    F->perm = wc.take<int>((size_t)n);
+    F->r = wc.take<int>(1);
+    int* rotc = wc.take<int>((size_t)G);
+    unsigned* bar = wc.take<unsigned>((size_t)(bar_k + 2) * BAR_STRIDE);
+    cudaStream_t s = ctx->stream;
+    RBF_CUDA(ctx, cudaMemsetAsync(bar, 0, (size_t)(bar_k + 2) * BAR_STRIDE * sizeof(unsigned), s));
+    RBF_CUDA(ctx, cudaMemsetAsync(&ctx->d_state->info[IN_ERR], 0, 2 * sizeof(int), s));  // IN_DONE, IN_ERR
     dim3 tb(32, 8), tg((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
-    k_fsvd_init<<<tg, tb, 0, s>>>((const double*)op->d_A, op->lda, n, w.W, w.V);
+    k_fsvd_init<<<tg, tb, 0, s>>>((const double*)op->d_A, op->lda, n, F->W, F->V);
     RBF_LAUNCHED(ctx, "k_fsvd_init");
-    const double tol = 8.0 * DBL_EPSILON;
+    double tol = sqrt((double)n) * DBL_EPSILON;
     long long budget = 1LL << 23;
     std::vector<int> rot((size_t)G);
     int sweeps = 0;
     for (; sweeps < MAX_SWEEPS; ++sweeps) {
-        double* Wp = w.W;
-        double* Vp = w.V;
+        double* Wp = F->W;
+        double* Vp = F->V;
         int64_t nn = n;
         int npp = np;
-        double tl = tol;
         rbf_dev_state* stt = ctx->d_state;
-        unsigned* bar = w.bar;
         int grp = group;
-        int* rp = w.rot;
-        void* args[] = {&Wp, &Vp, &nn, &npp, &tl, &stt, &bar, &grp, &budget, &rp};
+        int* rp = rotc;
+        unsigned* bp = bar;
+        void* args[] = {&Wp, &Vp, &nn, &npp, &tol, &stt, &bp, &grp, &budget, &rp};
         RBF_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_jacobi_sweep, dim3(G), dim3(JT), args, 0, s));
         ctx->launches++;
         int err = 0;
-        RBF_CUDA(ctx, cudaMemcpyAsync(rot.data(), w.rot, sizeof(int) * G, cudaMemcpyDeviceToHost, s));
+        RBF_CUDA(ctx, cudaMemcpyAsync(rot.data(), rotc, sizeof(int) * G, cudaMemcpyDeviceToHost, s));
         RBF_CUDA(ctx, cudaMemcpyAsync(&err, &ctx->d_state->info[IN_ERR], sizeof(int), cudaMemcpyDeviceToHost, s));
         RBF_CUDA(ctx, cudaStreamSynchronize(s));
         if (err) return rbf_fail(ctx, (rbf_status)err, "a bounded grid barrier of the Jacobi sweep gave up");
@@ -364,18 +596,115 @@ rbf_status fsvd_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, FsvdW
             break;
         }
     }
-    k_colnorm<<<(unsigned)n, JT, 0, s>>>(w.W, n, w.sig);
+    F->sweeps = sweeps;
+    k_colnorm<<<(unsigned)n, JT, 0, s>>>(F->W, n, sig_raw);
     RBF_LAUNCHED(ctx, "k_colnorm");
-    k_sort_rank<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w.sig, n, w.perm, w.sig_sorted);
+    k_sort_rank<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(sig_raw, n, F->perm, F->sig);
     RBF_LAUNCHED(ctx, "k_sort_rank");
     if (f) {
-        k_fhat<<<(unsigned)n, JT, 0, s>>>(w.W, n, w.perm, w.sig_sorted, f, w.fhat);
+        k_fhat<<<(unsigned)n, JT, 0, s>>>(F->W, n, F->perm, F->sig, f, F->fhat);
         RBF_LAUNCHED(ctx, "k_fhat");
-        k_fsvd_rank<<<1, 32, 0, s>>>(w.sig_sorted, w.fhat, n, w.r, w.sperp);
-        RBF_LAUNCHED(ctx, "k_fsvd_rank");
     }
-    *out = w;
-    if (sweeps_out) *sweeps_out = sweeps;
+    return fsvd_common_tail(ctx, F, f);
+}
+
+// Bidiagonalization path (n <= 1023)
+rbf_status fsvd_bidiag(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fsvd* F) {
+    const int64_t n = op->n;
+    int group, bar_k;
+    const int G = coop_grid(ctx, (const void*)k_bidiag, BT, ctx->sm_count, &group, &bar_k);
+    const int J = ctx->opt.grid_j;
+    const int L = (int)n;
+    const size_t need = ws_align((size_t)n * (n + 1) * 8) + ws_align((size_t)n * n * 8) +
+                        ws_align((size_t)(n + 1) * n * 8) + 8 * ws_align((size_t)(n + 2) * 8) +
+                        ws_align((size_t)(J > n ? J : n) * 8) + ws_align(8) + ws_align(4) +
+                        ws_align((size_t)(bar_k + 2) * BAR_STRIDE * 4) + svd_ws_bytes(L) + 4096;
+    RBF_TRY(rbf_ws_reserve(ctx, need));
+    WsCarve wc(ctx->ws);
+    F->tgk = true;
+    F->n = n;
+    F->sweeps = 0;
+    F->Wb = wc.take<double>((size_t)n * (n + 1));
+    F->Vt = wc.take<double>((size_t)n * n);
+    F->Ut = wc.take<double>((size_t)(n + 1) * n);
+    double* dg = wc.take<double>((size_t)n + 2);
+    double* eg = wc.take<double>((size_t)n + 2);
+    F->taur = wc.take<double>((size_t)n + 2);
+    F->scaler = wc.take<double>((size_t)n + 2);
+    double* alpha = wc.take<double>((size_t)n + 2);
+    double* beta = wc.take<double>((size_t)n + 2);
+    double* ftil = wc.take<double>((size_t)n + 2);
+    F->sig = wc.take<double>((size_t)n + 2);
+    F->fhat = wc.take<double>((size_t)n + 2);
+    F->d = wc.take<double>((size_t)n + 2);
+    F->curve = wc.take<double>((size_t)(J > n ? J : n));
+    F->sperp = wc.take<double>(1);
+    F->r = wc.take<int>(1);
+    unsigned* bar = wc.take<unsigned>((size_t)(bar_k + 2) * BAR_STRIDE);
+    void* svd = (void*)wc.take<char>(svd_ws_bytes(L));
+    cudaStream_t s = ctx->stream;
+    RBF_CUDA(ctx, cudaMemsetAsync(bar, 0, (size_t)(bar_k + 2) * BAR_STRIDE * sizeof(unsigned), s));
+    RBF_CUDA(ctx, cudaMemsetAsync(&ctx->d_state->info[IN_ERR], 0, 2 * sizeof(int), s));
+    RBF_CUDA(ctx, cudaMemsetAsync(F->taur, 0, sizeof(double) * (n + 2), s));
+    // W = [A f] column-major (V is only a scratch target of the init kernel here)
+    dim3 tb(32, 8), tg((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+    k_fsvd_init<<<tg, tb, 0, s>>>((const double*)op->d_A, op->lda, n, F->Wb, F->Vt);
+    RBF_LAUNCHED(ctx, "k_fsvd_init");
+    if (f) RBF_CUDA(ctx, cudaMemcpyAsync(F->Wb + n * n, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else RBF_CUDA(ctx, cudaMemsetAsync(F->Wb + n * n, 0, sizeof(double) * n, s));
+    {
+        double* Wp = F->Wb;
+        int64_t nn = n;
+        double* dp = dg;
+        double* ep = eg;
+        double* tp = F->taur;
+        double* sp = F->scaler;
+        rbf_dev_state* stt = ctx->d_state;
+        unsigned* bp = bar;
+        int grp = group;
+        long long budget = 1LL << 23;
+        void* args[] = {&Wp, &nn, &dp, &ep, &tp, &sp, &stt, &bp, &grp, &budget};
+        RBF_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_bidiag, dim3(G), dim3(BT), args, 0, s));
+        ctx->launches++;
+    }
+    int err = 0;
+    RBF_CUDA(ctx, cudaMemcpyAsync(&err, &ctx->d_state->info[IN_ERR], sizeof(int), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(ctx, cudaStreamSynchronize(s));
+    if (err) return rbf_fail(ctx, (rbf_status)err, "a bounded grid barrier of the bidiagonalization gave up");
+    k_bidiag_ab<<<(unsigned)((n + 256) / 256), 256, 0, s>>>(dg, eg, n, alpha, beta);
+    RBF_LAUNCHED(ctx, "k_bidiag_ab");
+    ProjDims dd{1, L, L, nullptr};
+    RBF_TRY(launch_projected_svd_batch(ctx, dd, alpha, beta, F->sig, ftil, F->Vt, n, svd, nullptr, nullptr, F->Ut,
+                                       n + 1));
+    if (f) {
+        k_vt_g<<<(unsigned)n, BT, 0, s>>>(F->Vt, n, F->Wb + n * n, F->fhat);
+        RBF_LAUNCHED(ctx, "k_vt_g");
+    }
+    return fsvd_common_tail(ctx, F, f);
+}
+
+rbf_status fsvd_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fsvd* F) {
+    const int64_t n = op->n;
+    if (op->storage != RBF_ASSEMBLED || op->precision != RBF_FP64 || !op->d_A)
+        return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "the full SVD needs an assembled FP64 operator");
+    if (n < 2 || n > 8192)
+        return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "full SVD for 2 <= n <= 8192 (n = %lld)", (long long)n);
+    return n <= TGK_MAX_N ? fsvd_bidiag(ctx, op, f, F) : fsvd_jacobi(ctx, op, f, F);
+}
+
+// coef = V d
+rbf_status fsvd_lift(rbf_ctx* ctx, const Fsvd* F, double* coef) {
+    const int64_t n = F->n;
+    cudaStream_t s = ctx->stream;
+    if (!F->tgk) {
+        k_fsvd_lift<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(F->V, n, F->perm, F->d, coef);
+        RBF_LAUNCHED(ctx, "k_fsvd_lift");
+        return RBF_OK;
+    }
+    k_u_d<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(F->Ut, n, F->d, coef);
+    RBF_LAUNCHED(ctx, "k_u_d");
+    k_apply_qr<<<1, BT, 0, s>>>(F->Wb, n, F->taur, F->scaler, coef, n);
+    RBF_LAUNCHED(ctx, "k_apply_qr");
     return RBF_OK;
 }
 
@@ -393,17 +722,26 @@ extern "C" rbf_status rbf_svd_full(rbf_ctx* ctx, const rbf_operator* op, const d
                                    double* d_fhat, double* d_V, int* sweeps) {
     if (!ctx) return RBF_ERR_INVALID;
     if (!op || !d_sigma || (d_fhat && !d_f)) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_svd_full: bad argument");
-    FsvdWs w;
-    RBF_TRY(fsvd_run(ctx, op, d_fhat ? d_f : nullptr, &w, sweeps));
+    Fsvd F;
+    RBF_TRY(fsvd_run(ctx, op, d_fhat ? d_f : nullptr, &F));
     const int64_t n = op->n;
     cudaStream_t s = ctx->stream;
-    RBF_CUDA(ctx, cudaMemcpyAsync(d_sigma, w.sig_sorted, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    if (d_fhat) RBF_CUDA(ctx, cudaMemcpyAsync(d_fhat, w.fhat, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    RBF_CUDA(ctx, cudaMemcpyAsync(d_sigma, F.sig, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (d_fhat) RBF_CUDA(ctx, cudaMemcpyAsync(d_fhat, F.fhat, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     if (d_V) {
-        k_gather_cols<<<dim3((unsigned)((n + 255) / 256), (unsigned)n), 256, 0, s>>>(w.V, n, w.perm, d_V);
-        RBF_LAUNCHED(ctx, "k_gather_cols");
+        if (F.tgk) {
+            k_copy_ut<<<dim3((unsigned)((n + 255) / 256), (unsigned)n), 256, 0, s>>>(F.Ut, n, d_V);
+            RBF_LAUNCHED(ctx, "k_copy_ut");
+            k_apply_qr<<<(unsigned)n, BT, 0, s>>>(F.Wb, n, F.taur, F.scaler, d_V, n);
+            RBF_LAUNCHED(ctx, "k_apply_qr");
+        } else {
+            k_gather_cols<<<dim3((unsigned)((n + 255) / 256), (unsigned)n), 256, 0, s>>>(F.V, n, F.perm, d_V);
+            RBF_LAUNCHED(ctx, "k_gather_cols");
+        }
     }
+    if (sweeps) *sweeps = F.sweeps;
     RBF_CUDA(ctx, cudaStreamSynchronize(s));
+    RBF_CUDA(ctx, cudaGetLastError());
     return RBF_OK;
 }
 
@@ -413,30 +751,28 @@ extern "C" rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const d
     if (!op || !d_f || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_tikhonov: NULL argument");
     if (rule != RBF_GCV && rule != RBF_FIXED) return rbf_fail(ctx, RBF_ERR_INVALID, "rule must be RBF_GCV or RBF_FIXED");
     if (rule == RBF_FIXED && !(lambda_in >= 0.0)) return rbf_fail(ctx, RBF_ERR_INVALID, "fixed lambda must be >= 0");
-    FsvdWs w;
-    int sweeps = 0;
-    RBF_TRY(fsvd_run(ctx, op, d_f, &w, &sweeps));
+    Fsvd F;
+    RBF_TRY(fsvd_run(ctx, op, d_f, &F));
     const int64_t n = op->n;
     const int J = ctx->opt.grid_j;
     cudaStream_t s = ctx->stream;
     const double tlo = ctx->opt.grid_t_lo, thi = ctx->opt.grid_t_hi;
     if (rule == RBF_GCV) {
-        k_fsvd_gcv<<<(J + 127) / 128, 128, 0, s>>>(w.sig_sorted, w.fhat, n, w.r, w.sperp, J, tlo, thi, w.curve);
+        k_fsvd_gcv<<<(J + 127) / 128, 128, 0, s>>>(F.sig, F.fhat, n, F.r, F.sperp, J, tlo, thi, F.curve);
         RBF_LAUNCHED(ctx, "k_fsvd_gcv");
     }
-    k_fsvd_choose<<<1, 1024, 0, s>>>(w.curve, J, 0, rule == RBF_FIXED, lambda_in, 0, w.sig_sorted, w.fhat, w.r, J,
-                                      tlo, thi, w.d, n, ctx->d_state);
+    k_fsvd_choose<<<1, 1024, 0, s>>>(F.curve, J, 0, rule == RBF_FIXED, lambda_in, 0, F.sig, F.fhat, F.r, J, tlo, thi,
+                                      F.d, n, ctx->d_state);
     RBF_LAUNCHED(ctx, "k_fsvd_choose");
-    k_fsvd_lift<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w.V, n, w.perm, w.d, d_coef);
-    RBF_LAUNCHED(ctx, "k_fsvd_lift");
+    RBF_TRY(fsvd_lift(ctx, &F, d_coef));
     int r = 0;
-    RBF_CUDA(ctx, cudaMemcpyAsync(&r, w.r, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(ctx, cudaMemcpyAsync(&r, F.r, sizeof(int), cudaMemcpyDeviceToHost, s));
     RBF_TRY(read_state(ctx));
     if (info) {
         info->lambda = ctx->h_state->scal[SC_LAMBDA];
         info->index = ctx->h_state->info[IN_INDEX];
         info->rank = r;
-        info->steps = sweeps;
+        info->steps = F.sweeps;
         info->sigma1 = ctx->h_state->scal[SC_SIGMA1];
         info->eta = 0.0;
         info->rho = 0.0;
@@ -449,31 +785,29 @@ extern "C" rbf_status rbf_tsvd(rbf_ctx* ctx, const rbf_operator* op, const doubl
     if (!ctx) return RBF_ERR_INVALID;
     if (!op || !d_f || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_tsvd: NULL argument");
     if (rank < 0 || rank > op->n) return rbf_fail(ctx, RBF_ERR_INVALID, "rank %d outside [0, n]", rank);
-    FsvdWs w;
-    int sweeps = 0;
-    RBF_TRY(fsvd_run(ctx, op, d_f, &w, &sweeps));
+    Fsvd F;
+    RBF_TRY(fsvd_run(ctx, op, d_f, &F));
     const int64_t n = op->n;
     cudaStream_t s = ctx->stream;
     if (rank == 0) {
-        k_fsvd_gcv_rank<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w.fhat, n, w.r, w.sperp, w.curve);
+        k_fsvd_gcv_rank<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(F.fhat, n, F.r, F.sperp, F.curve);
         RBF_LAUNCHED(ctx, "k_fsvd_gcv_rank");
     }
     int r = 0;
-    RBF_CUDA(ctx, cudaMemcpyAsync(&r, w.r, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(ctx, cudaMemcpyAsync(&r, F.r, sizeof(int), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(ctx, cudaStreamSynchronize(s));
     const int kmax = (int)(r < n - 1 ? r : n - 1);
     if (rank == 0 && kmax < 1) return rbf_fail(ctx, RBF_ERR_INVALID, "numerical rank 0: no TSVD solution");
-    k_fsvd_choose<<<1, 1024, 0, s>>>(w.curve, kmax, 1, rank != 0, 0.0, rank, w.sig_sorted, w.fhat, w.r,
-                                      ctx->opt.grid_j, ctx->opt.grid_t_lo, ctx->opt.grid_t_hi, w.d, n, ctx->d_state);
+    k_fsvd_choose<<<1, 1024, 0, s>>>(F.curve, kmax, 1, rank != 0, 0.0, rank, F.sig, F.fhat, F.r, ctx->opt.grid_j,
+                                      ctx->opt.grid_t_lo, ctx->opt.grid_t_hi, F.d, n, ctx->d_state);
     RBF_LAUNCHED(ctx, "k_fsvd_choose");
-    k_fsvd_lift<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(w.V, n, w.perm, w.d, d_coef);
-    RBF_LAUNCHED(ctx, "k_fsvd_lift");
+    RBF_TRY(fsvd_lift(ctx, &F, d_coef));
     RBF_TRY(read_state(ctx));
     if (info) {
         info->lambda = 0.0;
         info->index = -1;
         info->rank = ctx->h_state->info[IN_RANK];
-        info->steps = sweeps;
+        info->steps = F.sweeps;
         info->sigma1 = ctx->h_state->scal[SC_SIGMA1];
         info->eta = 0.0;
         info->rho = 0.0;

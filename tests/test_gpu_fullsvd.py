@@ -56,7 +56,7 @@ def test_small_svd_exact(ctx, R, n):
     fh = torch.empty(n, dtype=torch.float64, device="cuda")
     V = torch.empty((n, n), dtype=torch.float64, device="cuda")  # row k = v_k
     sweeps = ctx.rbf_svd_full(op, sig, torch.as_tensor(f, device="cuda"), fh, V)
-    assert 1 <= sweeps <= 40
+    assert 0 <= sweeps <= 40  # 0: the bidiagonalization path (n <= 1023)
     s_ref = np.linalg.svd(A, compute_uv=False)
     s = sig.cpu().numpy()
     assert np.max(np.abs(s - s_ref)) <= 1e-13 * s_ref[0]
@@ -107,6 +107,28 @@ def test_cube1000_tikhonov_and_tsvd_against_oracle(ctx, R):
     ctx.rbf_tsvd(op, fd, ts["rank"], coef)
     tol = max(1e-10, 1e3 * n * EPS * fs.sigma[0] / fs.sigma[ts["rank"] - 1])
     assert np.linalg.norm(coef.cpu().numpy() - ts["coef"]) <= tol * np.linalg.norm(ts["coef"]), tol
+
+
+def test_jacobi_path_above_1023(ctx, R):
+    """n > 1023 takes the one-sided Jacobi path: singular values and the
+    Tikhonov solution at a fixed lambda against the oracle."""
+    n = 1100
+    rng = np.random.Generator(np.random.PCG64(77))
+    ns = w.cube_faces_random(n, 0.3, rng)
+    op = _op(ctx, R, ns, 0.5, 2.0)
+    A = OM.assemble(ns.X, ns.n_interior, 0.5, 2.0)
+    f = w.plane_wave_rhs(ns, 2.0)
+    fs = OR.full_svd(A, f)
+    sig = torch.empty(n, dtype=torch.float64, device="cuda")
+    sweeps = ctx.rbf_svd_full(op, sig)
+    assert 1 <= sweeps <= 40
+    assert np.max(np.abs(sig.cpu().numpy() - fs.sigma)) <= 1e-12 * fs.sigma[0]
+    lam = 1e-8 * fs.sigma[0]
+    tk = OR.tikhonov_full(A, f, "fixed", lam=lam, fs=fs)
+    coef = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.rbf_tikhonov(op, torch.as_tensor(f, device="cuda"), R.RBF_FIXED, lam, coef)
+    tol = max(1e-10, 1e3 * n * EPS * fs.sigma[0] / lam)
+    assert np.linalg.norm(coef.cpu().numpy() - tk["coef"]) <= tol * np.linalg.norm(tk["coef"])
 
 
 def test_full_svd_rejects_other_operators(ctx, R):
