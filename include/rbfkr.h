@@ -88,6 +88,8 @@ typedef struct {
     int timing;              /* bit 0: per-phase CUDA-event timings (synchronises at
                                 each phase end); bit 1: time every GKB product launch
                                 with CUDA events, no synchronisation (rbf_counters) */
+    int svd_method;          /* full SVD: 0 Householder bidiagonalization + tridiagonal
+                                SVD (default), 1 one-sided Jacobi */
 } rbf_options;
 
 /* Operator description; filled by rbf_operator_init. */
@@ -250,11 +252,13 @@ rbf_status rbf_lsqr(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, int k_fixed
                     double* d_curve, rbf_solve_info* info);
 
 /* Full SVD of an assembled FP64 operator (Algorithm 3 step 1), 2 <= n <=
- * 8192, by one-sided Jacobi: d_sigma[n] receives the singular values in
+ * 8192, by Householder bidiagonalization and the tridiagonal SVD of the
+ * bidiagonal (opt.svd_method 0) or one-sided Jacobi (1; *sweeps = number of
+ * sweeps, 0 for the first method): d_sigma[n] receives the singular values in
  * descending order; with d_f given, d_fhat[n] receives f^ = U^T f; d_V
  * (optional, n x n column-major) the right singular vectors in the same order.
- * *sweeps (optional) receives the number of Jacobi sweeps.  Uses 2 n^2 doubles
- * of workspace.  Synchronises.  RBF_ERR_UNSUPPORTED for other operators. */
+ * Workspace: about 3 n^2 doubles plus 8 n^2 (bidiagonal path) or 2 n^2
+ * (Jacobi).  Synchronises.  RBF_ERR_UNSUPPORTED for other operators. */
 rbf_status rbf_svd_full(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, double* d_sigma,
                         double* d_fhat, double* d_V, int* sweeps);
 
@@ -263,7 +267,7 @@ rbf_status rbf_svd_full(rbf_ctx* ctx, const rbf_operator* op, const double* d_f,
  * r = #{s_i > N eps s_1}, s_perp = sum_{i>r} f^_i^2) or fixed (RBF_FIXED);
  * d_coef[n] = sum_{i<=r} phi_i / s_i f^_i v_i (eq. tikh_svd_solution).
  * Assembled FP64 operators, n <= 8192.  Synchronises; info: lambda, index,
- * rank = r, steps = Jacobi sweeps, sigma1. */
+ * rank = r, steps = Jacobi sweeps (0 on the bidiagonal path), sigma1. */
 rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int rule,
                         double lambda_in, double* d_coef, rbf_solve_info* info);
 

@@ -32,6 +32,7 @@
 namespace {
 
 constexpr int BS_WARPS = 4;
+constexpr int SVD_MAX_L = 8192;  // bidiagonal dimension (shared memory: 2 L doubles)
 
 __device__ __forceinline__ int proj_l(const ProjDims& d, int b) { return d.l_arr ? d.l_arr[b] : d.l; }
 
@@ -106,11 +107,10 @@ __global__ void k_tgk_bisect(ProjDims d, const double* __restrict__ alpha_all,
     const double* alpha = alpha_all + (size_t)b * d.L;
     const double* beta = beta_all + (size_t)b * (d.L + 1);
     double* sigma = sigma_all + (size_t)b * d.L;
-    double* e = sh;           // 2l
-    double* e2 = sh + 2 * l;  // 2l
+    double* e2 = sh;  // 2l: the normalised off-diagonal, squared in place
     double bound;
-    load_e(alpha, beta, l, e, &bound);
-    for (int k = threadIdx.x; k < 2 * l; k += blockDim.x) e2[k] = e[k] * e[k];
+    load_e(alpha, beta, l, e2, &bound);
+    for (int k = threadIdx.x; k < 2 * l; k += blockDim.x) e2[k] = e2[k] * e2[k];
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) bound_all[b] = bound;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -213,8 +213,7 @@ constexpr int CL_MAX = 32;
 
 __global__ void k_tgk_clusters(ProjDims d, const double* __restrict__ sigma_all, double tol,
                                const double* __restrict__ invdp_all, const double* __restrict__ rp_all,
-                               double* __restrict__ X_all, double* __restrict__ tmp_all) {
-    __shared__ int cl_start[512], cl_end[512];
+                               double* __restrict__ X_all, double* __restrict__ tmp_all, int* __restrict__ cl_all) {
     __shared__ int ncl;
     const int b = blockIdx.x;
     const int l = proj_l(d, b);
@@ -226,13 +225,15 @@ __global__ void k_tgk_clusters(ProjDims d, const double* __restrict__ sigma_all,
     const double* rp = rp_all + sc;
     double* X = X_all + sc;
     double* tmp = tmp_all + (size_t)b * CL_WARPS * CL_MAX * NT;
+    int* cl_start = cl_all + (size_t)b * (L + 2);  // at most l/2 clusters of >= 2 members
+    int* cl_end = cl_start + L / 2 + 1;
     if (threadIdx.x == 0) {
         int c = 0;
         int i = 0;
         while (i < l) {
             int j = i;
             while (j + 1 < l && j - i + 1 < CL_MAX && fabs(sigma[j] - sigma[j + 1]) < tol * sigma[j]) ++j;
-            if (j > i && c < 512) {
+            if (j > i) {
                 cl_start[c] = i;
                 cl_end[c] = j;
                 ++c;
@@ -295,7 +296,7 @@ __global__ void k_tgk_finalize(ProjDims d, const double* __restrict__ alpha_all,
                                rbf_dev_state* __restrict__ stt, const double* __restrict__ sigma_all,
                                double* __restrict__ sigma1_out, double* __restrict__ ftil_last_out,
                                double* __restrict__ U_all, int64_t ldu) {
-    __shared__ double Ls[1024];
+    extern __shared__ double Ls[];  // l + 1
     __shared__ double red[32];
     const int b = blockIdx.x;
     const int l = proj_l(d, b);
@@ -334,7 +335,7 @@ __global__ void k_tgk_finalize(ProjDims d, const double* __restrict__ alpha_all,
         Ls[j] = (j == 0 || zero_tail) ? 0.0 : log(alpha[j - 1]) - log(beta[j]);
     __syncthreads();
     if (threadIdx.x == 0) {
-        // sequential prefix sums (l <= 1023 additions) and log-sum-exp
+        // sequential prefix sums (l additions) and log-sum-exp
         double acc = 0.0, mx = 0.0;
         for (int j = 0; j <= l; ++j) {
             acc += Ls[j];
@@ -375,6 +376,7 @@ size_t svd_ws_bytes_batch(int L, int B) {
     b += 4 * ws_align(NT * L * 8 * B);            // X, invdp, rp, rm
     b += ws_align((size_t)CL_WARPS * CL_MAX * NT * 8 * B);
     b += ws_align((size_t)8 * B);
+    b += ws_align((size_t)(L + 2) * 4 * B);  // cluster bounds
     return b + 4096;
 }
 
@@ -382,7 +384,8 @@ rbf_status launch_projected_svd_batch(rbf_ctx* ctx, ProjDims d, const double* al
                                       double* sigma, double* ftil, double* V, int64_t ldv, void* ws,
                                       double* sigma1_out, double* ftil_last_out, double* U, int64_t ldu) {
     const int L = d.L, B = d.B;
-    if (L < 1 || L > 1023) return rbf_fail(ctx, RBF_ERR_INVALID, "projected dimension %d outside [1, 1023]", L);
+    if (L < 1 || L > SVD_MAX_L)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "bidiagonal dimension %d outside [1, %d]", L, SVD_MAX_L);
     const size_t NT = 2 * (size_t)L + 1;
     WsCarve wc(ws);
     double* X = wc.take<double>(NT * L * B);
@@ -391,17 +394,24 @@ rbf_status launch_projected_svd_batch(rbf_ctx* ctx, ProjDims d, const double* al
     double* rm = wc.take<double>(NT * L * B);
     double* tmp = wc.take<double>((size_t)CL_WARPS * CL_MAX * NT * B);
     double* bound = wc.take<double>((size_t)B);
+    int* cl = wc.take<int>((size_t)(L + 2) * B);
     cudaStream_t s = ctx->stream;
-    const size_t sh_b = 4 * (size_t)L * sizeof(double);
+    const size_t sh_b = 2 * (size_t)L * sizeof(double);  // also the vectors' e
+    const size_t sh_f = ((size_t)L + 1) * sizeof(double);
+    if (sh_b > 48 * 1024) {
+        RBF_CUDA(ctx, cudaFuncSetAttribute(k_tgk_bisect, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_b));
+        RBF_CUDA(ctx, cudaFuncSetAttribute(k_tgk_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_b));
+    }
+    if (sh_f > 48 * 1024)
+        RBF_CUDA(ctx, cudaFuncSetAttribute(k_tgk_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_f));
     k_tgk_bisect<<<dim3((L + BS_WARPS - 1) / BS_WARPS, B), BS_WARPS * 32, sh_b, s>>>(d, alpha, beta, sigma, bound);
     RBF_LAUNCHED(ctx, "k_tgk_bisect");
-    const size_t sh_v = 2 * (size_t)L * sizeof(double);
-    k_tgk_vectors<<<dim3((L + 31) / 32, B), 32, sh_v, s>>>(d, alpha, beta, sigma, bound, invdp, rp, rm, X);
+    k_tgk_vectors<<<dim3((L + 31) / 32, B), 32, sh_b, s>>>(d, alpha, beta, sigma, bound, invdp, rp, rm, X);
     RBF_LAUNCHED(ctx, "k_tgk_vectors");
-    k_tgk_clusters<<<B, CL_WARPS * 32, 0, s>>>(d, sigma, ctx->opt.cluster_tol, invdp, rp, X, tmp);
+    k_tgk_clusters<<<B, CL_WARPS * 32, 0, s>>>(d, sigma, ctx->opt.cluster_tol, invdp, rp, X, tmp, cl);
     RBF_LAUNCHED(ctx, "k_tgk_clusters");
-    k_tgk_finalize<<<B, 256, 0, s>>>(d, alpha, beta, X, ftil, V, ldv, B == 1 ? ctx->d_state : nullptr, sigma,
-                                     sigma1_out, ftil_last_out, U, ldu);
+    k_tgk_finalize<<<B, 256, sh_f, s>>>(d, alpha, beta, X, ftil, V, ldv, B == 1 ? ctx->d_state : nullptr, sigma,
+                                        sigma1_out, ftil_last_out, U, ldu);
     RBF_LAUNCHED(ctx, "k_tgk_finalize");
     return RBF_OK;
 }

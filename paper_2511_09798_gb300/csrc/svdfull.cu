@@ -2,7 +2,7 @@
 // the full-SVD methods on top of it: Tikhonov with GCV (Algorithm 3, eqs.
 // gcv_svd and tikh_svd_solution) and TSVD (eq. tsvd_solution).
 //
-// n <= 1023: Householder bidiagonalization A = Q_L B Q_R^T in one cooperative
+// Default: Householder bidiagonalization A = Q_L B Q_R^T in one cooperative
 // kernel (per step a left reflector on column k applied to the trailing
 // columns and to f, which rides along as an extra column so that g = Q_L^T f
 // comes out of the same pass, then a right reflector on row k applied to the
@@ -11,7 +11,8 @@
 // kernels with C = [B^T; 0]: sigma, V~ = U_B and U~ = V_B), f^ = V~^T g and
 // alpha = Q_R (U~ d).
 //
-// Larger n: one-sided (Hestenes) Jacobi: the columns of W = A are rotated in
+// Option svd_method = 1: one-sided (Hestenes) Jacobi (high relative accuracy
+// for small singular values, far more work): the columns of W = A are rotated in
 // pairs until they are mutually orthogonal (W = U Sigma, V = product of the
 // rotations).  One cooperative kernel per sweep: each round pairs the columns
 // by the circle method (n/2 disjoint pairs), one CTA per pair: the three dot
@@ -495,7 +496,7 @@ __global__ void k_copy_ut(const double* __restrict__ Ut, int64_t n, double* __re
     if (i < n) out[k * n + i] = Ut[k * (n + 1) + i];
 }
 
-constexpr int64_t TGK_MAX_N = 1023;
+constexpr int64_t TGK_MAX_N = 8192;
 
 // Result of either path.
 struct Fsvd {
@@ -536,7 +537,7 @@ rbf_status fsvd_common_tail(rbf_ctx* ctx, Fsvd* F, const double* f) {
     return RBF_OK;
 }
 
-// Jacobi path (any 2 <= n <= 8192)
+// Jacobi path
 rbf_status fsvd_jacobi(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fsvd* F) {
     const int64_t n = op->n;
     const int np = (int)(n + (n & 1));
@@ -608,7 +609,7 @@ rbf_status fsvd_jacobi(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fs
     return fsvd_common_tail(ctx, F, f);
 }
 
-// Bidiagonalization path (n <= 1023)
+// Bidiagonalization path
 rbf_status fsvd_bidiag(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fsvd* F) {
     const int64_t n = op->n;
     int group, bar_k;
@@ -689,7 +690,7 @@ rbf_status fsvd_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fsvd*
         return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "the full SVD needs an assembled FP64 operator");
     if (n < 2 || n > 8192)
         return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "full SVD for 2 <= n <= 8192 (n = %lld)", (long long)n);
-    return n <= TGK_MAX_N ? fsvd_bidiag(ctx, op, f, F) : fsvd_jacobi(ctx, op, f, F);
+    return (n <= TGK_MAX_N && ctx->opt.svd_method == 0) ? fsvd_bidiag(ctx, op, f, F) : fsvd_jacobi(ctx, op, f, F);
 }
 
 // coef = V d

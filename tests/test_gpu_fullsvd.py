@@ -109,9 +109,12 @@ def test_cube1000_tikhonov_and_tsvd_against_oracle(ctx, R):
     assert np.linalg.norm(coef.cpu().numpy() - ts["coef"]) <= tol * np.linalg.norm(ts["coef"]), tol
 
 
-def test_jacobi_path_above_1023(ctx, R):
-    """n > 1023 takes the one-sided Jacobi path: singular values and the
-    Tikhonov solution at a fixed lambda against the oracle."""
+@pytest.mark.parametrize("method", [0, 1])
+def test_both_methods_above_1023(R, method):
+    """n = 1100 by the bidiagonal path (method 0) and by one-sided Jacobi
+    (method 1): singular values and the Tikhonov solution at a fixed lambda
+    against the oracle."""
+    ctx = R.Context(0, svd_method=method)
     n = 1100
     rng = np.random.Generator(np.random.PCG64(77))
     ns = w.cube_faces_random(n, 0.3, rng)
@@ -121,7 +124,7 @@ def test_jacobi_path_above_1023(ctx, R):
     fs = OR.full_svd(A, f)
     sig = torch.empty(n, dtype=torch.float64, device="cuda")
     sweeps = ctx.rbf_svd_full(op, sig)
-    assert 1 <= sweeps <= 40
+    assert (sweeps == 0) if method == 0 else (1 <= sweeps <= 40)
     assert np.max(np.abs(sig.cpu().numpy() - fs.sigma)) <= 1e-12 * fs.sigma[0]
     lam = 1e-8 * fs.sigma[0]
     tk = OR.tikhonov_full(A, f, "fixed", lam=lam, fs=fs)
@@ -129,6 +132,7 @@ def test_jacobi_path_above_1023(ctx, R):
     ctx.rbf_tikhonov(op, torch.as_tensor(f, device="cuda"), R.RBF_FIXED, lam, coef)
     tol = max(1e-10, 1e3 * n * EPS * fs.sigma[0] / lam)
     assert np.linalg.norm(coef.cpu().numpy() - tk["coef"]) <= tol * np.linalg.norm(tk["coef"])
+    ctx.close()
 
 
 def test_full_svd_rejects_other_operators(ctx, R):
