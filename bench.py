@@ -67,6 +67,28 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "_fallback": True}
 
 
+def reduce_over_ranks(ms, work, device="cpu"):
+    """Whole-job figures of a replicated run: the slowest rank's time and the
+    work summed over ranks (one process per GPU; a no-op without a process
+    group).  The all-reduces run on `device` (CUDA tensors for NCCL, CPU
+    tensors for gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms), work
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    d = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(d, op=dist.ReduceOp.SUM)
+    return float(t.item()), (int(d.item()) if isinstance(work, int) else float(d.item()))
+
+
+def rank_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
 # --------------------------------------------------------------------------- workloads
 def workload(name):
     import numpy as np
@@ -209,8 +231,7 @@ def run_ours(args, rank, world, local_rank):
         return done
 
     def timed(k_steps, e2e):
-        if world > 1:
-            torch.distributed.barrier()
+        rank_barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -219,15 +240,7 @@ def run_ours(args, rank, world, local_rank):
             done += one_step(e2e)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-            d = torch.tensor([done], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(d)
-            done = int(d.item())
-        return ms, done
+        return reduce_over_ranks(e0.elapsed_time(e1), done, dev)
 
     for _ in range(args.warmup):
         one_step()
@@ -414,7 +427,8 @@ def run_batch(args, rank, world, local_rank):
     sampler = ClockSampler(local_rank) if rank == 0 else None
     if sampler:
         sampler.start()
-    t0 = time.perf_counter()
+    rank_barrier()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     steps_total = 0
@@ -426,8 +440,9 @@ def run_batch(args, rank, world, local_rank):
                        for b in range(len(inst)))
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms, instances_all = reduce_over_ranks(e0.elapsed_time(e1), len(inst) * args.steps, dev)
     clocks = sampler.stop() if sampler else None
+
     def errors():
         uh = u.cpu().numpy().reshape(len(inst), m)
         out = []
@@ -454,7 +469,7 @@ def run_batch(args, rank, world, local_rank):
     ctx.close()
     if rank != 0:
         return None
-    value = len(inst) * args.steps * world / (ms / 1e3)
+    value = instances_all / (ms / 1e3)
     name = "batch96-learned" if learned_arm else "batch96"
     return {"metric": ("batched learned-stop HKT instances/s (96 uneven instances, at most 150 GKB steps each)"
                        if learned_arm else "batched HKT instances/s (96 uneven instances, 150 GKB steps each)"),
@@ -535,20 +550,14 @@ def run_learned(args, rank, world, local_rank):
         return info.steps
 
     def timed(k_steps, e2e):
-        if world > 1:
-            torch.distributed.barrier()
+        rank_barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         done = sum(one_step(f_d, e2e) for _ in range(k_steps))
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, done
+        return reduce_over_ranks(e0.elapsed_time(e1), done, dev)
 
     for _ in range(args.warmup):
         one_step(f_d)
