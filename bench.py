@@ -645,6 +645,80 @@ def run_learned(args, rank, world, local_rank):
             "clocks": clocks}
 
 
+# --------------------------------------------------------------------------- paper-shaped sweep
+def run_paper_sweep(args, rank, world, local_rank):
+    """Stand-in for the accuracy tables of the cube and sphere examples (Sec.
+    5, Examples 1 and 2; their Gmsh nodes are not available): the Gaussian
+    exp(-|X - X0|^2 / 20) (X0 = 0 in the cube, (0.25, 0.25, 0) in the ball),
+    k = 3, c = 2 (the shape parameter is not printed; c = 2 gives kappa(A) of
+    the printed order at N = 359), random / uniform / Halton nodes at N ~ 359,
+    2154, 6511, FP64 assembled.  Per case: full-SVD Tikhonov with GCV
+    (Tikh-Rg), Ine-TSVD and HKT on 140 (cube) or 180 (sphere) GKB steps with
+    GCV, HKT with the L-curve, each timed on the device from the assembled
+    operator to u at 2000 points, with Re = max|u - u_exact| / max|u_exact|."""
+    import numpy as np
+    import torch
+
+    import workloads as w
+    from paper_2511_09798_gb300 import rbfkr as R
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    stream = torch.cuda.current_stream()
+    ctx = R.Context(local_rank, stream=stream)
+    c, k, sigma = 2.0, 3.0, 20.0
+    rows = []
+    t_all = 0.0
+    for dom, L, center in (("cube", 140, (0.0, 0.0, 0.0)), ("sphere", 180, (0.25, 0.25, 0.0))):
+        for dist in ("random", "uniform", "halton"):
+            for n_target in (359, 2154, 6511):
+                ns = w.paper_nodes(dom, dist, n_target, w.nodes.BASE_SEED + 700 + n_target)
+                n = ns.n
+                P = w.test_points(ns, 2000, seed=w.nodes.BASE_SEED + 1700 + n_target)
+                ue = w.gaussian(P, sigma, center)
+                f = torch.as_tensor(w.gaussian_rhs(ns, sigma, k, center), device=dev)
+                nodes = torch.as_tensor(ns.soa(), device=dev)
+                pts = torch.as_tensor(np.ascontiguousarray(P.T), device=dev)
+                lda = R.padded_lda(n, R.RBF_FP64)
+                A = torch.empty((n, lda), dtype=torch.float64, device=dev)
+                op = ctx.rbf_operator_init(nodes, n, ns.n_interior, c, k, R.RBF_ASSEMBLED, R.RBF_FP64, A=A, lda=lda)
+                st, *_ = R.make_state(torch, n, L, dev)
+                coef = torch.empty(n, dtype=torch.float64, device=dev)
+                u = torch.empty(2000, dtype=torch.float64, device=dev)
+                row = {"domain": dom, "nodes": dist, "n": n}
+
+                def timed(name, fn):
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ctx.rbf_assemble(op)
+                    fn()
+                    ctx.rbf_evaluate(op, coef, pts, 2000, u)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    err = float(np.max(np.abs(u.cpu().numpy() - ue)) / np.max(np.abs(ue)))
+                    row[name] = {"re": err, "ms": round(ms, 2)}
+                    return ms
+
+                t_all += timed("tikh_rg", lambda: ctx.rbf_tikhonov(op, f, R.RBF_GCV, 0.0, coef))
+                t_all += timed("ine_tsvd", lambda: (ctx.rbf_gkb(op, f, L, st), ctx.rbf_ine_tsvd(st, 0, coef)))
+                t_all += timed("hkt_gcv", lambda: (ctx.rbf_gkb(op, f, L, st), ctx.rbf_hkt(st, R.RBF_GCV, 0.0, coef)))
+                t_all += timed("hkt_lcurve",
+                               lambda: (ctx.rbf_gkb(op, f, L, st), ctx.rbf_hkt(st, R.RBF_LCURVE, 0.0, coef)))
+                rows.append(row)
+                del A, st, op
+    ctx.close()
+    if rank != 0:
+        return None
+    return {"metric": "paper-shaped accuracy sweep: Re and device time per method", "value": round(t_all / 1e3, 3),
+            "unit": "device seconds for the sweep", "n_gpus": world, "steps": 1, "warmup": 0,
+            "ms_per_step": round(t_all, 1), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper-sweep", "c": c, "k": k, "sigma": sigma,
+                       "gkb_steps": {"cube": 140, "sphere": 180}, "test_points": 2000},
+            "rows": rows}
+
+
 # --------------------------------------------------------------------------- oracle
 def oracle_solve(wl, c, k, steps):
     from oracle import evaluate as OE
@@ -755,6 +829,8 @@ def main():
         out = run_batch(args, rank, world, local_rank)
     elif args.workload == "pump40000-learned":
         out = run_learned(args, rank, world, local_rank)
+    elif args.workload == "paper-sweep":
+        out = run_paper_sweep(args, rank, world, local_rank)
     else:
         out = run_ours(args, rank, world, local_rank)
         if out is not None and not args.no_cpu_baseline:

@@ -54,3 +54,26 @@ def test_pump_like_small():
     assert np.all(inside("pump", ns.X[:1200]))
     P = w.test_points(ns, 200)
     assert np.all(inside("pump", P))
+
+
+def test_paper_shaped_node_sets():
+    import numpy as np
+    import workloads as w
+    for dom in ("cube", "sphere"):
+        for dist in ("random", "uniform", "halton"):
+            for n in (359, 2154):
+                ns = w.paper_nodes(dom, dist, n, 9798 + 7)
+                assert abs(ns.n - n) <= 0.06 * n, (dom, dist, n, ns.n)
+                X = ns.X
+                I, B = X[: ns.n_interior], X[ns.n_interior:]
+                if dom == "cube":
+                    assert np.all((I > 0) & (I < 1))
+                    assert np.all(np.any((B == 0) | (B == 1), axis=1))
+                else:
+                    assert np.all(np.sum(I * I, axis=1) < 1)
+                    assert np.allclose(np.sum(B * B, axis=1), 1.0)
+                assert len(np.unique(X.round(12), axis=0)) == ns.n
+    # seeded: the same seed gives the same set
+    a = w.paper_nodes("cube", "halton", 359, 5)
+    b = w.paper_nodes("cube", "halton", 359, 5)
+    assert np.array_equal(a.X, b.X)

@@ -14,6 +14,7 @@ from .nodes import (  # noqa: F401
     pump_like,
     batch_instances,
     stop_instances,
+    paper_nodes,
     test_points,
     scrambled_halton,
     fibonacci_sphere,

@@ -417,6 +417,85 @@ def stop_instances(count: int, n_lo: int, n_hi: int, seed0: int = BASE_SEED + 60
     return out
 
 
+def _lattice_boundary_share(n: int) -> float:
+    """Boundary share of an m^3 lattice with m^3 close to n: 1 - ((m-2)/m)^3."""
+    m = max(3, int(round(n ** (1.0 / 3.0))))
+    return 1.0 - ((m - 2) / m) ** 3
+
+
+def _cube_faces_points(nb: int, pts2d: np.ndarray) -> np.ndarray:
+    """nb points on the 6 faces of [0,1]^3 from 2D points in [0,1)^2, dealt to
+    the faces in turn (face f: coordinate f//2 fixed at f%2)."""
+    out = np.empty((nb, 3))
+    for i in range(nb):
+        f = i % 6
+        u, v = pts2d[i]
+        ax = f // 2
+        rest = [a for a in range(3) if a != ax]
+        out[i, ax] = float(f % 2)
+        out[i, rest[0]] = u
+        out[i, rest[1]] = v
+    return out
+
+
+def paper_nodes(domain: str, dist: str, n: int, seed: int) -> NodeSet:
+    """Node sets shaped like the cube and sphere examples (Sec. 5, Examples 1
+    and 2), whose Gmsh meshes are not available: 'random' (i.i.d. uniform),
+    'uniform' (a cubic lattice, clipped to the ball for the sphere, of about
+    n points) and 'halton' (scrambled Halton), with the boundary share of an
+    m^3 lattice (cube: nodes on the faces; sphere: a Fibonacci lattice on the
+    unit sphere).  Interior nodes first."""
+    rng = _rng(seed)
+    share = _lattice_boundary_share(n)
+    if domain == "cube":
+        if dist == "uniform":
+            m = max(3, int(round(n ** (1.0 / 3.0))))
+            g = np.linspace(0.0, 1.0, m)
+            P = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+            on_b = np.any((P == 0.0) | (P == 1.0), axis=1)
+            return NodeSet(np.ascontiguousarray(np.concatenate([P[~on_b], P[on_b]])), int((~on_b).sum()),
+                           "cube", f"cube_uniform{P.shape[0]}")
+        nb = int(round(share * n))
+        ni = n - nb
+        if dist == "random":
+            I = uniform_cube(ni, rng)
+            B = _cube_faces_points(nb, rng.uniform(0.0, 1.0, size=(nb, 2)))
+        elif dist == "halton":
+            I = scrambled_halton(ni, rng)
+            B = _cube_faces_points(nb, scrambled_halton(nb, rng, bases=(2, 3)))
+            I[(I == 0.0)] = 0.5
+        else:
+            raise ValueError(dist)
+        return NodeSet(np.ascontiguousarray(np.concatenate([I, B])), ni, "cube", f"cube_{dist}{n}")
+    if domain == "sphere":
+        nb = int(round(share * n))
+        ni = n - nb
+        if dist == "uniform":
+            h = (4.0 / 3.0 * math.pi / ni) ** (1.0 / 3.0)
+            for _ in range(8):  # lattice spacing giving about ni points inside r < 1 - h/2
+                g = np.arange(-1.0 + h / 2, 1.0, h)
+                P = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+                I = P[np.sum(P * P, axis=1) < (1.0 - 0.5 * h) ** 2]
+                h *= (I.shape[0] / ni) ** (1.0 / 3.0)
+        elif dist == "random":
+            I = uniform_ball(ni, rng)
+        elif dist == "halton":
+            out, have, skip = [], 0, 1
+            while have < ni:
+                H = 2.0 * scrambled_halton(2 * ni, _rng(seed + 1), skip=skip) - 1.0
+                skip += 2 * ni
+                H = H[np.sum(H * H, axis=1) < 1.0]
+                out.append(H)
+                have += H.shape[0]
+            I = np.concatenate(out)[:ni]
+        else:
+            raise ValueError(dist)
+        B = fibonacci_sphere(nb)
+        return NodeSet(np.ascontiguousarray(np.concatenate([I, B])), I.shape[0], "sphere",
+                       f"sphere_{dist}{I.shape[0] + nb}")
+    raise ValueError(domain)
+
+
 # ----------------------------------------------------------------------------
 # named workload presets
 # ----------------------------------------------------------------------------
