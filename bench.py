@@ -455,7 +455,7 @@ def run_batch(args, rank, world, local_rank):
     mean_steps = steps_total / (len(inst) * args.steps)
     tune = ctx.rbf_get_tuning()
     other = None
-    if learned_arm:  # the same batch with GCV-HKT at 150 steps, once, for comparison
+    if learned_arm:  # the same instances by the other forms, once each, for comparison
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record()
@@ -463,9 +463,42 @@ def run_batch(args, rank, world, local_rank):
         g1.record()
         torch.cuda.synchronize()
         eg = errors()
-        other = {"gcv_hkt_ms": round(g0.elapsed_time(g1), 2),
-                 "gcv_hkt_re_vs_exact": {"median": float(np.median(eg)), "max": float(np.max(eg))},
-                 "learned_err_not_worse_frac": float(np.mean(np.array(errs) <= 1.05 * np.array(eg)))}
+        other = {"mixed_batched_gcv_hkt": {"ms": round(g0.elapsed_time(g1), 2),
+                                           "re_median": float(np.median(eg)), "re_max": float(np.max(eg))},
+                 "learned_err_not_worse_than_batched_gcv_frac":
+                     float(np.mean(np.array(errs) <= 1.05 * np.array(eg)))}
+        for name, prec, storage in (("fp64_single_gcv_hkt", R.RBF_FP64, R.RBF_ASSEMBLED),
+                                    ("mixed_single_gcv_hkt", R.RBF_MIXED, R.RBF_MATRIX_FREE)):
+            ms_sum, es = 0.0, []
+            for b, s_ in enumerate(inst):
+                n_b = s_.n
+                nodes_b = torch.as_tensor(s_.soa(), device=dev)
+                f_b = torch.as_tensor(fs[b], device=dev)
+                P_b = torch.as_tensor(np.ascontiguousarray(pts[b].T), device=dev)
+                A_b, lda_b = None, 0
+                if storage == R.RBF_ASSEMBLED:
+                    lda_b = R.padded_lda(n_b, prec)
+                    A_b = torch.empty((n_b, lda_b), dtype=torch.float64, device=dev)
+                op_b = ctx.rbf_operator_init(nodes_b, n_b, s_.n_interior, s_.params["c"], s_.params["k"], storage,
+                                             prec, R.RBF_FORM_C, A_b, lda_b)
+                st_b, *_ = R.make_state(torch, n_b, L, dev)
+                c_b = torch.empty(n_b, dtype=torch.float64, device=dev)
+                u_b = torch.empty(m, dtype=torch.float64, device=dev)
+                torch.cuda.synchronize()
+                h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                h0.record()
+                if A_b is not None:
+                    ctx.rbf_assemble(op_b)
+                ctx.rbf_gkb(op_b, f_b, L, st_b)
+                ctx.rbf_hkt(st_b, R.RBF_GCV, 0.0, c_b)
+                ctx.rbf_evaluate(op_b, c_b, P_b, m, u_b)
+                h1.record()
+                torch.cuda.synchronize()
+                ms_sum += h0.elapsed_time(h1)
+                ue = w.plane_wave(pts[b], s_.params["k"], s_.params["d"])
+                es.append(float(np.max(np.abs(u_b.cpu().numpy() - ue)) / np.max(np.abs(ue))))
+                del A_b, op_b, st_b
+            other[name] = {"ms": round(ms_sum, 2), "re_median": float(np.median(es)), "re_max": float(np.max(es))}
     ctx.close()
     if rank != 0:
         return None
