@@ -39,6 +39,17 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # FP64 FMA pipe, max clock
 FP32_LANE_TOPS = 152 * 128 * 2.07e9 / 1e12  # FP32 pipe: one operation per lane per clock
 
 
+# DRAM bytes (read + write) per launch of the dominant product kernel, from one
+# ncu capture of that kernel at the workload's size (dram__bytes_read.sum +
+# dram__bytes_write.sum); None where the kernel changed after its capture.
+MEASURED_TRAFFIC = {
+    ("cube8000", 0): 512.700e6 + 3.319e6,                      # k_gemv_nseg_f64
+    ("cube8000", 1): 512.146e6 + 3.710e6,                      # k_gemv_t_f64
+    ("sphere20000-mixed-assembled", 0): 1600.665e6 + 4.324e6,  # k_gemv_nseg_f32
+    ("sphere20000-mixed-assembled", 1): 1600.146e6 + 3.266e6,  # k_gemv_t_f32
+}
+
+
 def mf_ops_per_entry(n, n_interior):
     """FP32 pipe operations per regenerated entry of the matrix-free product:
     3 differences, 3 FMA for s, then 5 for a PDE entry (rs^2, two FMA, one
@@ -297,6 +308,7 @@ def run_ours(args, rank, world, local_rank):
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
     else:
         roof = mf_roofline(n, ns.n_interior, avg_ms)
+    roof["traffic"] = MEASURED_TRAFFIC.get((wl["name"], dom))
     roof.update({"kernel": kinds[dom], "avg_launch_ms": round(avg_ms, 5),
                  "avg_launch_ms_both": round(both_avg_ms, 5), "launches_timed": int(p_cnt[0] + p_cnt[1]),
                  "algorithmic_per_launch": (f"{s * n * n} bytes, {2 * n * n} flop" if storage == R.RBF_ASSEMBLED

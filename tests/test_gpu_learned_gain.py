@@ -2,8 +2,8 @@
 
 A small network is trained on the GPU (the library's forward, backward and
 Adam kernels) on GKB runs the method generates, then compared on held-out
-runs with GCV-driven HKT at the full step count -- the fallback and the judge
-of its error -- and with L-curve HKT.  The learned stop must use fewer GKB
+runs with GCV-driven HKT at the full step count -- the fallback and the
+reference for its error -- and with L-curve HKT.  The learned stop must use fewer GKB
 steps and less time, with an error no worse than GCV-HKT's on most runs.
 """
 import math
