@@ -113,6 +113,10 @@ def workload(name):
         ns = w.preset("cube8000")
         cases = [(c, k) for c in (0.1, 0.2, 0.5) for k in (2.0, 5.0)]
         steps, prec, storage = 100, "fp64", "assembled"
+    elif name == "cube8000-fp64-mf":
+        ns = w.preset("cube8000")
+        cases = [(0.2, 5.0)]
+        steps, prec, storage = 100, "fp64", "matrix_free"
     elif name == "cube8000-mixed-mf":
         ns = w.preset("cube8000")
         cases = [(c, k) for c in (0.1, 0.2, 0.5) for k in (2.0, 5.0)]
@@ -306,6 +310,13 @@ def run_ours(args, rank, world, local_rank):
             roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                     "frac": round(gbs / peaks.get("hbm_gbs", 6790.7), 4), "traffic": None,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    elif prec == R.RBF_FP64:  # FP64 regeneration: ~16 FP64-pipe operations per entry
+        ent = n * n / (avg_ms / 1e3)
+        peak = 152 * 2 * 2.07e9 / 1e12
+        ops = ent * 16 / 1e12
+        roof = {"bound": "alu", "achieved": round(ops, 4), "peak": round(peak, 4), "unit": "T FP64-pipe ops/s",
+                "frac": round(ops / peak, 4), "traffic": None, "entries_per_s": ent, "ops_per_entry": 16,
+                "peak_source": "152 SMs x 2 FP64 ops/clk x 2.07 GHz (unit counts and max clock)"}
     else:
         roof = mf_roofline(n, ns.n_interior, avg_ms)
     roof["traffic"] = MEASURED_TRAFFIC.get((wl["name"], dom))

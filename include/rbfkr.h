@@ -59,7 +59,8 @@ typedef enum {
 
 typedef enum {
     RBF_ASSEMBLED = 0,   /* A stored densely (caller-owned buffer) */
-    RBF_MATRIX_FREE = 1  /* entries regenerated from node coordinates per product */
+    RBF_MATRIX_FREE = 1  /* entries regenerated from node coordinates per product
+                            (in FP32 for RBF_MIXED, in FP64 for RBF_FP64) */
 } rbf_storage;
 
 typedef enum {

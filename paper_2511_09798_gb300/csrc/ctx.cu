@@ -187,9 +187,6 @@ rbf_status rbf_operator_init(rbf_ctx* ctx, rbf_operator* op, const double* d_nod
         if (lda % vec != 0 || ((uintptr_t)d_A & 15u) != 0)
             return rbf_fail(ctx, RBF_ERR_INVALID,
                             "d_A must be 16-byte aligned and lda a multiple of %d elements", vec);
-    } else if (precision == RBF_FP64) {
-        return rbf_fail(ctx, RBF_ERR_UNSUPPORTED,
-                        "matrix-free operators regenerate entries in FP32: use RBF_MIXED");
     }
     op->d_nodes = d_nodes;
     op->n = n;

@@ -457,8 +457,8 @@ extern "C" rbf_status rbf_matvec(rbf_ctx* ctx, const rbf_operator* op, int trans
         WsCarve wc(ctx->ws);
         float* x32 = wc.take<float>((size_t)n);
         double* part = wc.take<double>((size_t)mf_chunks(ctx, op) * n);
-        RBF_TRY(launch_to_f32(ctx, n, d_x, x32));
-        RBF_TRY(launch_mf_partial(ctx, op, trans, x32, part, nullptr));
+        if (op->precision == RBF_MIXED) RBF_TRY(launch_to_f32(ctx, n, d_x, x32));
+        RBF_TRY(launch_mf_partial(ctx, op, trans, d_x, x32, part, nullptr));
         return launch_reduce_partials(ctx, n, mf_chunks(ctx, op), part, d_y);
     }
     RBF_TRY(rbf_ws_reserve(ctx, gemv_ws_bytes(ctx, n)));

@@ -123,11 +123,11 @@ rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, 
 rbf_status launch_gemv_t_partial(rbf_ctx* ctx, const rbf_operator* op, const double* x,
                                  const float* x32, double* part, const int* done);
 rbf_status launch_reduce_partials(rbf_ctx* ctx, int64_t n, int chunks, const double* part, double* y);
-// mf.cu (matrix-free FP32 products; partial sums over `mf_chunks` centre chunks)
+// mf.cu (matrix-free products, FP32 or FP64; partial sums over `mf_chunks` centre chunks)
 int mf_chunks(const rbf_ctx* ctx, const rbf_operator* op);
 size_t mf_ws_bytes(const rbf_ctx* ctx, int64_t n);
-rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, const float* x32,
-                             double* part, const int* done);
+rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, const double* x,
+                             const float* x32, double* part, const int* done);  // x (FP64 op) or x32
 // gkb.cu
 rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_begin, int j_end,
                    rbf_gkb_state* st);

@@ -111,6 +111,77 @@ __global__ void __launch_bounds__(MF_T, MF_MIN_CTAS) k_mf_partial(const double* 
     }
 }
 
+// FP64 matrix-free products (RBF_FP64 operators): the same entry formula and
+// tiling as the FP32 kernel, in FP64 (s^{-1/2} from an FP32 estimate refined
+// to FP64 accuracy) with FP64 accumulators; bound by the FP64 pipe (about 15
+// FP64 operations per regenerated entry).
+template <int TRANS>
+__global__ void __launch_bounds__(MF_T) k_mf_partial_f64(const double* __restrict__ X, int64_t n, int64_t ni,
+                                                         double c2, double k2, double scale,
+                                                         const double* __restrict__ x, int64_t chunk,
+                                                         double* __restrict__ part, const int* __restrict__ done) {
+    if (gkb_done(done)) return;
+    __shared__ double4 tile[MF_S];
+    const int64_t obase = (int64_t)blockIdx.x * MF_OUT;
+    double ox[MF_R], oy[MF_R], oz[MF_R], a0[MF_R], a1[MF_R], a2[MF_R], acc[MF_R];
+#pragma unroll
+    for (int r = 0; r < MF_R; ++r) {
+        const int64_t o = obase + threadIdx.x + r * MF_T;
+        const bool ok = o < n;
+        ox[r] = ok ? X[o] : 0.0;
+        oy[r] = ok ? X[n + o] : 0.0;
+        oz[r] = ok ? X[2 * n + o] : 0.0;
+        const bool interior = TRANS == 0 && o < ni;
+        a0[r] = interior ? c2 : 0.0;
+        a1[r] = interior ? 2.0 : 0.0;
+        a2[r] = interior ? k2 : 1.0;
+        acc[r] = 0.0;
+    }
+    const int64_t s0 = (int64_t)blockIdx.y * chunk;
+    const int64_t s1 = min(n, s0 + chunk);
+    for (int seg = 0; seg < (TRANS ? 2 : 1); ++seg) {
+        int64_t lo = s0, hi = s1;
+        if (TRANS) {
+            const bool pde = seg == 0;
+            if (pde) hi = min(s1, ni);
+            else lo = max(s0, ni);
+#pragma unroll
+            for (int r = 0; r < MF_R; ++r) {
+                a0[r] = pde ? c2 : 0.0;
+                a1[r] = pde ? 2.0 : 0.0;
+                a2[r] = pde ? k2 : 1.0;
+            }
+            if (hi <= lo) continue;
+        }
+        for (int64_t tb = lo; tb < hi; tb += MF_S) {
+            __syncthreads();
+            for (int q = threadIdx.x; q < MF_S; q += MF_T) {
+                const int64_t sidx = tb + q;
+                tile[q] = sidx < hi ? make_double4(X[sidx], X[n + sidx], X[2 * n + sidx], x[sidx])
+                                    : make_double4(0.0, 0.0, 0.0, 0.0);
+            }
+            __syncthreads();
+            const int cnt = (int)min((int64_t)MF_S, hi - tb);
+            for (int q = 0; q < cnt; ++q) {
+                const double4 nd = tile[q];
+#pragma unroll
+                for (int r = 0; r < MF_R; ++r) {
+                    const double dx = ox[r] - nd.x, dy = oy[r] - nd.y, dz = oz[r] - nd.z;
+                    const double s = fma(dx, dx, fma(dy, dy, fma(dz, dz, c2)));
+                    const double rs = rsqrt_f64(s);
+                    const double g = fma(a0[r], rs * rs, fma(a2[r], s, a1[r]));
+                    acc[r] = fma(rs * g, nd.w, acc[r]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < MF_R; ++r) {
+        const int64_t o = obase + threadIdx.x + r * MF_T;
+        if (o < n) part[(int64_t)blockIdx.y * n + o] = acc[r] * scale;
+    }
+}
+
 // Resident CTAs per SM of the two product kernels (the smaller), per device.
 int mf_occupancy(const rbf_ctx* ctx) {
     static int occ[64] = {0};
@@ -158,16 +229,25 @@ size_t mf_ws_bytes(const rbf_ctx* ctx, int64_t n) {
     return ws_align((size_t)ch * n * sizeof(double));
 }
 
-rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, const float* x32,
-                             double* part, const int* done) {
-    if (op->precision != RBF_MIXED)
-        return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "matrix-free products are FP32 (RBF_MIXED)");
+rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, const double* x,
+                             const float* x32, double* part, const int* done) {
     int64_t tiles, len;
     int ch;
     mf_plan(ctx, op->n, &tiles, &ch, &len);
     if (tiles > 2147483647LL) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large");
     dim3 grid((unsigned)tiles, (unsigned)ch);
     const double scale = op->form == RBF_FORM_EPS ? 1.0 / op->c : 1.0;
+    if (op->precision == RBF_FP64) {
+        const double c2d = op->c * op->c, k2d = op->k * op->k;
+        if (trans)
+            k_mf_partial_f64<1><<<grid, MF_T, 0, ctx->stream>>>(op->d_nodes, op->n, op->n_interior, c2d, k2d, scale,
+                                                                x, len, part, done);
+        else
+            k_mf_partial_f64<0><<<grid, MF_T, 0, ctx->stream>>>(op->d_nodes, op->n, op->n_interior, c2d, k2d, scale,
+                                                                x, len, part, done);
+        RBF_LAUNCHED(ctx, "k_mf_partial_f64");
+        return RBF_OK;
+    }
     const float c2 = (float)(op->c * op->c), k2 = (float)(op->k * op->k);
     if (trans)
         k_mf_partial<1><<<grid, MF_T, 0, ctx->stream>>>(op->d_nodes, op->n, op->n_interior, c2, k2,

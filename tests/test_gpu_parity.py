@@ -119,6 +119,39 @@ def test_matvec_mixed(ctx, R, storage, n):
     assert np.max(np.abs(y1 - A.T @ x) / (np.abs(A).T @ np.abs(x))) < 1e-5
 
 
+@pytest.mark.parametrize("n", [6, 1029, 5000])
+def test_matvec_fp64_matrix_free(ctx, R, n):
+    """FP64 operators regenerate the entries in FP64 (matrix-free): products
+    agree with the dense FP64 matrix to rounding."""
+    ns = random_nodes(n, (3 * n) // 4, n + 5)
+    c, k = 0.25, 3.0
+    op = ctx.rbf_operator_init(dev(ns.soa()), n, ns.n_interior, c, k, R.RBF_MATRIX_FREE, R.RBF_FP64)
+    A = OM.assemble(ns.X, ns.n_interior, c, k)
+    x, y0, y1 = _products(ctx, R, op, n, 3)
+    assert np.max(np.abs(y0 - A @ x) / (np.abs(A) @ np.abs(x))) < 1e-13
+    assert np.max(np.abs(y1 - A.T @ x) / (np.abs(A).T @ np.abs(x))) < 1e-13
+
+
+def test_gkb_fp64_matrix_free_matches_assembled(ctx, R):
+    ns = random_nodes(900, 640, 77)
+    c, k = 0.3, 2.0
+    f = w.plane_wave_rhs(ns, k)
+    op_a, _, _ = gpu_matrix(ctx, R, ns, c, k)
+    op_m = ctx.rbf_operator_init(dev(ns.soa()), ns.n, ns.n_interior, c, k, R.RBF_MATRIX_FREE, R.RBF_FP64)
+    A = OM.assemble(ns.X, ns.n_interior, c, k)
+    ls = max(1, l_stable(A, f, 30)[0])
+    st_a, _, _, al_a, be_a = run_gkb(ctx, R, op_a, f, 30, ns.n)
+    st_m, _, _, al_m, be_m = run_gkb(ctx, R, op_m, f, 30, ns.n)
+    assert st_a.steps_done == st_m.steps_done
+    assert np.max(np.abs(al_m[:ls] - al_a[:ls]) / al_a[:ls]) < 1e-10
+    assert np.max(np.abs(be_m[1:ls + 1] - be_a[1:ls + 1]) / be_a[1:ls + 1]) < 1e-10
+    ca = torch.empty(ns.n, dtype=torch.float64, device="cuda")
+    cm = torch.empty_like(ca)
+    ia = ctx.rbf_hkt(st_a, R.RBF_FIXED_T, -6.0, ca)
+    ctx.rbf_hkt(st_m, R.RBF_FIXED_T, -6.0, cm)
+    assert torch.max(torch.abs(ca - cm)).item() <= 1e-8 * torch.max(torch.abs(ca)).item(), ia.lambda_
+
+
 # ---------------------------------------------------------------- GKB
 def run_gkb(ctx, R, op, f, steps, n):
     st, W, Z, al, be = R.make_state(torch, n, steps)
