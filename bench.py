@@ -197,7 +197,6 @@ def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
 
-    from paper_2511_09798_gb300 import pipeline as Pp
     from paper_2511_09798_gb300 import rbfkr as R
 
     torch.cuda.set_device(local_rank)

@@ -1,5 +1,7 @@
-// Assembled matrix-vector products of Algorithm 1: p = A z (row-major GEMV)
-// and r = A^T w (GEMV^T by row chunks with deterministic partial sums).
+// Assembled matrix-vector products of Algorithm 1: p = A z (row-major GEMV,
+// balanced (row, column-segment) units per warp, partials per segment) and
+// r = A^T w (GEMV^T by row chunks); every partial sum is reduced in a fixed
+// order by the consumer, so results are deterministic.
 //
 // A is streamed once per product with 16-byte vector loads (evict-first), the
 // input vector is read through L1.  FP64 operators use FP64 FMAs (on GB300 the
@@ -13,58 +15,12 @@
 
 namespace {
 
-constexpr int GN_THREADS = 256;  // 8 warps, one row per warp at a time
+constexpr int GN_THREADS = 256;  // 8 warps, one (row, segment) unit per warp at a time
 constexpr int GT_THREADS = 256;
 constexpr int GT_MAX_CHUNK_ROWS = 4096;
 
 __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
-
-// ---------------------------------------------------------------------------
-// y_i = sum_j A_ij x_j for the rows of this CTA's slab.
-// Epilogue (sc != nullptr): y_i = acc * sc[SC_INV_ALPHA] - sc[SC_ALPHA] * w_i and
-// z_out_i = x_i * sc[SC_INV_ALPHA]  (p = A z_j - alpha_j w_j with z_j = r / alpha_j).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(GN_THREADS) k_gemv_n_f64(
-    const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x,
-    double* __restrict__ y, const double* __restrict__ sc, const double* __restrict__ w,
-    double* __restrict__ z_out, const int* __restrict__ done) {
-    if (gkb_done(done)) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = n * (int64_t)blockIdx.x / gridDim.x;  // balanced row partition
-    const int64_t r1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
-    const int64_t nvec = n >> 1;  // full double2 vectors per row
-    const double2* __restrict__ xv = reinterpret_cast<const double2*>(x);
-    for (int64_t i = r0 + warp; i < r1; i += GN_THREADS / 32) {
-        const double2* __restrict__ row = reinterpret_cast<const double2*>(A + i * lda);
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int64_t v = lane;
-        for (; v + 96 < nvec; v += 128) {
-            double2 m0 = ld_stream(row + v), m1 = ld_stream(row + v + 32);
-            double2 m2 = ld_stream(row + v + 64), m3 = ld_stream(row + v + 96);
-            double2 x0 = __ldg(xv + v), x1 = __ldg(xv + v + 32);
-            double2 x2 = __ldg(xv + v + 64), x3 = __ldg(xv + v + 96);
-            a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
-            a1 = fma(m1.x, x1.x, a1); a1 = fma(m1.y, x1.y, a1);
-            a2 = fma(m2.x, x2.x, a2); a2 = fma(m2.y, x2.y, a2);
-            a3 = fma(m3.x, x3.x, a3); a3 = fma(m3.y, x3.y, a3);
-        }
-        for (; v < nvec; v += 32) {
-            double2 m0 = ld_stream(row + v), x0 = __ldg(xv + v);
-            a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
-        }
-        if ((n & 1) && lane == 0) a1 = fma(A[i * lda + n - 1], __ldg(x + n - 1), a1);
-        double acc = warp_sum((a0 + a1) + (a2 + a3));
-        if (lane == 0) {
-            if (sc) {
-                y[i] = acc * sc[SC_INV_ALPHA] - sc[SC_ALPHA] * w[i];
-                if (z_out) z_out[i] = x[i] * sc[SC_INV_ALPHA];
-            } else {
-                y[i] = acc;
-            }
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // part[g][i] = sum_{j in column segment g} A_ij x_j: the n x S (row, segment)
@@ -154,50 +110,6 @@ __global__ void __launch_bounds__(GN_THREADS) k_gemv_nseg_f32(
         for (int64_t c = c0 + nvec * 4 + lane; c < c1; c += 32) acc += (double)(A[i * lda + c] * x32[c]);
         acc = warp_sum(acc);
         if (lane == 0) part[(int64_t)g * n + i] = acc;
-    }
-}
-
-__global__ void __launch_bounds__(GN_THREADS) k_gemv_n_f32(
-    const float* __restrict__ A, int64_t lda, int64_t n, const float* __restrict__ x32,
-    const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ sc,
-    const double* __restrict__ w, double* __restrict__ z_out, const int* __restrict__ done) {
-    if (gkb_done(done)) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t r0 = n * (int64_t)blockIdx.x / gridDim.x;  // balanced row partition
-    const int64_t r1 = n * (int64_t)(blockIdx.x + 1) / gridDim.x;
-    const int64_t nvec = n >> 2;
-    const float4* __restrict__ xv = reinterpret_cast<const float4*>(x32);
-    for (int64_t i = r0 + warp; i < r1; i += GN_THREADS / 32) {
-        const float4* __restrict__ row = reinterpret_cast<const float4*>(A + i * lda);
-        double acc = 0.0;
-        int64_t v = lane;
-        for (; v + 96 < nvec; v += 128) {
-            float4 m0 = ld_stream(row + v), m1 = ld_stream(row + v + 32);
-            float4 m2 = ld_stream(row + v + 64), m3 = ld_stream(row + v + 96);
-            float4 x0 = __ldg(xv + v), x1 = __ldg(xv + v + 32);
-            float4 x2 = __ldg(xv + v + 64), x3 = __ldg(xv + v + 96);
-            float s0 = m0.x * x0.x, s1 = m1.x * x1.x, s2 = m2.x * x2.x, s3 = m3.x * x3.x;
-            s0 = fmaf(m0.y, x0.y, s0); s1 = fmaf(m1.y, x1.y, s1); s2 = fmaf(m2.y, x2.y, s2); s3 = fmaf(m3.y, x3.y, s3);
-            s0 = fmaf(m0.z, x0.z, s0); s1 = fmaf(m1.z, x1.z, s1); s2 = fmaf(m2.z, x2.z, s2); s3 = fmaf(m3.z, x3.z, s3);
-            s0 = fmaf(m0.w, x0.w, s0); s1 = fmaf(m1.w, x1.w, s1); s2 = fmaf(m2.w, x2.w, s2); s3 = fmaf(m3.w, x3.w, s3);
-            acc += (double)((s0 + s1) + (s2 + s3));
-        }
-        for (; v < nvec; v += 32) {
-            float4 m0 = ld_stream(row + v), x0 = __ldg(xv + v);
-            float s0 = m0.x * x0.x;
-            s0 = fmaf(m0.y, x0.y, s0); s0 = fmaf(m0.z, x0.z, s0); s0 = fmaf(m0.w, x0.w, s0);
-            acc += (double)s0;
-        }
-        for (int64_t c = nvec * 4 + lane; c < n; c += 32) acc += (double)(A[i * lda + c] * x32[c]);
-        acc = warp_sum(acc);
-        if (lane == 0) {
-            if (sc) {
-                y[i] = acc * sc[SC_INV_ALPHA] - sc[SC_ALPHA] * w[i];
-                if (z_out) z_out[i] = x[i] * sc[SC_INV_ALPHA];
-            } else {
-                y[i] = acc;
-            }
-        }
     }
 }
 
@@ -334,13 +246,6 @@ int gemv_t_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
     return ch;
 }
 
-static int gemv_n_grid(const rbf_ctx* ctx, int64_t n) {
-    int64_t g = (int64_t)ctx->sm_count * 4;
-    int64_t rows_min = (n + 7) / 8;
-    if (g > rows_min) g = rows_min;
-    return (int)(g < 1 ? 1 : g);
-}
-
 // FP64 A x: grid = one wave of resident CTAs; S column segments per row chosen
 // so that the n S units divide as evenly as possible over the grid's warps
 // (efficiency x / ceil(x) with x = n S / warps), segments of >= 256 columns.
@@ -389,31 +294,19 @@ int gemv_n_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
     return S;
 }
 
-rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, const float* x32,
-                         double* y, const double* sc, const double* w, double* z_out,
+rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, const float* x32, double* part,
                          const int* done) {
-    const int grid = gemv_n_grid(ctx, op->n);
-    if (!sc) {  // column-segment partials [S][n] into y
-        int g, S;
-        int64_t len;
-        gemv_nseg_plan(ctx, op->n, op->precision == RBF_FP64, &g, &S, &len);
-        if (op->precision == RBF_FP64) {
-            k_gemv_nseg_f64<<<g, GN_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x, S, len,
-                                                               y, done);
-            RBF_LAUNCHED(ctx, "k_gemv_nseg_f64");
-        } else {
-            k_gemv_nseg_f32<<<g, GN_THREADS, 0, ctx->stream>>>((const float*)op->d_A, op->lda, op->n, x32, S, len,
-                                                               y, done);
-            RBF_LAUNCHED(ctx, "k_gemv_nseg_f32");
-        }
-    } else if (op->precision == RBF_FP64) {
-        k_gemv_n_f64<<<grid, GN_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x,
-                                                           y, sc, w, z_out, done);
-        RBF_LAUNCHED(ctx, "k_gemv_n_f64");
+    int g, S;
+    int64_t len;
+    gemv_nseg_plan(ctx, op->n, op->precision == RBF_FP64, &g, &S, &len);
+    if (op->precision == RBF_FP64) {
+        k_gemv_nseg_f64<<<g, GN_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x, S, len, part,
+                                                           done);
+        RBF_LAUNCHED(ctx, "k_gemv_nseg_f64");
     } else {
-        k_gemv_n_f32<<<grid, GN_THREADS, 0, ctx->stream>>>((const float*)op->d_A, op->lda, op->n, x32,
-                                                           x, y, sc, w, z_out, done);
-        RBF_LAUNCHED(ctx, "k_gemv_n_f32");
+        k_gemv_nseg_f32<<<g, GN_THREADS, 0, ctx->stream>>>((const float*)op->d_A, op->lda, op->n, x32, S, len, part,
+                                                           done);
+        RBF_LAUNCHED(ctx, "k_gemv_nseg_f32");
     }
     return RBF_OK;
 }
@@ -469,8 +362,8 @@ extern "C" rbf_status rbf_matvec(rbf_ctx* ctx, const rbf_operator* op, int trans
     if (op->precision == RBF_MIXED) RBF_TRY(launch_to_f32(ctx, n, d_x, x32));
     if (trans == 0) {
         const int S = gemv_n_chunks(ctx, op);
-        if (S == 1) return launch_gemv_n(ctx, op, d_x, x32, d_y, nullptr, nullptr, nullptr, nullptr);
-        RBF_TRY(launch_gemv_n(ctx, op, d_x, x32, part, nullptr, nullptr, nullptr, nullptr));
+        if (S == 1) return launch_gemv_n(ctx, op, d_x, x32, d_y, nullptr);
+        RBF_TRY(launch_gemv_n(ctx, op, d_x, x32, part, nullptr));
         return launch_reduce_partials(ctx, n, S, part, d_y);
     }
     RBF_TRY(launch_gemv_t_partial(ctx, op, d_x, x32, part, nullptr));

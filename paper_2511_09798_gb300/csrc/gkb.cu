@@ -440,7 +440,7 @@ static rbf_status gkb_product(rbf_ctx* ctx, const rbf_operator* op, int trans, c
     rbf_status st;
     if (op->storage == RBF_MATRIX_FREE) st = launch_mf_partial(ctx, op, trans, q_raw, q32, part, done);
     else if (trans) st = launch_gemv_t_partial(ctx, op, q_raw, q32, part, done);
-    else st = launch_gemv_n(ctx, op, q_raw, q32, part, nullptr, nullptr, nullptr, done);
+    else st = launch_gemv_n(ctx, op, q_raw, q32, part, done);
     rbf_prod_end(ctx, trans, slot);
     return st;
 }

@@ -22,7 +22,6 @@ Labels (the paper is silent; these are this module's readings):
 """
 from __future__ import annotations
 
-import ctypes as C
 import math
 
 import numpy as np

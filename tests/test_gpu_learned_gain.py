@@ -8,7 +8,6 @@ steps and less time, with an error no worse than GCV-HKT's on most runs.
 """
 import math
 
-import numpy as np
 import pytest
 
 import workloads as w
