@@ -446,6 +446,7 @@ def run_batch(args, rank, world, local_rank):
     for _ in range(args.warmup):
         one()
     torch.cuda.synchronize()
+    ctx.rbf_get_counters(reset=True)
     sampler = ClockSampler(local_rank) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -464,6 +465,7 @@ def run_batch(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ms, instances_all = reduce_over_ranks(e0.elapsed_time(e1), len(inst) * args.steps, dev)
     clocks = sampler.stop() if sampler else None
+    cnt = ctx.rbf_get_counters(reset=True)
 
     def errors():
         uh = u.cpu().numpy().reshape(len(inst), m)
@@ -476,6 +478,41 @@ def run_batch(args, rank, world, local_rank):
     errs = errors()
     mean_steps = steps_total / (len(inst) * args.steps)
     tune = ctx.rbf_get_tuning()
+
+    # end to end: every step copies its inputs (nodes, f, test points) from
+    # pinned host memory and reads u back
+    nodes_h, f_h, P_h = (t.cpu().pin_memory() for t in (keep["nodes"], keep["f"], P))
+    u_h = torch.empty(u.shape, dtype=u.dtype).pin_memory()
+    rank_barrier()
+    torch.cuda.synchronize()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record()
+    for _ in range(args.steps):
+        keep["nodes"].copy_(nodes_h, non_blocking=True)
+        keep["f"].copy_(f_h, non_blocking=True)
+        P.copy_(P_h, non_blocking=True)
+        one()
+        u_h.copy_(u, non_blocking=True)
+    x1.record()
+    torch.cuda.synchronize()
+    ms_e2e, inst_e2e = reduce_over_ranks(x0.elapsed_time(x1), len(inst) * args.steps, dev)
+    h2d = (nodes_h.numel() + f_h.numel() + P_h.numel()) * 8
+    d2h = u_h.numel() * 8
+
+    # dominant kernel: the batched matrix-free products, timed live by the
+    # autotuner (one A and one A^T product over the whole batch, best config)
+    roof = None
+    if tune.get("best_ms", 0) > 0:
+        ops = sum(2 * s_.n * (11 * s_.n_interior + 8 * (s_.n - s_.n_interior)) for s_ in inst)
+        tops = ops / (tune["best_ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": round(tops, 3), "peak": round(FP32_LANE_TOPS, 3),
+                "unit": "T FP32-pipe ops/s", "frac": round(tops / FP32_LANE_TOPS, 4), "traffic": None,
+                "kernel": "k_mf_batch (one A and one A^T product of all instances)",
+                "avg_launch_ms": round(tune["best_ms"] / 2, 5),
+                "timing": "the autotuner's CUDA-event timing of the chosen configuration, this run",
+                "algorithmic_per_launch": f"{sum(s_.n * s_.n for s_ in inst)} entries, "
+                                          f"{ops // 2} FP32-pipe ops (11 per PDE entry, 8 per Dirichlet entry)",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts and max clock)"}
     other = None
     if learned_arm:  # the same instances by the other forms, once each, for comparison
         torch.cuda.synchronize()
@@ -539,7 +576,13 @@ def run_batch(args, rank, world, local_rank):
             "gkb_steps_per_s": round(steps_total / (ms / 1e3), 1),
             "regenerated_entries_per_s": entries / (ms / 1e3),
             "re_vs_exact": {"median": float(np.median(errs)), "max": float(np.max(errs))},
-            "tuning": tune, "clocks": clocks}
+            "roofline": roof,
+            "e2e": {"value": round(inst_e2e / (ms_e2e / 1e3), 3), "unit": "instances/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": round(ms_e2e / args.steps, 2)},
+            "gpu_launches": int(cnt["launches"]),
+            "tuning": tune, "clocks": clocks,
+            "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline_batch(inst, fs, pts, L)}
 
 
 # --------------------------------------------------------------------------- learned stop (pump casing)
@@ -788,6 +831,70 @@ def oracle_solve(wl, c, k, steps):
     return g.steps_done
 
 
+def host_info():
+    """Host threads the NumPy oracle uses, CPU model and BLAS build (for the CPU baseline)."""
+    import numpy as np
+    threads = None
+    try:
+        from threadpoolctl import threadpool_info
+        blas = [d for d in threadpool_info() if d.get("user_api") == "blas"]
+        if blas:
+            threads = int(blas[0]["num_threads"])
+    except Exception:
+        pass
+    if threads is None:
+        env = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
+        threads = int(env) if env and env.isdigit() else os.cpu_count()
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    import platform
+    model = f"{platform.machine()} {model}" if model else platform.machine()
+    try:
+        b = np.show_config(mode="dicts")["Build Dependencies"]["blas"]
+        blas_name = f"{b.get('name')} {b.get('version')}"
+    except Exception:
+        blas_name = "unknown"
+    return {"cores": threads, "cpu": model, "blas": blas_name}
+
+
+def cpu_baseline_batch(inst, fs, pts, steps, budget_s=15.0):
+    """The oracle on the batch's instances in order (each one a full FP64
+    solve: assemble, GKB, HKT with GCV, u at the test points) until budget_s
+    has passed; instances/s over that sample."""
+    from oracle import evaluate as OE
+    from oracle import gkb as OG
+    from oracle import mq as OM
+    from oracle import regularize as OR
+    t0 = time.perf_counter()
+    count, rows = 0, 0
+    for b, s_ in enumerate(inst):
+        c, k = s_.params["c"], s_.params["k"]
+        A = OM.assemble(s_.X, s_.n_interior, c, k)
+        g = OG.gkb(A, None, fs[b], steps)
+        h = OR.hkt(g, "gcv")
+        OE.reconstruct(h["coef"], s_.X, pts[b], c)
+        del A, g, h
+        count += 1
+        rows += s_.n
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    hi = host_info()
+    return {"value": round(count / dt, 4), "unit": "instances/s", "cores": hi["cores"], "kind": "oracle",
+            "cpu": hi["cpu"], "blas": hi["blas"],
+            "sample": f"the first {count} of {len(inst)} instances ({rows} rows in all), each a full FP64 solve "
+                      f"(assemble, {steps} GKB steps, SVD, GCV, lift, u at {pts[0].shape[0]} points): {dt:.1f} s"}
+
+
 def cpu_baseline(wl, sample_steps):
     if wl["ns"].n > 10000:
         sample_steps = min(sample_steps, 10)
@@ -795,7 +902,9 @@ def cpu_baseline(wl, sample_steps):
     t0 = time.perf_counter()
     done = oracle_solve(wl, c, k, sample_steps)
     dt = time.perf_counter() - t0
-    return {"value": round(done / dt, 3), "unit": "GKB steps/s", "cores": os.cpu_count(), "kind": "oracle",
+    hi = host_info()
+    return {"value": round(done / dt, 3), "unit": "GKB steps/s", "cores": hi["cores"], "kind": "oracle",
+            "cpu": hi["cpu"], "blas": hi["blas"],
             "sample": f"one full solve (assemble, {sample_steps} GKB steps, SVD, GCV, lift, u at "
                       f"{wl['points'].shape[0]} points) of {wl['name']} at c={c}, k={k}: {dt:.1f} s"}
 
@@ -819,7 +928,7 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": wl["name"], "n": wl["ns"].n, "gkb_steps": L, "cases_c_k": [(c, k)],
                        "solves_per_step": 1, "precision": "fp64", "storage": "assembled", "rule": "gcv"},
-            "cpu_baseline": {"value": v, "unit": "GKB steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "GKB steps/s", **host_info(), "kind": "oracle",
                              "sample": f"one full solve of {wl['name']} at c={c}, k={k} per step"},
             "e2e": {"value": v, "unit": "GKB steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

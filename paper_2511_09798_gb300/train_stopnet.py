@@ -63,7 +63,7 @@ def evaluate(ctx, torch, net, insts, L, m=500):
             ctx.rbf_evaluate(op, coef, dP, m, u)
             return float(np.max(np.abs(u.cpu().numpy() - ue)) / np.max(np.abs(ue)))
 
-        row = {"n": ns.n, "c": c, "k": k, "rhs": ns.params["rhs"]}
+        row = {"n": ns.n, "c": c, "k": k, "rhs": ns.params["rhs"], "domain": ns.domain}
         for name, rule in (("gcv", R.RBF_GCV), ("lcurve", R.RBF_LCURVE)):
             st, *_ = R.make_state(torch, ns.n, L)
             torch.cuda.synchronize()
@@ -88,7 +88,16 @@ def evaluate(ctx, torch, net, insts, L, m=500):
     return rows
 
 
-def summarize(rows):
+def summarize(rows, by_domain=True):
+    out = _summarize(rows)
+    if by_domain:
+        doms = sorted({r.get("domain", "?") for r in rows})
+        if len(doms) > 1:
+            out["by_domain"] = {d: _summarize([r for r in rows if r.get("domain", "?") == d]) for d in doms}
+    return out
+
+
+def _summarize(rows):
     g = np.array([[r["gcv_err"], r["lcurve_err"], r["learned_err"], r["gcv_s"], r["lcurve_s"], r["learned_s"],
                    r["learned_steps"], r["learned_accepted"]] for r in rows])
     eg, el, ex, tg, tl, tx, sx, acc = g.T
@@ -119,6 +128,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--rel-tol", type=float, default=0.25)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--pump-share", type=float, default=0.25,
+                    help="share of casing-like node sets among the training and evaluation runs")
     ap.add_argument("--out", default=None)
     ap.add_argument("--summary", default=None)
     a = ap.parse_args(argv)
@@ -133,7 +144,7 @@ def main(argv=None):
     ells = list(range(10, L + 1, 10))
     tgrid = learned.grid_t(ctx.grid_j, ctx.grid_t_lo, ctx.grid_t_hi, 4)
     t0 = time.time()
-    tr = w.stop_instances(a.runs, a.n_lo, a.n_hi, seed0=w.nodes.BASE_SEED + 600)
+    tr = w.stop_instances(a.runs, a.n_lo, a.n_hi, seed0=w.nodes.BASE_SEED + 600, pump_share=a.pump_share)
     F, E = generate(ctx, torch, tr, L, ells)
     torch.cuda.synchronize()
     t_gen = time.time() - t0
@@ -148,10 +159,11 @@ def main(argv=None):
                                 z_max=6.0)
     torch.cuda.synchronize()
     t_train = time.time() - t1
-    ev = w.stop_instances(a.eval_runs, a.n_lo, a.n_hi, seed0=w.nodes.BASE_SEED + 50000)
+    ev = w.stop_instances(a.eval_runs, a.n_lo, a.n_hi, seed0=w.nodes.BASE_SEED + 50000, pump_share=a.pump_share)
     rows = evaluate(ctx, torch, net, ev, L)
     summ = {
         "training_runs": int(ok.sum()), "gkb_steps": L, "n_range": [a.n_lo, a.n_hi], "rel_tol": a.rel_tol,
+        "pump_share": a.pump_share,
         "generate_s": t_gen, "train_s": t_train, "train_steps": a.train_steps, "losses": losses,
         "label_l_mean": float(np.exp(Y[ok, 0]).mean()), "t_range": [t_min, t_max],
         "eval": summarize(rows),

@@ -77,3 +77,26 @@ def test_paper_shaped_node_sets():
     a = w.paper_nodes("cube", "halton", 359, 5)
     b = w.paper_nodes("cube", "halton", 359, 5)
     assert np.array_equal(a.X, b.X)
+
+
+def test_stop_instances_casing_share(monkeypatch):
+    """pump_share = 0 keeps the cube/sphere draws; a positive share mixes in
+    casing-like node sets drawn without repetition from the pool."""
+    import workloads.nodes as N
+    small = w.pump_like(400, 1600, seed=N.BASE_SEED + 651)
+    monkeypatch.setattr(N, "_PUMP_POOL", (small.X[small.n_interior:].copy(), small.X[:small.n_interior].copy()))
+    plain = w.stop_instances(12, 300, 600)
+    again = w.stop_instances(12, 300, 600, pump_share=0.0)
+    assert {s.domain for s in plain} <= {"cube", "sphere"}
+    for a, b in zip(plain, again):
+        assert a.domain == b.domain and np.array_equal(a.X, b.X) and a.params["c"] == b.params["c"]
+    mixed = w.stop_instances(24, 300, 600, pump_share=0.5)
+    pumps = [s for s in mixed if s.domain == "pump"]
+    assert pumps
+    for s in pumps:
+        assert s.n_boundary == round(0.2 * s.n)
+        assert np.unique(s.X, axis=0).shape[0] == s.n
+        assert inside("pump", s.X[:s.n_interior]).all()
+        assert s.params["rhs"] in ("plane", "gauss")
+        if s.params["rhs"] == "gauss":
+            assert inside("pump", s.params["center"][None, :]).all()

@@ -378,26 +378,62 @@ def batch_instances(count: int = 96, n_lo: int = 2000, n_hi: int = 16000,
     return out
 
 
+_PUMP_POOL = None
+
+
+def _pump_pool():
+    """One large casing-like sample (16 000 boundary, 64 000 interior nodes),
+    drawn once per process; pump_subsample takes instances from it."""
+    global _PUMP_POOL
+    if _PUMP_POOL is None:
+        ns = pump_like(16000, 64000, seed=BASE_SEED + 650)
+        _PUMP_POOL = (ns.X[ns.n_interior:].copy(), ns.X[:ns.n_interior].copy())
+    return _PUMP_POOL
+
+
+def pump_subsample(n: int, boundary_share: float, rng: np.random.Generator) -> NodeSet:
+    """Casing-like node set of n nodes: a uniform subsample (without
+    replacement) of the pool's boundary and interior nodes, which is again a
+    uniform sample of the surface and of the volume (pump_like itself takes
+    seconds per call at these sizes)."""
+    B, I = _pump_pool()
+    nb = int(round(boundary_share * n))
+    ni = n - nb
+    if nb > B.shape[0] or ni > I.shape[0]:
+        raise ValueError(f"pump_subsample: n = {n} exceeds the pool")
+    bsel = np.sort(rng.choice(B.shape[0], nb, replace=False))
+    isel = np.sort(rng.choice(I.shape[0], ni, replace=False))
+    return NodeSet(np.ascontiguousarray(np.concatenate([I[isel], B[bsel]])), ni, "pump", f"pump{n}")
+
+
 def stop_instances(count: int, n_lo: int, n_hi: int, seed0: int = BASE_SEED + 600,
-                   gauss_share: float = 0.5):
+                   gauss_share: float = 0.5, pump_share: float = 0.0):
     """Training / evaluation runs for the learned stopping index.
 
     Node sets and (c, k) are drawn like the batched sweep (cube or sphere,
-    N ~ U{n_lo..n_hi}, c log-uniform in [0.05, 1], k ~ U[1, 20]).  The exact
-    solution is a plane wave sin(k d.X) with d uniform on S^2, or, with
-    probability gauss_share, the Gaussian exp(-|X - X0|^2 / sigma) of the
-    paper's examples with sigma log-uniform in [0.05, 10] (the casing example
-    uses sigma = 10) and X0 uniform in the middle half of the domain.  params: c, k, seed, rhs ('plane' | 'gauss'),
-    d or (sigma, center).
+    N ~ U{n_lo..n_hi}, c log-uniform in [0.05, 1], k ~ U[1, 20]); with
+    probability pump_share the node set is casing-like instead (pump_subsample,
+    boundary share 0.2).  The exact solution is a plane wave sin(k d.X) with d
+    uniform on S^2, or, with probability gauss_share, the Gaussian
+    exp(-|X - X0|^2 / sigma) of the paper's examples with sigma log-uniform in
+    [0.05, 10] (the casing example uses sigma = 10) and X0 uniform in the
+    middle half of the domain (a random interior node for the casing).
+    params: c, k, seed, rhs ('plane' | 'gauss'), d or (sigma, center).
+    With pump_share = 0 the draws are those of the cube/sphere-only sampler.
     """
     out = []
     for b in range(count):
         rng = _rng(seed0 + b)
-        is_cube = rng.uniform() < 0.5
+        u = rng.uniform()
+        is_pump = u < pump_share
+        is_cube = (not is_pump) and (u - pump_share) / (1.0 - pump_share) < 0.5
         n = int(rng.integers(n_lo, n_hi + 1))
         c = float(math.exp(rng.uniform(math.log(0.05), math.log(1.0))))
         k = float(rng.uniform(1.0, 20.0))
-        if is_cube:
+        if is_pump:
+            ns = pump_subsample(n, 0.20, rng)
+            center = ns.X[int(rng.integers(ns.n_interior))].copy()
+        elif is_cube:
             ns = cube_faces_random(n, 0.30, rng)
             center = rng.uniform(0.25, 0.75, 3)
         else:
