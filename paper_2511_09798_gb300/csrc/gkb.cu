@@ -9,8 +9,8 @@
 //             of rows:  finalize nrm = |q_raw| from the previous |v|^2
 //             partials (alpha_j or beta_j, breakdown test tau = factor * N *
 //             eps * c_hat) -> v = (sum of partials) / nrm - nrm * u, store
-//             q_raw / nrm into its basis -> [per-slab Q^T v partials, grid
-//             barrier, distributed reduction, grid barrier, v -= Q h] twice
+//             q_raw / nrm into its basis -> [per-slab Q^T v partials, one
+//             grid barrier that also sums them into h, v -= Q h] twice
 //             -> |v|^2 partials.  The CTA's slab of Q and of the product
 //             partials is staged in shared memory (cp.async) while the norm
 //             is finalised.
@@ -153,6 +153,7 @@ struct HalfArgs {
     int64_t ldq;
     int mcount;
     double* hpart;        // [mcount][G] dot partials
+    double* gpart;        // [mcount][barrier groups] group sums of the partials
     double* h;            // [mcount] reduced dots
     double* npart;        // in: |q_raw|^2 partials; out: |v|^2 partials
     int rmax;             // max slab rows (shared-memory stride)
@@ -280,18 +281,8 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
             for (; i < R; ++i) a0 = fma(q[i], vs[i], a0);
             a.hpart[(int64_t)m * gridDim.x + blockIdx.x] = (a0 + a1) + (a2 + a3);
         }
-        if (!grid_sync(stt, a.bar, a.bar_group, a.budget)) return;
-        // distributed reduction: CTA b sums the partials of the vectors m = b, b+G, ...
-        if (threadIdx.x < 32) {
-            const int G = gridDim.x;
-            for (int m = blockIdx.x; m < M; m += G) {
-                double acc = 0.0;
-                for (int b = threadIdx.x; b < G; b += 32) acc += __ldcg(a.hpart + (int64_t)m * G + b);
-                acc = warp_sum(acc);
-                if (threadIdx.x == 0) a.h[m] = acc;
-            }
-        }
-        if (!grid_sync(stt, a.bar, a.bar_group, a.budget)) return;
+        // h = Q^T v: the partials are summed inside the barrier (fixed order)
+        if (!grid_reduce_sync(stt, a.bar, a.bar_group, a.budget, a.hpart, a.gpart, a.h, M)) return;
         for (int m = threadIdx.x; m < M; m += SL_THREADS) hs[m] = __ldcg(a.h + m);
         __syncthreads();
         // v -= Q h: thread (row, group of basis vectors), two chains each
@@ -427,6 +418,7 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
     b += 2 * ws_align((size_t)n * 8);                 // vr, vp
     b += 2 * ws_align((size_t)n * 4);                 // vr32, vp32
     b += ws_align((size_t)(steps + 2) * G * 8);       // hpart
+    b += ws_align((size_t)(steps + 2) * G * 8);       // gpart (at most G groups)
     b += ws_align((size_t)(steps + 2) * 8);           // h
     b += ws_align((size_t)(G + 2) * BAR_STRIDE * 4);  // barrier counters
     b += ws_align((size_t)G * 8);                     // npart
@@ -460,10 +452,11 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
     float* vr32 = wc.take<float>((size_t)n);
     float* vp32 = wc.take<float>((size_t)n);
     double* hpart = wc.take<double>((size_t)(st->capacity + 2) * G);
-    double* h = wc.take<double>((size_t)(st->capacity + 2));
     int bar_group = 1;
     while (bar_group * bar_group < G) ++bar_group;
     const int bar_k = (G + bar_group - 1) / bar_group;
+    double* gpart = wc.take<double>((size_t)(st->capacity + 2) * G);
+    double* h = wc.take<double>((size_t)(st->capacity + 2));
     unsigned* bar = wc.take<unsigned>((size_t)(bar_k + 2) * BAR_STRIDE);
     RBF_CUDA(ctx, cudaMemsetAsync(bar, 0, (size_t)(bar_k + 2) * BAR_STRIDE * sizeof(unsigned), ctx->stream));
     // shared-memory plan of the half-step kernel: stage the Q slab when it fits
@@ -531,6 +524,7 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
         a.ldq = ldq;
         a.mcount = mcount;
         a.hpart = hpart;
+        a.gpart = gpart;
         a.h = h;
         a.npart = npart;
         a.rmax = rmax;
