@@ -11,9 +11,8 @@
 //             eps * c_hat) -> v = (sum of partials) / nrm - nrm * u, store
 //             q_raw / nrm into its basis -> [per-slab Q^T v partials, one
 //             grid barrier that also sums them into h, v -= Q h] twice
-//             -> |v|^2 partials.  The CTA's slab of Q and of the product
-//             partials is staged in shared memory (cp.async) while the norm
-//             is finalised.
+//             -> |v|^2 partials.  The CTA's slabs of Q, u, q_raw and the
+//             product partials are staged in shared memory (cp.async).
 //
 // i.e. classical Gram-Schmidt applied twice ("twice is enough") against the
 // current basis before the norm, which is the reorthogonalization placement
@@ -34,6 +33,7 @@ constexpr int SL_WARPS = SL_THREADS / 32;
 constexpr int SL_MAX_ROWS = 2048;  // slab rows held in shared memory
 constexpr int UPD_ROWS = 64;       // rows per update pass
 constexpr int UPD_GROUPS = SL_THREADS / UPD_ROWS;
+constexpr int SPLIT = 4;           // threads per row (partial sums) and per basis vector (dots)
 
 struct Slab {
     int64_t r0, r1;
@@ -153,27 +153,33 @@ struct HalfArgs {
     int64_t ldq;
     int mcount;
     double* hpart;        // [mcount][G] dot partials
-    double* gpart;        // [mcount][barrier groups] group sums of the partials
-    double* h;            // [mcount] reduced dots
+    double* gpart;        // 2 x [mcount][barrier groups] group sums (by barrier parity)
     double* npart;        // in: |q_raw|^2 partials; out: |v|^2 partials
-    int rmax;             // max slab rows (shared-memory stride)
-    unsigned* bar;        // barrier counters (see grid_sync)
+    int rmax;             // slab rows held in shared memory (odd: conflict-free strides)
+    unsigned* bar;        // barrier counters (see grid_reduce_sync)
     int bar_group;        // CTAs per barrier group
+    unsigned epoch0;      // barriers completed on `bar` before this launch
     long long budget;
 };
 
 // One half-step of Algorithm 1 after the product: finalize the norm of q_raw
 // (alpha_j or beta_j, breakdown test), form v, and reorthogonalize it twice
 // against Q (classical Gram-Schmidt), ending with the |v|^2 partials.
-// STAGE: the CTA's slab of Q is copied to shared memory once (cp.async,
-// overlapped with the norm finalisation) and all four passes over Q read it
-// there; otherwise they read Q from L2.  The product partials of the slab are
-// always staged.
+//
+// The work runs on v' = v / inv (inv = 1 / nrm, or 1 for a resumed run):
+// v' = sum(partials) - (nrm / inv) u with nrm / inv = |q_raw|^2, so the square
+// root, the division and the breakdown test (one thread of the last warp) run
+// beside the partial sums instead of before them; Gram-Schmidt is linear in
+// v', and v = v' inv is formed when v is stored.  The CTA's slabs of the
+// product partials, u, q_raw and (STAGE) Q are copied to shared memory with
+// cp.async; without STAGE the passes read Q from L2.  Partial sums and dot
+// products are split over SPLIT threads per row or per basis vector so that
+// all warps share the FP64 work.
 template <bool STAGE>
 __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
     extern __shared__ double dsm[];
     __shared__ double red[UPD_GROUPS * UPD_ROWS];
-    __shared__ double nrm_s, inv_s;
+    __shared__ double acc_s, fu_s, inv_s;
     __shared__ int brk_s;
     rbf_dev_state* stt = a.stt;
     if (*(volatile int*)&stt->info[IN_DONE]) return;
@@ -181,146 +187,169 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
     const int R = (int)(s.r1 - s.r0);
     const int RM = a.rmax;
     const int M = a.mcount;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* Qs = dsm;                                 // [M][RM]   (STAGE)
     double* ps = Qs + (STAGE ? (size_t)M * RM : 0);   // [chunks][RM]
-    double* vs = ps + (size_t)a.chunks * RM;          // [RM]
-    double* hs = vs + RM;                             // [M]
-    // ---- stage the slab's product partials and (STAGE) its rows of Q
-    for (int q = threadIdx.x / 32; q < a.chunks; q += SL_WARPS)
-        for (int i = threadIdx.x & 31; i < R; i += 32)
-            cp_async8(ps + (size_t)q * RM + i, a.part + (int64_t)q * a.n + s.r0 + i);
+    double* vs = ps + (size_t)a.chunks * RM;          // [RM]  v' of the slab
+    double* us = vs + RM;                             // [RM]  u of the slab
+    double* qs = us + RM;                             // [RM]  q_raw of the slab
+    double* r4 = qs + RM;                             // [SPLIT][RM]
+    double* d4 = r4 + (size_t)SPLIT * RM;             // [SPLIT][M]
+    double* hs = d4 + (size_t)SPLIT * M;              // [M]   Q^T v'
+    // ---- stage the slab's product partials, u, q_raw and (STAGE) its rows of Q
+    for (int q = warp; q < a.chunks; q += SL_WARPS)
+        for (int i = lane; i < R; i += 32) cp_async8(ps + (size_t)q * RM + i, a.part + (int64_t)q * a.n + s.r0 + i);
+    for (int i = threadIdx.x; i < R; i += SL_THREADS) {
+        if (a.u) cp_async8(us + i, a.u + s.r0 + i);
+        cp_async8(qs + i, a.q_raw + s.r0 + i);
+    }
     if (STAGE)
-        for (int m = threadIdx.x / 32; m < M; m += SL_WARPS)
-            for (int i = threadIdx.x & 31; i < R; i += 32)
+        for (int m = warp; m < M; m += SL_WARPS)
+            for (int i = lane; i < R; i += 32)
                 cp_async8(Qs + (size_t)m * RM + i, a.Q + (int64_t)m * a.ldq + s.r0 + i);
-    // ---- finalize the norm (every CTA computes the same value in the same order)
-    if (threadIdx.x < 32) {
+    // ---- |q_raw|^2 (every CTA sums the previous partials in the same order)
+    if (warp == 0) {
         double acc = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) acc += a.npart[b];
+        for (int b = lane; b < (int)gridDim.x; b += 32) acc += a.npart[b];
         acc = warp_sum(acc);
-        if (threadIdx.x == 0) {
-            double* sc = stt->scal;
-            const double eps = DBL_EPSILON;
-            double nrm = sqrt(acc);
-            int brk = 0;
-            // c_hat double buffer: the r-side of step j reads slot j&1, writes (j+1)&1;
-            // the p-side of step j reads slot (j+1)&1
-            const int rd = a.side == 0 ? (a.j & 1) : ((a.j + 1) & 1);
-            const double ch_old = sc[SC_CHAT0 + rd];
-            double ch_new = ch_old;
-            if (a.resume) {
-                nrm = sc[SC_BETA];
-            } else if (a.side == 1) {
-                brk = nrm <= a.factor * (double)a.n * eps * fmax(ch_old, nrm) ? 1 : 0;
-            } else if (a.j == 1) {
-                brk = nrm > 0.0 ? 0 : 1;
-            } else {
-                ch_new = fmax(ch_old, hypot(a.alpha[a.j - 2], nrm));
-                brk = nrm <= a.factor * (double)a.n * eps * ch_new ? 2 : 0;
-            }
-            nrm_s = nrm;
-            inv_s = a.resume ? 1.0 : 1.0 / nrm;
-            brk_s = brk;
-            if (blockIdx.x == 0) {
-                if (a.side == 0 && !a.resume) sc[SC_CHAT0 + ((a.j + 1) & 1)] = ch_new;
-                if (brk) {
-                    stt->info[IN_STEPS] = a.j - 1;
-                    stt->info[IN_BREAK] = brk;
-                    if (brk == 2) a.beta[a.j - 1] = 0.0;
-                    stt->info[IN_DONE] = 1;
-                } else if (a.side == 1) {
-                    a.alpha[a.j - 1] = nrm;
-                    sc[SC_ALPHA] = nrm;
-                } else {
-                    a.beta[a.j - 1] = nrm;
-                    sc[SC_BETA] = nrm;
-                    stt->info[IN_STEPS] = a.j - 1;
-                }
-            }
+        if (lane == 0) {
+            acc_s = acc;
+            fu_s = a.resume ? stt->scal[SC_BETA] : acc;
         }
     }
     cp_async_wait_all();
+    __syncthreads();
+    // ---- norm, inverse and breakdown test: one thread of the last warp
+    if (threadIdx.x == SL_THREADS - 32) {
+        double* sc = stt->scal;
+        const double eps = DBL_EPSILON;
+        double nrm = sqrt(acc_s);
+        int brk = 0;
+        // c_hat double buffer: the r-side of step j reads slot j&1, writes (j+1)&1;
+        // the p-side of step j reads slot (j+1)&1
+        const int rd = a.side == 0 ? (a.j & 1) : ((a.j + 1) & 1);
+        const double ch_old = sc[SC_CHAT0 + rd];
+        double ch_new = ch_old;
+        if (a.resume) {
+            nrm = sc[SC_BETA];
+        } else if (a.side == 1) {
+            brk = nrm <= a.factor * (double)a.n * eps * fmax(ch_old, nrm) ? 1 : 0;
+        } else if (a.j == 1) {
+            brk = nrm > 0.0 ? 0 : 1;
+        } else {
+            ch_new = fmax(ch_old, hypot(a.alpha[a.j - 2], nrm));
+            brk = nrm <= a.factor * (double)a.n * eps * ch_new ? 2 : 0;
+        }
+        inv_s = a.resume ? 1.0 : 1.0 / nrm;
+        brk_s = brk;
+        if (blockIdx.x == 0) {
+            if (a.side == 0 && !a.resume) sc[SC_CHAT0 + ((a.j + 1) & 1)] = ch_new;
+            if (brk) {
+                stt->info[IN_STEPS] = a.j - 1;
+                stt->info[IN_BREAK] = brk;
+                if (brk == 2) a.beta[a.j - 1] = 0.0;
+                stt->info[IN_DONE] = 1;
+            } else if (a.side == 1) {
+                a.alpha[a.j - 1] = nrm;
+                sc[SC_ALPHA] = nrm;
+            } else {
+                a.beta[a.j - 1] = nrm;
+                sc[SC_BETA] = nrm;
+                stt->info[IN_STEPS] = a.j - 1;
+            }
+        }
+    }
+    // ---- R1: v' = (sum of partials) - fu u, the chunk sum split SPLIT ways
+    const double fu = fu_s;
+    for (int p = threadIdx.x; p < SPLIT * R; p += SL_THREADS) {
+        const int i = p % R, k = p / R;
+        double t0 = 0.0, t1 = 0.0;
+        int q = k;
+        for (; q + SPLIT < a.chunks; q += 2 * SPLIT) {
+            t0 += ps[(size_t)q * RM + i];
+            t1 += ps[(size_t)(q + SPLIT) * RM + i];
+        }
+        if (q < a.chunks) t0 += ps[(size_t)q * RM + i];
+        r4[(size_t)k * RM + i] = t0 + t1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < R; i += SL_THREADS) {
+        double v = (r4[i] + r4[RM + i]) + (r4[2 * RM + i] + r4[3 * RM + i]);
+        if (a.u) v = fma(-fu, us[i], v);
+        vs[i] = v;
+    }
     __syncthreads();
     if (brk_s) {
         if (brk_s == 2 && a.basis_out)  // w_j = 0 after a beta breakdown
             for (int64_t i = s.r0 + threadIdx.x; i < s.r1; i += SL_THREADS) a.basis_out[i] = 0.0;
         return;
     }
-    const double nrm = nrm_s, inv = inv_s;
-    // ---- R1: v = (sum of partials) / nrm - nrm u; store q_raw / nrm
-    for (int i = threadIdx.x; i < R; i += SL_THREADS) {
-        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-        int q = 0;
-        for (; q + 3 < a.chunks; q += 4) {
-            p0 += ps[(size_t)q * RM + i];
-            p1 += ps[(size_t)(q + 1) * RM + i];
-            p2 += ps[(size_t)(q + 2) * RM + i];
-            p3 += ps[(size_t)(q + 3) * RM + i];
-        }
-        for (; q < a.chunks; ++q) p0 += ps[(size_t)q * RM + i];
-        double v = ((p0 + p1) + (p2 + p3)) * inv;
-        if (a.u) v = fma(-nrm, a.u[s.r0 + i], v);
-        vs[i] = v;
-        a.basis_out[s.r0 + i] = a.q_raw[s.r0 + i] * inv;
-    }
-    __syncthreads();
-    const double* qb = STAGE ? (const double*)Qs : a.Q + s.r0;
-    const int64_t qld = STAGE ? (int64_t)RM : a.ldq;
-    for (int pass = 0; pass < 2; ++pass) {
-        // per-slab partials of Q^T v: one thread per basis vector, 4 chains
-        for (int m = threadIdx.x; m < M; m += SL_THREADS) {
-            const double* q = qb + (int64_t)m * qld;
-            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-            int i = 0;
-            for (; i + 3 < R; i += 4) {
-                a0 = fma(q[i], vs[i], a0);
-                a1 = fma(q[i + 1], vs[i + 1], a1);
-                a2 = fma(q[i + 2], vs[i + 2], a2);
-                a3 = fma(q[i + 3], vs[i + 3], a3);
-            }
-            for (; i < R; ++i) a0 = fma(q[i], vs[i], a0);
-            a.hpart[(int64_t)m * gridDim.x + blockIdx.x] = (a0 + a1) + (a2 + a3);
-        }
-        // h = Q^T v: the partials are summed inside the barrier (fixed order)
-        if (!grid_reduce_sync(stt, a.bar, a.bar_group, a.budget, a.hpart, a.gpart, a.h, M)) return;
-        for (int m = threadIdx.x; m < M; m += SL_THREADS) hs[m] = __ldcg(a.h + m);
-        __syncthreads();
-        // v -= Q h: thread (row, group of basis vectors), two chains each
-        const int row = threadIdx.x % UPD_ROWS;
-        const int grp = threadIdx.x / UPD_ROWS;
-        for (int base = 0; base < R; base += UPD_ROWS) {
-            const int i = base + row;
-            double c0 = 0.0, c1 = 0.0;
-            if (i < R) {
-                const double* q = qb + i;
-                int m = grp;
-                for (; m + UPD_GROUPS < M; m += 2 * UPD_GROUPS) {
-                    c0 = fma(q[(int64_t)m * qld], hs[m], c0);
-                    c1 = fma(q[(int64_t)(m + UPD_GROUPS) * qld], hs[m + UPD_GROUPS], c1);
+    const double inv = inv_s;
+    for (int i = threadIdx.x; i < R; i += SL_THREADS) a.basis_out[s.r0 + i] = qs[i] * inv;
+    if (M > 0) {
+        const double* qb = STAGE ? (const double*)Qs : a.Q + s.r0;
+        const int64_t qld = STAGE ? (int64_t)RM : a.ldq;
+        for (int pass = 0; pass < 2; ++pass) {
+            // per-slab partials of Q^T v': SPLIT threads per basis vector (rows k, k+SPLIT, ...)
+            for (int p = threadIdx.x; p < SPLIT * M; p += SL_THREADS) {
+                const int m = p % M, k = p / M;
+                const double* q = qb + (int64_t)m * qld;
+                double c0 = 0.0, c1 = 0.0;
+                int i = k;
+                for (; i + SPLIT < R; i += 2 * SPLIT) {
+                    c0 = fma(q[i], vs[i], c0);
+                    c1 = fma(q[i + SPLIT], vs[i + SPLIT], c1);
                 }
-                for (; m < M; m += UPD_GROUPS) c0 = fma(q[(int64_t)m * qld], hs[m], c0);
+                if (i < R) c0 = fma(q[i], vs[i], c0);
+                d4[(size_t)k * M + m] = c0 + c1;
             }
-            red[grp * UPD_ROWS + row] = c0 + c1;
             __syncthreads();
-            if (grp == 0 && i < R) {
-                double t = 0.0;
+            for (int m = threadIdx.x; m < M; m += SL_THREADS)
+                a.hpart[(int64_t)m * gridDim.x + blockIdx.x] = (d4[m] + d4[M + m]) + (d4[2 * M + m] + d4[3 * M + m]);
+            // hs = Q^T v': one grid barrier that also sums the partials (fixed order)
+            if (!grid_reduce_sync(stt, a.bar, a.bar_group, a.budget, a.epoch0 + pass + 1, a.hpart, a.gpart, hs, M))
+                return;
+            // v' -= Q hs: thread (row, group of basis vectors), two chains each
+            const int row = threadIdx.x % UPD_ROWS;
+            const int grp = threadIdx.x / UPD_ROWS;
+            for (int base = 0; base < R; base += UPD_ROWS) {
+                const int i = base + row;
+                double c0 = 0.0, c1 = 0.0;
+                if (i < R) {
+                    const double* q = qb + i;
+                    int m = grp;
+                    for (; m + UPD_GROUPS < M; m += 2 * UPD_GROUPS) {
+                        c0 = fma(q[(int64_t)m * qld], hs[m], c0);
+                        c1 = fma(q[(int64_t)(m + UPD_GROUPS) * qld], hs[m + UPD_GROUPS], c1);
+                    }
+                    for (; m < M; m += UPD_GROUPS) c0 = fma(q[(int64_t)m * qld], hs[m], c0);
+                }
+                red[grp * UPD_ROWS + row] = c0 + c1;
+                __syncthreads();
+                if (grp == 0 && i < R) {
+                    double t = 0.0;
 #pragma unroll
-                for (int gq = 0; gq < UPD_GROUPS; ++gq) t += red[gq * UPD_ROWS + row];
-                vs[i] -= t;
+                    for (int gq = 0; gq < UPD_GROUPS; ++gq) t += red[gq * UPD_ROWS + row];
+                    vs[i] -= t;
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
+    } else if (!grid_reduce_sync(stt, a.bar, a.bar_group, a.budget, a.epoch0 + 1, a.hpart, a.gpart, hs, 0)) {
+        // nothing to reorthogonalize against: a plain barrier, so that no CTA
+        // overwrites npart below while another still reads it above
+        return;
     }
-    // ---- store v (+ FP32 copy) and the |v|^2 partials
+    // ---- store v = v' inv (+ FP32 copy) and the |v|^2 partials
     double acc = 0.0;
     for (int i = threadIdx.x; i < R; i += SL_THREADS) {
-        const double t = vs[i];
+        const double t = vs[i] * inv;
         a.v[s.r0 + i] = t;
         if (a.v32) a.v32[s.r0 + i] = (float)t;
         acc = fma(t, t, acc);
     }
     acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    if (lane == 0) red[warp] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
@@ -329,7 +358,6 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
     }
 }
 
-// Squared norm partials of an input vector (start of the run) + FP32 copy.
 __global__ void __launch_bounds__(SL_THREADS) k_norm_partials(int64_t n, const double* __restrict__ x,
                                                               double* __restrict__ npart,
                                                               double* __restrict__ copy,
@@ -382,7 +410,8 @@ __global__ void k_reset_state(rbf_dev_state* stt, int steps_done, double beta_no
 constexpr size_t HALF_SMEM_STAGE_MAX = 200 * 1024;
 
 static size_t half_smem_bytes(bool stage, int mcount, int chunks, int rmax) {
-    return ((stage ? (size_t)mcount * rmax : 0) + (size_t)chunks * rmax + rmax + (size_t)mcount) * sizeof(double);
+    return ((stage ? (size_t)mcount * rmax : 0) + (size_t)chunks * rmax + (size_t)(3 + SPLIT) * rmax +
+            (size_t)(SPLIT + 1) * mcount) * sizeof(double);
 }
 
 static int slab_grid(const rbf_ctx* ctx, int64_t n) {
@@ -418,8 +447,7 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
     b += 2 * ws_align((size_t)n * 8);                 // vr, vp
     b += 2 * ws_align((size_t)n * 4);                 // vr32, vp32
     b += ws_align((size_t)(steps + 2) * G * 8);       // hpart
-    b += ws_align((size_t)(steps + 2) * G * 8);       // gpart (at most G groups)
-    b += ws_align((size_t)(steps + 2) * 8);           // h
+    b += ws_align((size_t)2 * (steps + 2) * G * 8);   // gpart (two buffers, at most G groups)
     b += ws_align((size_t)(G + 2) * BAR_STRIDE * 4);  // barrier counters
     b += ws_align((size_t)G * 8);                     // npart
     return b + 4096;
@@ -455,12 +483,11 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
     int bar_group = 1;
     while (bar_group * bar_group < G) ++bar_group;
     const int bar_k = (G + bar_group - 1) / bar_group;
-    double* gpart = wc.take<double>((size_t)(st->capacity + 2) * G);
-    double* h = wc.take<double>((size_t)(st->capacity + 2));
+    double* gpart = wc.take<double>((size_t)2 * (st->capacity + 2) * G);
     unsigned* bar = wc.take<unsigned>((size_t)(bar_k + 2) * BAR_STRIDE);
     RBF_CUDA(ctx, cudaMemsetAsync(bar, 0, (size_t)(bar_k + 2) * BAR_STRIDE * sizeof(unsigned), ctx->stream));
     // shared-memory plan of the half-step kernel: stage the Q slab when it fits
-    const int rmax = (int)((n + G - 1) / G);
+    const int rmax = (int)((n + G - 1) / G) | 1;
     const int chmax = chT > chN ? chT : chN;
     const bool stage = half_smem_bytes(true, st->capacity + 1, chmax, rmax) <= HALF_SMEM_STAGE_MAX;
     {
@@ -502,6 +529,7 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
         RBF_LAUNCHED(ctx, "k_norm_partials");
         q_raw = vp;
     }
+    unsigned epochs = 0;  // barriers on `bar` since it was zeroed
     auto half = [&](int side, int j, int resume, const double* u, const double* qr, double* bout,
                     double* v, float* v32, const double* Q, int64_t ldq, int mcount, int chunks) -> rbf_status {
         HalfArgs a;
@@ -525,11 +553,11 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
         a.mcount = mcount;
         a.hpart = hpart;
         a.gpart = gpart;
-        a.h = h;
         a.npart = npart;
         a.rmax = rmax;
         a.bar = bar;
         a.bar_group = bar_group;
+        a.epoch0 = epochs;
         a.budget = 1LL << 23;
         void* args[] = {&a};
         const size_t smem = half_smem_bytes(stage, mcount, chunks, rmax);
@@ -538,6 +566,7 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
         ctx->launches++;
         if (e != cudaSuccess)
             return rbf_fail(ctx, RBF_ERR_CUDA, "cooperative launch of k_half failed: %s", cudaGetErrorString(e));
+        epochs += mcount > 0 ? 2 : 1;  // two reorthogonalization barriers, or one plain barrier
         return RBF_OK;
     };
     for (int j = j_begin; j <= j_end; ++j) {

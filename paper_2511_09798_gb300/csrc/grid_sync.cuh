@@ -56,21 +56,39 @@ static __device__ bool grid_sync(rbf_dev_state* __restrict__ stt, unsigned* __re
 
 
 // ---------------------------------------------------------------------------
-// Grid barrier that also reduces per-CTA partial sums.  part is [M][G] (CTA b
-// wrote part[m * G + b]); on a true return h[m] holds, for every m < M,
-//   sum over groups q = 0..K-1 (in order) of
-//     ( sum over the CTAs b of group q (in order) of part[m * G + b] ),
-// and is visible to every CTA.  The last CTA to arrive in a group sums that
-// group's columns into gpart[m * K + q]; the last group to arrive sums the K
-// group sums into h and then releases the barrier, so the reduction costs no
-// barrier of its own.  The order of the additions does not depend on which
-// CTA arrives last: the result is deterministic.  Same counters and bounded
-// polling as grid_sync.
+// Grid barrier number `epoch` (1, 2, ... since the counters were zeroed) that
+// also reduces per-CTA partial sums.  part is [M][G] (CTA b wrote
+// part[m * G + b]); on a true return every CTA holds in hs (shared memory)
+//   hs[m] = sum over groups q = 0..K-1 of ( sum over the CTAs b of group q of
+//           part[m * G + b] ),
+// each sum taken in a fixed order (two interleaved chains, then their sum),
+// so the result does not depend on which CTA arrives last.  The counters only
+// grow: the last CTA to arrive in a group (its counter reaches
+// members * epoch) sums the group's columns into gpart (two buffers by epoch
+// parity, so that a slow CTA still reading the previous sums is never
+// overwritten) and then adds 1 to the top counter with release semantics;
+// every CTA waits (acquire) for the top counter to reach K * epoch and sums
+// the K group sums itself.  With M = 0 it is a plain barrier.  Bounded: after
+// `budget` polls it records RBF_ERR_TIMEOUT, stops the run and returns false.
 // ---------------------------------------------------------------------------
+static __device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+static __device__ __forceinline__ void red_add_release_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+static __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 static __device__ bool grid_reduce_sync(rbf_dev_state* __restrict__ stt, unsigned* __restrict__ bar, int group,
-                                        long long budget, const double* __restrict__ part,
-                                        double* __restrict__ gpart, double* __restrict__ h, int M) {
-    __shared__ int role;  // bit 0: last of its group, bit 1: last group
+                                        long long budget, unsigned epoch, const double* __restrict__ part,
+                                        double* __restrict__ gpart, double* __restrict__ hs, int M) {
+    __shared__ int role;
     __shared__ int ok;
     const int G = gridDim.x;
     const int K = (G + group - 1) / group;
@@ -79,50 +97,36 @@ static __device__ bool grid_reduce_sync(rbf_dev_state* __restrict__ stt, unsigne
     const int members = min(group, G - b0);
     unsigned* sub = bar + (size_t)grp * BAR_STRIDE;
     unsigned* top = bar + (size_t)K * BAR_STRIDE;
-    volatile unsigned* gen = bar + (size_t)(K + 1) * BAR_STRIDE;
-    unsigned g0 = 0;
+    double* gp = gpart + (size_t)(epoch & 1u) * (size_t)M * K;
     __syncthreads();
     if (threadIdx.x == 0) {
-        g0 = *gen;
         __threadfence();
-        role = atomicAdd(sub, 1u) == (unsigned)members - 1 ? 1 : 0;
-        __threadfence();
+        role = atom_add_acq_rel_u32(sub, 1u) == (unsigned)members * epoch - 1u ? 1 : 0;
     }
     __syncthreads();
-    if (role & 1) {
+    if (role) {
         for (int m = threadIdx.x; m < M; m += blockDim.x) {
             const double* p = part + (int64_t)m * G + b0;
-            double s = 0.0;
-            for (int b = 0; b < members; ++b) s += __ldcg(p + b);
-            gpart[(int64_t)m * K + grp] = s;
+            double s0 = 0.0, s1 = 0.0;
+            int b = 0;
+            for (; b + 1 < members; b += 2) {
+                s0 += __ldcg(p + b);
+                s1 += __ldcg(p + b + 1);
+            }
+            if (b < members) s0 += __ldcg(p + b);
+            gp[(int64_t)m * K + grp] = s0 + s1;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            atomicExch(sub, 0u);
             __threadfence();
-            role = atomicAdd(top, 1u) == (unsigned)K - 1 ? 3 : 1;
-            __threadfence();
-        }
-        __syncthreads();
-        if (role & 2) {
-            for (int m = threadIdx.x; m < M; m += blockDim.x) {
-                const double* p = gpart + (int64_t)m * K;
-                double s = 0.0;
-                for (int q = 0; q < K; ++q) s += __ldcg(p + q);
-                h[m] = s;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                atomicExch(top, 0u);
-                __threadfence();
-                atomicAdd((unsigned*)gen, 1u);
-            }
+            red_add_release_u32(top, 1u);
         }
     }
     if (threadIdx.x == 0) {
         int good = 1;
         long long it = 0;
-        while (*gen == g0) {
+        const unsigned target = (unsigned)K * epoch;
+        while (ld_acquire_u32(top) < target) {
             if (++it > budget) {
                 good = 0;
                 atomicExch(&stt->info[IN_ERR], (int)RBF_ERR_TIMEOUT);
@@ -130,9 +134,21 @@ static __device__ bool grid_reduce_sync(rbf_dev_state* __restrict__ stt, unsigne
                 break;
             }
         }
-        __threadfence();
         ok = good;
     }
     __syncthreads();
-    return ok != 0;
+    if (!ok) return false;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const double* p = gp + (int64_t)m * K;
+        double s0 = 0.0, s1 = 0.0;
+        int q = 0;
+        for (; q + 1 < K; q += 2) {
+            s0 += __ldcg(p + q);
+            s1 += __ldcg(p + q + 1);
+        }
+        if (q < K) s0 += __ldcg(p + q);
+        hs[m] = s0 + s1;
+    }
+    __syncthreads();
+    return true;
 }
