@@ -1,4 +1,5 @@
-// Assembled matrix-vector products of Algorithm 1: p = A z (row-major GEMV,
+// Assembled matrix-vector products of Algorithm 1: p = A z (row-major GEMV;
+// FP64: an equal share of the entries per warp, partials per row piece; FP32:
 // balanced (row, column-segment) units per warp, partials per segment) and
 // r = A^T w (GEMV^T by row chunks); every partial sum is reduced in a fixed
 // order by the consumer, so results are deterministic.
@@ -23,29 +24,42 @@ __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 
 // ---------------------------------------------------------------------------
-// part[g][i] = sum_{j in column segment g} A_ij x_j: the n x S (row, segment)
-// units are split into equal contiguous ranges, one per warp of the grid, so
-// every resident warp does the same work to within one unit (row-granular
-// work would leave a tail of warps with one row more than the others).
-// Segments start on even columns (16-byte aligned double2 loads).
+// FP64 A x by a flat split of the matrix: warp w (of W active warps) owns the
+// row-major elements [b_w, b_{w+1}) with b_w = floor(n^2 w / W), its column
+// rounded down to even (16-byte aligned double2 loads), so every warp streams
+// the same number of entries to within two.  Each row piece of a warp is
+// reduced across the warp and written to part[slot][row], slot = w minus the
+// first warp that touches the row; the warp holding the end of a row writes
+// zeros into the row's remaining slots, so part[0 .. chunks-1][row] always sum
+// to (A x)_row.  n^2 W stays far below 2^63 for any matrix that fits in
+// device memory.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(GN_THREADS) k_gemv_nseg_f64(
-    const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x, int S,
-    int64_t seglen, double* __restrict__ part, const int* __restrict__ done) {
+__device__ __forceinline__ int64_t flat_bound(int64_t n, int64_t W, int64_t w) {
+    if (w >= W) return n * n;
+    const int64_t b = n * n * w / W;
+    const int64_t r = b / n;
+    return r * n + ((b - r * n) & ~(int64_t)1);
+}
+
+__global__ void __launch_bounds__(GN_THREADS) k_gemv_flat_f64(
+    const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x, int64_t W, int chunks,
+    double* __restrict__ part, const int* __restrict__ done) {
     if (gkb_done(done)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t W = (int64_t)gridDim.x * (GN_THREADS / 32);
     const int64_t w = (int64_t)blockIdx.x * (GN_THREADS / 32) + warp;
-    const int64_t U = n * S;
-    const int64_t u0 = U * w / W, u1 = U * (w + 1) / W;
-    for (int64_t u = u0; u < u1; ++u) {
-        const int64_t i = u / S;
-        const int g = (int)(u - i * S);
-        const int64_t c0 = (int64_t)g * seglen;
-        const int64_t c1 = min(n, c0 + seglen);
-        const double2* __restrict__ row = reinterpret_cast<const double2*>(A + i * lda + c0);
-        const double2* __restrict__ xv = reinterpret_cast<const double2*>(x + c0);
-        const int64_t nvec = (c1 - c0) >> 1;
+    if (w >= W) return;
+    const int64_t e0 = flat_bound(n, W, w), e1 = flat_bound(n, W, w + 1);
+    if (e1 <= e0) return;
+    const int64_t r0 = e0 / n, r1 = (e1 - 1) / n;
+    for (int64_t r = r0; r <= r1; ++r) {
+        const int64_t cs = r == r0 ? e0 - r * n : 0;
+        const int64_t ce = r == r1 ? e1 - r * n : n;
+        int64_t wf = w;  // first warp of the row
+        while (wf > 0 && flat_bound(n, W, wf) > r * n) --wf;
+        const int slot = (int)(w - wf);
+        const double2* __restrict__ row = reinterpret_cast<const double2*>(A + r * lda + cs);
+        const double2* __restrict__ xv = reinterpret_cast<const double2*>(x + cs);
+        const int64_t nvec = (ce - cs) >> 1;
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         int64_t v = lane;
         for (; v + 96 < nvec; v += 128) {
@@ -62,9 +76,13 @@ __global__ void __launch_bounds__(GN_THREADS) k_gemv_nseg_f64(
             double2 m0 = ld_stream(row + v), x0 = __ldg(xv + v);
             a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
         }
-        if (((c1 - c0) & 1) && lane == 0) a1 = fma(A[i * lda + c1 - 1], __ldg(x + c1 - 1), a1);
+        if (((ce - cs) & 1) && lane == 0) a1 = fma(A[r * lda + ce - 1], __ldg(x + ce - 1), a1);
         const double acc = warp_sum((a0 + a1) + (a2 + a3));
-        if (lane == 0) part[(int64_t)g * n + i] = acc;
+        if (lane == 0) {
+            part[(int64_t)slot * n + r] = acc;
+            if (ce == n)
+                for (int s2 = slot + 1; s2 < chunks; ++s2) part[(int64_t)s2 * n + r] = 0.0;
+        }
     }
 }
 
@@ -114,8 +132,11 @@ __global__ void __launch_bounds__(GN_THREADS) k_gemv_nseg_f32(
 }
 
 // ---------------------------------------------------------------------------
-// part[q][c] = sum_{i in row chunk q} A_ic x_i for the columns of this CTA's panel.
+// part[q][c] = sum_{i in row chunk q} A_ic x_i for the columns of this CTA's
+// panel; 8 rows of A are loaded before their 16 FMAs (8 independent pairs of
+// accumulators), which keeps enough loads in flight to feed the FP64 pipe.
 // ---------------------------------------------------------------------------
+constexpr int GT_UNROLL = 8;
 __global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f64(
     const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x,
     int panel_cols, int chunks, double* __restrict__ part, const int* __restrict__ done) {
@@ -136,25 +157,34 @@ __global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f64(
         return;
     }
     const double* __restrict__ base = A + i0 * lda + c;
-    double ax0 = 0, ay0 = 0, ax1 = 0, ay1 = 0, ax2 = 0, ay2 = 0, ax3 = 0, ay3 = 0;
+    double ax[GT_UNROLL], ay[GT_UNROLL];
+#pragma unroll
+    for (int u = 0; u < GT_UNROLL; ++u) ax[u] = ay[u] = 0.0;
     const int64_t rows = i1 - i0;
     int64_t r = 0;
-    for (; r + 3 < rows; r += 4) {
-        double2 m0 = ld_stream(reinterpret_cast<const double2*>(base + (r + 0) * lda));
-        double2 m1 = ld_stream(reinterpret_cast<const double2*>(base + (r + 1) * lda));
-        double2 m2 = ld_stream(reinterpret_cast<const double2*>(base + (r + 2) * lda));
-        double2 m3 = ld_stream(reinterpret_cast<const double2*>(base + (r + 3) * lda));
-        ax0 = fma(m0.x, xs[r], ax0); ay0 = fma(m0.y, xs[r], ay0);
-        ax1 = fma(m1.x, xs[r + 1], ax1); ay1 = fma(m1.y, xs[r + 1], ay1);
-        ax2 = fma(m2.x, xs[r + 2], ax2); ay2 = fma(m2.y, xs[r + 2], ay2);
-        ax3 = fma(m3.x, xs[r + 3], ax3); ay3 = fma(m3.y, xs[r + 3], ay3);
+    for (; r + GT_UNROLL - 1 < rows; r += GT_UNROLL) {
+        double2 m[GT_UNROLL];
+#pragma unroll
+        for (int u = 0; u < GT_UNROLL; ++u) m[u] = ld_stream(reinterpret_cast<const double2*>(base + (r + u) * lda));
+#pragma unroll
+        for (int u = 0; u < GT_UNROLL; ++u) {
+            ax[u] = fma(m[u].x, xs[r + u], ax[u]);
+            ay[u] = fma(m[u].y, xs[r + u], ay[u]);
+        }
     }
     for (; r < rows; ++r) {
         double2 m0 = ld_stream(reinterpret_cast<const double2*>(base + r * lda));
-        ax0 = fma(m0.x, xs[r], ax0); ay0 = fma(m0.y, xs[r], ay0);
+        ax[0] = fma(m0.x, xs[r], ax[0]);
+        ay[0] = fma(m0.y, xs[r], ay[0]);
     }
-    part[(int64_t)q * n + c] = (ax0 + ax1) + (ax2 + ax3);
-    if (c + 1 < n) part[(int64_t)q * n + c + 1] = (ay0 + ay1) + (ay2 + ay3);
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int u = 0; u < GT_UNROLL; ++u) {
+        sx += ax[u];
+        sy += ay[u];
+    }
+    part[(int64_t)q * n + c] = sx;
+    if (c + 1 < n) part[(int64_t)q * n + c + 1] = sy;
 }
 
 __global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f32(
@@ -236,7 +266,7 @@ size_t gemv_ws_bytes(const rbf_ctx* ctx, int64_t n) {
     int pc4, pn4, ch4;
     plan_t(ctx, n, 4, &pc4, &pn4, &ch4);
     int c = ch > ch4 ? ch : ch4;
-    if (c < 8) c = 8;  // column segments of the FP64 A x
+    if (c < 8) c = 8;  // partial-sum rows of the FP64 A x (at most 8)
     return ws_align((size_t)c * n * sizeof(double)) + ws_align((size_t)n * sizeof(float));
 }
 
@@ -246,16 +276,13 @@ int gemv_t_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
     return ch;
 }
 
-// FP64 A x: grid = one wave of resident CTAs; S column segments per row chosen
-// so that the n S units divide as evenly as possible over the grid's warps
-// (efficiency x / ceil(x) with x = n S / warps), segments of >= 256 columns.
-static void gemv_nseg_plan(const rbf_ctx* ctx, int64_t n, bool fp64, int* grid, int* S, int64_t* seglen) {
+static int gemv_n_occupancy(const rbf_ctx* ctx, bool fp64) {
     static int occ[2][64] = {{0}};
     const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
     int& o = occ[fp64 ? 0 : 1][dev];
     if (!o) {
         int a = 0;
-        const cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_nseg_f64, GN_THREADS, 0)
+        const cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_flat_f64, GN_THREADS, 0)
                                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_nseg_f32, GN_THREADS, 0);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -263,7 +290,35 @@ static void gemv_nseg_plan(const rbf_ctx* ctx, int64_t n, bool fp64, int* grid, 
         }
         o = a < 1 ? 1 : a;
     }
-    int64_t g = (int64_t)ctx->sm_count * o;
+    return o;
+}
+
+// FP64 A x (flat split): W active warps, at most one wave of resident CTAs,
+// at least 256 entries per warp, and few enough warps that no row is split
+// into more than 8 pieces (the partial-sum rows the workspace provides).  A
+// row of n entries meets at most ceil(n / (per - 2)) + 1 warp ranges, per =
+// floor(n^2 / W) (each boundary is rounded down by at most one entry).
+static void gemv_flat_plan(const rbf_ctx* ctx, int64_t n, int* grid, int64_t* W_out, int* chunks) {
+    const int64_t e = n * n;
+    int64_t W = (int64_t)ctx->sm_count * gemv_n_occupancy(ctx, true) * (GN_THREADS / 32);
+    if (W > e / 256) W = e / 256;
+    if (W < 1) W = 1;
+    auto pieces = [&](int64_t w) -> int64_t {
+        if (w <= 1) return 1;
+        const int64_t per = e / w;
+        return (n + per - 3) / (per - 2) + 1;
+    };
+    while (W > 1 && pieces(W) > 8) --W;
+    *W_out = W;
+    *grid = (int)((W + GN_THREADS / 32 - 1) / (GN_THREADS / 32));
+    *chunks = (int)pieces(W);
+}
+
+// FP32 A x: grid = one wave of resident CTAs; S column segments per row chosen
+// so that the n S units divide as evenly as possible over the grid's warps
+// (efficiency x / ceil(x) with x = n S / warps), segments of >= 256 columns.
+static void gemv_nseg_plan(const rbf_ctx* ctx, int64_t n, int* grid, int* S, int64_t* seglen) {
+    int64_t g = (int64_t)ctx->sm_count * gemv_n_occupancy(ctx, false);
     const int64_t rows_min = (n + 7) / 8;
     if (g > rows_min) g = rows_min;
     if (g < 1) g = 1;
@@ -280,8 +335,7 @@ static void gemv_nseg_plan(const rbf_ctx* ctx, int64_t n, bool fp64, int* grid, 
         }
     }
     int64_t len = (n + best - 1) / best;
-    const int64_t al = fp64 ? 2 : 4;  // segments start on 16-byte boundaries
-    len = (len + al - 1) / al * al;
+    len = (len + 3) / 4 * 4;  // segments start on 16-byte boundaries
     *grid = (int)g;
     *S = (int)((n + len - 1) / len);
     *seglen = len;
@@ -289,21 +343,28 @@ static void gemv_nseg_plan(const rbf_ctx* ctx, int64_t n, bool fp64, int* grid, 
 
 int gemv_n_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
     int g, S;
+    if (op->precision == RBF_FP64) {
+        int64_t W;
+        gemv_flat_plan(ctx, op->n, &g, &W, &S);
+        return S;
+    }
     int64_t len;
-    gemv_nseg_plan(ctx, op->n, op->precision == RBF_FP64, &g, &S, &len);
+    gemv_nseg_plan(ctx, op->n, &g, &S, &len);
     return S;
 }
 
 rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, const float* x32, double* part,
                          const int* done) {
     int g, S;
-    int64_t len;
-    gemv_nseg_plan(ctx, op->n, op->precision == RBF_FP64, &g, &S, &len);
     if (op->precision == RBF_FP64) {
-        k_gemv_nseg_f64<<<g, GN_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x, S, len, part,
+        int64_t W;
+        gemv_flat_plan(ctx, op->n, &g, &W, &S);
+        k_gemv_flat_f64<<<g, GN_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x, W, S, part,
                                                            done);
-        RBF_LAUNCHED(ctx, "k_gemv_nseg_f64");
+        RBF_LAUNCHED(ctx, "k_gemv_flat_f64");
     } else {
+        int64_t len;
+        gemv_nseg_plan(ctx, op->n, &g, &S, &len);
         k_gemv_nseg_f32<<<g, GN_THREADS, 0, ctx->stream>>>((const float*)op->d_A, op->lda, op->n, x32, S, len, part,
                                                            done);
         RBF_LAUNCHED(ctx, "k_gemv_nseg_f32");

@@ -440,7 +440,7 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
     int ch3 = gemv_t_chunks(ctx, &fake);
     if (ch2 > ch) ch = ch2;
     if (ch3 > ch) ch = ch3;
-    if (ch < 8) ch = 8;  // column segments of the FP64 A x (at most 8)
+    if (ch < 8) ch = 8;  // partial-sum rows of the FP64 A x (at most 8)
     const int G = slab_grid(ctx, n);
     size_t b = 0;
     b += ws_align((size_t)ch * n * 8);                // partials
