@@ -8,15 +8,11 @@ namespace {
 constexpr int AS_TN = 256;  // columns per CTA (one per thread)
 constexpr int AS_TM = 16;   // rows per CTA
 
-// Entry of A in FP64.  s = r^2 + c^2; interior rows: L Phi = Delta Phi + k^2 Phi
+// Entry of A.  s = r^2 + c^2; interior rows: L Phi = Delta Phi + k^2 Phi
 // = (c^2 + s (2 + k^2 s)) s^{-3/2} (since 2 r^2 + 3 c^2 = 2 s + c^2);
 // boundary rows: Phi = s^{1/2}.
-__device__ __forceinline__ double mq_entry_f64(double dx, double dy, double dz, double c2, double k2,
-                                               bool interior) {
-    double s = fma(dx, dx, fma(dy, dy, fma(dz, dz, c2)));
-    double rs = rsqrt_f64(s);
-    if (!interior) return s * rs;
-    double poly = fma(s, fma(k2, s, 2.0), c2);
+__device__ __forceinline__ double lphi_from(double s, double rs, double c2, double k2) {
+    const double poly = fma(s, fma(k2, s, 2.0), c2);
     return (rs * rs) * (rs * poly);
 }
 
@@ -29,10 +25,10 @@ __device__ __forceinline__ float mq_entry_f32(float dx, float dy, float dz, floa
     return (rs * rs) * (rs * poly);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(AS_TN) k_assemble(const double* __restrict__ X, int64_t n,
-                                                    int64_t ni, double c, double k, double scale,
-                                                    T* __restrict__ A, int64_t lda) {
+// FP32 assembly (mixed precision): one column per thread, AS_TM rows per CTA.
+__global__ void __launch_bounds__(AS_TN) k_assemble_f32(const double* __restrict__ X, int64_t n, int64_t ni,
+                                                        double c, double k, double scale, float* __restrict__ A,
+                                                        int64_t lda) {
     __shared__ double rx[AS_TM], ry[AS_TM], rz[AS_TM];
     const int64_t j = (int64_t)blockIdx.x * AS_TN + threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.y * AS_TM;
@@ -50,15 +46,69 @@ __global__ void __launch_bounds__(AS_TN) k_assemble(const double* __restrict__ X
     const int rows = (int)min((int64_t)AS_TM, n - i0);
     for (int r = 0; r < rows; ++r) {
         const int64_t i = i0 + r;
-        T v;
-        if constexpr (sizeof(T) == 8) {
-            v = mq_entry_f64(rx[r] - xj, ry[r] - yj, rz[r] - zj, c2, k2, i < ni) * scale;
-        } else {
-            v = mq_entry_f32((float)rx[r] - (float)xj, (float)ry[r] - (float)yj,
-                             (float)rz[r] - (float)zj, (float)c2, (float)k2, i < ni) *
-                (float)scale;
+        A[i * lda + j] = mq_entry_f32((float)rx[r] - (float)xj, (float)ry[r] - (float)yj, (float)rz[r] - (float)zj,
+                                      (float)c2, (float)k2, i < ni) * (float)scale;
+    }
+}
+
+// FP64 assembly by pairs of 32-row tiles.  The entries (i, j) and (j, i)
+// share s = |X_i - X_j|^2 + c^2 and 1/sqrt(s) (the squared differences do not
+// change sign), and are equal whenever rows i and j are of the same kind, so
+// one CTA per tile pair (I <= J) computes s and 1/sqrt(s) once for the 32 x 32
+// node pairs, writes tile (I, J) row by row and tile (J, I) through a
+// shared-memory transpose (coalesced stores in both).  CTAs below the
+// diagonal return at once.
+constexpr int SY_T = 32;     // tile edge
+constexpr int SY_ROWS = 8;   // thread rows per CTA
+
+__global__ void __launch_bounds__(SY_T * SY_ROWS) k_assemble_sym_f64(const double* __restrict__ X, int64_t n,
+                                                                      int64_t ni, double c, double k, double scale,
+                                                                      double* __restrict__ A, int64_t lda) {
+    __shared__ double tr[SY_T][SY_T + 1];
+    __shared__ double pi[3][SY_T], pj[3][SY_T];
+    const int bi = blockIdx.y, bj = blockIdx.x;
+    if (bi > bj) return;
+    const int tx = threadIdx.x % SY_T, ty = threadIdx.x / SY_T;
+    const int64_t I0 = (int64_t)bi * SY_T, J0 = (int64_t)bj * SY_T;
+    if (threadIdx.x < SY_T) {
+        const int64_t i = I0 + threadIdx.x, j = J0 + threadIdx.x;
+        for (int d = 0; d < 3; ++d) {
+            pi[d][threadIdx.x] = i < n ? X[d * n + i] : 0.0;
+            pj[d][threadIdx.x] = j < n ? X[d * n + j] : 0.0;
         }
-        A[i * lda + j] = v;
+    }
+    __syncthreads();
+    const double c2 = c * c, k2 = k * k;
+    const int64_t j = J0 + tx;
+    const bool jint = j < ni;
+    const bool scaled = scale != 1.0;
+#pragma unroll
+    for (int rr = 0; rr < SY_T / SY_ROWS; ++rr) {
+        const int li = ty + SY_ROWS * rr;
+        const int64_t i = I0 + li;
+        double eji = 0.0;
+        if (i < n && j < n) {
+            const double dx = pi[0][li] - pj[0][tx], dy = pi[1][li] - pj[1][tx], dz = pi[2][li] - pj[2][tx];
+            const double s = fma(dx, dx, fma(dy, dy, fma(dz, dz, c2)));
+            const double rs = rsqrt_f64(s);
+            const bool iint = i < ni;
+            double eij = iint ? lphi_from(s, rs, c2, k2) : s * rs;
+            eji = jint == iint ? eij : (jint ? lphi_from(s, rs, c2, k2) : s * rs);
+            if (scaled) {
+                eij *= scale;
+                eji *= scale;
+            }
+            A[i * lda + j] = eij;
+        }
+        tr[li][tx] = eji;
+    }
+    if (bi == bj) return;
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < SY_T / SY_ROWS; ++rr) {
+        const int lj = ty + SY_ROWS * rr;
+        const int64_t jr = J0 + lj, ic = I0 + tx;
+        if (jr < n && ic < n) A[jr * lda + ic] = tr[tx][lj];
     }
 }
 
@@ -112,13 +162,17 @@ rbf_status launch_assemble(rbf_ctx* ctx, const rbf_operator* op) {
     dim3 grid((unsigned)((n + AS_TN - 1) / AS_TN), (unsigned)((n + AS_TM - 1) / AS_TM));
     if (grid.y > 65535u) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large for assembly grid");
     const double scale = op->form == RBF_FORM_EPS ? 1.0 / op->c : 1.0;
-    if (op->precision == RBF_FP64)
-        k_assemble<double><<<grid, AS_TN, 0, ctx->stream>>>(op->d_nodes, n, op->n_interior, op->c,
-                                                            op->k, scale, (double*)op->d_A, op->lda);
-    else
-        k_assemble<float><<<grid, AS_TN, 0, ctx->stream>>>(op->d_nodes, n, op->n_interior, op->c,
-                                                           op->k, scale, (float*)op->d_A, op->lda);
-    RBF_LAUNCHED(ctx, "k_assemble");
+    if (op->precision == RBF_FP64) {
+        const int64_t nt = (n + SY_T - 1) / SY_T;
+        if (nt > 65535) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large for assembly grid");
+        k_assemble_sym_f64<<<dim3((unsigned)nt, (unsigned)nt), SY_T * SY_ROWS, 0, ctx->stream>>>(
+            op->d_nodes, n, op->n_interior, op->c, op->k, scale, (double*)op->d_A, op->lda);
+        RBF_LAUNCHED(ctx, "k_assemble_sym_f64");
+        return RBF_OK;
+    }
+    k_assemble_f32<<<grid, AS_TN, 0, ctx->stream>>>(op->d_nodes, n, op->n_interior, op->c, op->k, scale,
+                                                    (float*)op->d_A, op->lda);
+    RBF_LAUNCHED(ctx, "k_assemble_f32");
     return RBF_OK;
 }
 
