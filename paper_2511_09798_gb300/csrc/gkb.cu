@@ -20,6 +20,7 @@
 // order), so repeated runs are bitwise identical.  Grid barriers poll a bounded
 // number of times and report RBF_ERR_TIMEOUT instead of hanging.  Once a
 // breakdown is found a device flag makes every later kernel return at once.
+#include <algorithm>
 #include <cfloat>
 
 #include "common.cuh"
@@ -193,8 +194,8 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
     double* vs = ps + (size_t)a.chunks * RM;          // [RM]  v' of the slab
     double* us = vs + RM;                             // [RM]  u of the slab
     double* qs = us + RM;                             // [RM]  q_raw of the slab
-    double* r4 = qs + RM;                             // [SPLIT][RM]
-    double* d4 = r4 + (size_t)SPLIT * RM;             // [SPLIT][M]
+    double* r4 = qs + RM;                             // [SPLIT][RM]  (partial sums only)
+    double* d4 = r4;                                  // [SPLIT][M]   (passes only: shares r4's space)
     double* hs = d4 + (size_t)SPLIT * M;              // [M]   Q^T v'
     // ---- stage the slab's product partials, u, q_raw and (STAGE) its rows of Q
     for (int q = warp; q < a.chunks; q += SL_WARPS)
@@ -407,11 +408,13 @@ __global__ void k_reset_state(rbf_dev_state* stt, int steps_done, double beta_no
 
 }  // namespace
 
-constexpr size_t HALF_SMEM_STAGE_MAX = 200 * 1024;
+// dynamic shared memory of the half-step kernel when the Q slab is staged:
+// the 227 KB a CTA may opt into, less about 2 KB of static shared memory
+constexpr size_t HALF_SMEM_STAGE_MAX = 224 * 1024;
 
 static size_t half_smem_bytes(bool stage, int mcount, int chunks, int rmax) {
-    return ((stage ? (size_t)mcount * rmax : 0) + (size_t)chunks * rmax + (size_t)(3 + SPLIT) * rmax +
-            (size_t)(SPLIT + 1) * mcount) * sizeof(double);
+    const size_t scratch = std::max((size_t)SPLIT * rmax, (size_t)(SPLIT + 1) * mcount);
+    return ((stage ? (size_t)mcount * rmax : 0) + (size_t)chunks * rmax + (size_t)3 * rmax + scratch) * sizeof(double);
 }
 
 static int slab_grid(const rbf_ctx* ctx, int64_t n) {
