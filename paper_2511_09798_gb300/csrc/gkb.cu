@@ -492,15 +492,18 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
     // shared-memory plan of the half-step kernel: stage the Q slab when it fits
     const int rmax = (int)((n + G - 1) / G) | 1;
     const int chmax = chT > chN ? chT : chN;
-    const bool stage = half_smem_bytes(true, st->capacity + 1, chmax, rmax) <= HALF_SMEM_STAGE_MAX;
+    // The Q slab is staged in every half-step whose slab fits (mcount grows with
+    // the step, so long runs on large N stage their early steps only); the
+    // unstaged kernel must fit for the largest basis.
     {
-        const size_t need = half_smem_bytes(stage, st->capacity + 1, chmax, rmax);
-        if (need > 48 * 1024) {
-            RBF_CUDA(ctx, cudaFuncSetAttribute(stage ? (const void*)k_half<true> : (const void*)k_half<false>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
-        }
-        if (need > HALF_SMEM_STAGE_MAX + 64 * 1024)
+        const size_t need = half_smem_bytes(false, st->capacity + 1, chmax, rmax);
+        if (need > HALF_SMEM_STAGE_MAX)
             return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "half-step shared memory too large (%zu bytes)", need);
+        if (need > 48 * 1024)
+            RBF_CUDA(ctx, cudaFuncSetAttribute((const void*)k_half<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)need));
+        RBF_CUDA(ctx, cudaFuncSetAttribute((const void*)k_half<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)HALF_SMEM_STAGE_MAX));
     }
     double* npart = wc.take<double>((size_t)G);
     rbf_dev_state* dst = ctx->d_state;
@@ -563,6 +566,7 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
         a.epoch0 = epochs;
         a.budget = 1LL << 23;
         void* args[] = {&a};
+        const bool stage = half_smem_bytes(true, mcount, chunks, rmax) <= HALF_SMEM_STAGE_MAX;
         const size_t smem = half_smem_bytes(stage, mcount, chunks, rmax);
         cudaError_t e = cudaLaunchCooperativeKernel(stage ? (const void*)k_half<true> : (const void*)k_half<false>,
                                                     dim3(G), dim3(SL_THREADS), args, smem, s);
