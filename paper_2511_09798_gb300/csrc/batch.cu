@@ -366,18 +366,19 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
             const int rows = (int)(seg_i1[sx] - i0);
             const int cslot = blockIdx.x - I.cfirst;
             const double* v = vs + seg_base[sx];
-            for (int m = threadIdx.x; m < M; m += HB_THREADS) {
+            // one warp per basis vector, lanes along the rows (coalesced loads of
+            // the basis column), reduced across the warp in a fixed order
+            for (int m = warp; m < M; m += HB_WARPS) {
                 const double* q = Q + (int64_t)m * I.n + i0;
-                double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-                int i = 0;
-                for (; i + 3 < rows; i += 4) {
+                double a0 = 0.0, a1 = 0.0;
+                int i = lane;
+                for (; i + 32 < rows; i += 64) {
                     a0 = fma(q[i], v[i], a0);
-                    a1 = fma(q[i + 1], v[i + 1], a1);
-                    a2 = fma(q[i + 2], v[i + 2], a2);
-                    a3 = fma(q[i + 3], v[i + 3], a3);
+                    a1 = fma(q[i + 32], v[i + 32], a1);
                 }
-                for (; i < rows; ++i) a0 = fma(q[i], v[i], a0);
-                a.hpart_all[I.hoff + (int64_t)m * I.ncta + cslot] = (a0 + a1) + (a2 + a3);
+                if (i < rows) a0 = fma(q[i], v[i], a0);
+                const double t = warp_sum(a0 + a1);
+                if (lane == 0) a.hpart_all[I.hoff + (int64_t)m * I.ncta + cslot] = t;
             }
         }
         if (!grid_sync_b(a.stt, a.bar, a.bar_group, a.budget)) return;
