@@ -168,10 +168,10 @@ struct HalfArgs {
 // against Q (classical Gram-Schmidt), ending with the |v|^2 partials.
 //
 // The work runs on v' = v / inv (inv = 1 / nrm, or 1 for a resumed run):
-// v' = sum(partials) - (nrm / inv) u with nrm / inv = |q_raw|^2, so the square
-// root, the division and the breakdown test (one thread of the last warp) run
-// beside the partial sums instead of before them; Gram-Schmidt is linear in
-// v', and v = v' inv is formed when v is stored.  The CTA's slabs of the
+// v' = sum(partials) - (nrm / inv) u with nrm / inv = |q_raw|^2 (beta_j for a
+// resumed run), so the square root, the division and the breakdown test (one
+// thread of the last warp) run beside the partial sums instead of before them;
+// Gram-Schmidt is linear in v', and v = v' inv is formed when v is stored.  The CTA's slabs of the
 // product partials, u, q_raw and (STAGE) Q are copied to shared memory with
 // cp.async; without STAGE the passes read Q from L2.  Partial sums and dot
 // products are split over SPLIT threads per row or per basis vector so that
