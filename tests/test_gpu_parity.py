@@ -93,7 +93,9 @@ def _products(ctx, R, op, n, seed):
     return x, y0.cpu().numpy(), y1.cpu().numpy()
 
 
-@pytest.mark.parametrize("n", [5, 257, 1003, 4099])
+# n = 1, 2, 5: one warp takes the whole matrix; n = 1116: rows split into up to
+# 6 warp pieces (the most for this grid); 4099: ragged against every tile size
+@pytest.mark.parametrize("n", [1, 2, 5, 64, 257, 1003, 1116, 4099])
 def test_matvec_fp64(ctx, R, n):
     ns = random_nodes(n, (2 * n) // 3, n + 1)
     op, _, _ = gpu_matrix(ctx, R, ns, 0.2, 4.0)
