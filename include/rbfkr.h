@@ -91,6 +91,11 @@ typedef struct {
                                 with CUDA events, no synchronisation (rbf_counters) */
     int svd_method;          /* full SVD: 0 Householder bidiagonalization + tridiagonal
                                 SVD (default), 1 one-sided Jacobi */
+    int64_t wait_budget;     /* polls a device-side wait (grid barrier) makes before it
+                                gives up: the run stops and the call returns
+                                RBF_ERR_TIMEOUT instead of waiting for ever (default
+                                2^23, several seconds; a tiny value forces the timeout
+                                path, which leaves the context usable) */
 } rbf_options;
 
 /* Operator description; filled by rbf_operator_init. */
@@ -123,7 +128,9 @@ typedef struct {
     int64_t n;
     int steps_done;   /* l: completed steps */
     int breakdown;    /* 0 none; 1 alpha_j <= tau (l = j-1); 2 beta_{j+1} <= tau (l = j,
-                         beta_{l+1} = 0, w_{l+1} = 0) */
+                         beta_{l+1} = 0, w_{l+1} = 0); 3 a norm was not finite (NaN or
+                         Inf in f, the nodes or the operator): the run stops as for 1
+                         (alpha_j) or 2 (beta_{j+1}), l counts the steps before it */
     double c_hat;     /* running estimate of |A|_2 used by the breakdown test */
 } rbf_gkb_state;
 

@@ -821,7 +821,7 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     a.stt = dst;
     a.bar = w.bar;
     a.bar_group = P.bar_group;
-    a.budget = 1LL << 23;
+    a.budget = ctx->opt.wait_budget;
     a.rmax = P.rmax;
     a.qraw_all = w.vp;
     a.v32_all = w.vp32;

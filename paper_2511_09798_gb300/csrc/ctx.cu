@@ -79,6 +79,7 @@ rbf_status rbf_create(rbf_ctx** out, int device, void* cuda_stream, const rbf_op
     }
     if (ctx->opt.breakdown_factor <= 0) ctx->opt.breakdown_factor = 64.0;
     if (ctx->opt.cluster_tol <= 0) ctx->opt.cluster_tol = 1e-3;
+    if (ctx->opt.wait_budget <= 0) ctx->opt.wait_budget = 1LL << 23;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_state, sizeof(rbf_dev_state));

@@ -104,14 +104,17 @@ __global__ void k_finalize(rbf_dev_state* __restrict__ stt, const double* __rest
             }
         } else {  // beta_j closes step j-1 (c_hat slot j&1 in, both slots out)
             double ch = fmax(sc[SC_CHAT0 + (j & 1)], hypot(alpha[j - 2], nrm));
-            sc[SC_CHAT0] = ch;
-            sc[SC_CHAT1] = ch;
+            const bool nonfinite = !isfinite(nrm);
+            if (!nonfinite) {
+                sc[SC_CHAT0] = ch;
+                sc[SC_CHAT1] = ch;
+            }
             double tau = factor * (double)n * eps * ch;
-            if (nrm <= tau) {
+            if (nrm <= tau || nonfinite) {
                 brk = 2;
                 beta[j - 1] = 0.0;
                 stt->info[IN_STEPS] = j - 1;
-                stt->info[IN_BREAK] = 2;
+                stt->info[IN_BREAK] = nonfinite ? 3 : 2;
                 stt->info[IN_DONE] = 1;
             } else {
                 beta[j - 1] = nrm;
@@ -241,13 +244,17 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
             ch_new = fmax(ch_old, hypot(a.alpha[a.j - 2], nrm));
             brk = nrm <= a.factor * (double)a.n * eps * ch_new ? 2 : 0;
         }
+        // a norm that is not finite stops the run like a breakdown of the same
+        // side (code 3): NaN or Inf in f, the nodes or the operator
+        const bool nonfinite = !isfinite(nrm);
+        if (nonfinite) brk = (a.side == 1 || a.j == 1) ? 1 : 2;
         inv_s = a.resume ? 1.0 : 1.0 / nrm;
         brk_s = brk;
         if (blockIdx.x == 0) {
-            if (a.side == 0 && !a.resume) sc[SC_CHAT0 + ((a.j + 1) & 1)] = ch_new;
+            if (a.side == 0 && !a.resume && !nonfinite) sc[SC_CHAT0 + ((a.j + 1) & 1)] = ch_new;
             if (brk) {
                 stt->info[IN_STEPS] = a.j - 1;
-                stt->info[IN_BREAK] = brk;
+                stt->info[IN_BREAK] = nonfinite ? 3 : brk;
                 if (brk == 2) a.beta[a.j - 1] = 0.0;
                 stt->info[IN_DONE] = 1;
             } else if (a.side == 1) {
@@ -564,7 +571,7 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
         a.bar = bar;
         a.bar_group = bar_group;
         a.epoch0 = epochs;
-        a.budget = 1LL << 23;
+        a.budget = ctx->opt.wait_budget;
         void* args[] = {&a};
         const bool stage = half_smem_bytes(true, mcount, chunks, rmax) <= HALF_SMEM_STAGE_MAX;
         const size_t smem = half_smem_bytes(stage, mcount, chunks, rmax);

@@ -570,7 +570,7 @@ rbf_status fsvd_jacobi(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fs
     k_fsvd_init<<<tg, tb, 0, s>>>((const double*)op->d_A, op->lda, n, F->W, F->V);
     RBF_LAUNCHED(ctx, "k_fsvd_init");
     double tol = sqrt((double)n) * DBL_EPSILON;
-    long long budget = 1LL << 23;
+    long long budget = ctx->opt.wait_budget;
     std::vector<int> rot((size_t)G);
     int sweeps = 0;
     for (; sweeps < MAX_SWEEPS; ++sweeps) {
@@ -663,7 +663,7 @@ rbf_status fsvd_bidiag(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fs
         rbf_dev_state* stt = ctx->d_state;
         unsigned* bp = bar;
         int grp = group;
-        long long budget = 1LL << 23;
+        long long budget = ctx->opt.wait_budget;
         void* args[] = {&Wp, &nn, &dp, &ep, &tp, &sp, &stt, &bp, &grp, &budget};
         RBF_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_bidiag, dim3(G), dim3(BT), args, 0, s));
         ctx->launches++;

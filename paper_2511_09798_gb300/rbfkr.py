@@ -33,7 +33,8 @@ class RbfError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("grid_j", C.c_int), ("grid_t_lo", C.c_double), ("grid_t_hi", C.c_double),
                 ("breakdown_factor", C.c_double), ("cluster_tol", C.c_double),
-                ("workspace_cap", C.c_int64), ("timing", C.c_int), ("svd_method", C.c_int)]
+                ("workspace_cap", C.c_int64), ("timing", C.c_int), ("svd_method", C.c_int),
+                ("wait_budget", C.c_int64)]
 
 
 class Operator(C.Structure):
