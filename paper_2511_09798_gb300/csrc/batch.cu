@@ -760,6 +760,7 @@ size_t max_items(const BatchPlan& P) {
 }  // namespace
 
 extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int form) {
+    RbfRange range_("rbf_batch_gkb");
     if (!ctx) return RBF_ERR_INVALID;
     if (!bt || bt->count < 1 || !bt->n || !bt->n_interior || !bt->c || !bt->k || !bt->d_nodes || !bt->d_f ||
         !bt->d_W || !bt->d_Z || !bt->d_alpha || !bt->d_beta || !bt->steps_done || !bt->breakdown)
@@ -1031,6 +1032,7 @@ static rbf_status batch_hkt_impl(rbf_ctx* ctx, const rbf_batch* bt, int rule, co
 }
 
 extern "C" rbf_status rbf_batch_hkt(rbf_ctx* ctx, const rbf_batch* bt, int rule, double* d_coef, double* h_lambda) {
+    RbfRange range_("rbf_batch_hkt");
     if (!ctx) return RBF_ERR_INVALID;
     if (!bt || !d_coef || !h_lambda || bt->count < 1) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_batch_hkt: NULL argument");
     if (rule != RBF_GCV && rule != RBF_LCURVE) return rbf_fail(ctx, RBF_ERR_INVALID, "rule must be GCV or L-curve");
@@ -1039,6 +1041,7 @@ extern "C" rbf_status rbf_batch_hkt(rbf_ctx* ctx, const rbf_batch* bt, int rule,
 
 extern "C" rbf_status rbf_batch_hkt_each(rbf_ctx* ctx, const rbf_batch* bt, const int* h_rules,
                                          const double* h_lambda_in, double* d_coef, double* h_lambda) {
+    RbfRange range_("rbf_batch_hkt_each");
     if (!ctx) return RBF_ERR_INVALID;
     if (!bt || !h_rules || !h_lambda_in || !d_coef || !h_lambda || bt->count < 1)
         return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_batch_hkt_each: NULL argument");
@@ -1056,6 +1059,7 @@ extern "C" rbf_status rbf_batch_hkt_each(rbf_ctx* ctx, const rbf_batch* bt, cons
 
 extern "C" rbf_status rbf_batch_evaluate(rbf_ctx* ctx, const rbf_batch* bt, int form, const double* d_coef,
                                          const double* d_points, const int64_t* m, double* d_u) {
+    RbfRange range_("rbf_batch_evaluate");
     if (!ctx) return RBF_ERR_INVALID;
     if (!bt || !d_coef || !d_points || !m || !d_u) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_batch_evaluate: NULL");
     int64_t off = 0, moff = 0;

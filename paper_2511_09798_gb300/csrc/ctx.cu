@@ -203,6 +203,7 @@ rbf_status rbf_operator_init(rbf_ctx* ctx, rbf_operator* op, const double* d_nod
 }
 
 rbf_status rbf_assemble(rbf_ctx* ctx, const rbf_operator* op) {
+    RbfRange range_("rbf_assemble");
     if (!ctx) return RBF_ERR_INVALID;
     if (!op || op->storage != RBF_ASSEMBLED || !op->d_A)
         return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_assemble needs an assembled operator");
@@ -214,6 +215,7 @@ rbf_status rbf_assemble(rbf_ctx* ctx, const rbf_operator* op) {
 
 rbf_status rbf_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* d_coef,
                         const double* d_points, int64_t m, double* d_u) {
+    RbfRange range_("rbf_evaluate");
     if (!ctx) return RBF_ERR_INVALID;
     if (!op || !d_coef || !d_points || !d_u)
         return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_evaluate: NULL argument");

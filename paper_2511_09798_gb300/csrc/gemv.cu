@@ -403,6 +403,7 @@ rbf_status launch_to_f32(rbf_ctx* ctx, int64_t n, const double* x, float* y) {
 
 extern "C" rbf_status rbf_matvec(rbf_ctx* ctx, const rbf_operator* op, int trans, const double* d_x,
                                  double* d_y) {
+    RbfRange range_("rbf_matvec");
     if (!ctx) return RBF_ERR_INVALID;
     if (!op || !d_x || !d_y) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_matvec: NULL argument");
     const int64_t n = op->n;

@@ -634,6 +634,7 @@ static rbf_status read_back(rbf_ctx* ctx, rbf_gkb_state* st) {
 
 extern "C" rbf_status rbf_gkb(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int steps,
                               rbf_gkb_state* st) {
+    RbfRange range_("rbf_gkb");
     if (!ctx) return RBF_ERR_INVALID;
     if (!d_f) return rbf_fail(ctx, RBF_ERR_INVALID, "d_f is NULL");
     RBF_TRY(check_state(ctx, op, st, steps));
@@ -647,6 +648,7 @@ extern "C" rbf_status rbf_gkb(rbf_ctx* ctx, const rbf_operator* op, const double
 
 extern "C" rbf_status rbf_gkb_resume(rbf_ctx* ctx, const rbf_operator* op, rbf_gkb_state* st,
                                      int more_steps) {
+    RbfRange range_("rbf_gkb_resume");
     if (!ctx) return RBF_ERR_INVALID;
     if (!st) return rbf_fail(ctx, RBF_ERR_INVALID, "state is NULL");
     if (st->breakdown != 0 || more_steps == 0) return RBF_OK;

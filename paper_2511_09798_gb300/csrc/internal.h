@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstdarg>
@@ -30,6 +31,16 @@ enum {
     SC_RHO = 10,    // projected residual of the last projected solve
 };
 enum { IN_STEPS = 0, IN_BREAK = 1, IN_DONE = 2, IN_ERR = 3, IN_INDEX = 4, IN_RANK = 5 };
+
+// Named NVTX range around a library call, shown on Nsight timelines; a
+// no-op unless a profiling tool is attached.  Scoped, so that a call that
+// returns early with an error still closes its range.
+struct RbfRange {
+    explicit RbfRange(const char* name) { nvtxRangePushA(name); }
+    ~RbfRange() { nvtxRangePop(); }
+    RbfRange(const RbfRange&) = delete;
+    RbfRange& operator=(const RbfRange&) = delete;
+};
 
 struct rbf_ctx {
     int device = 0;

@@ -153,6 +153,7 @@ extern "C" rbf_status rbf_hkt_error_table(rbf_ctx* ctx, const rbf_gkb_state* st,
 extern "C" rbf_status rbf_learned_hkt(rbf_ctx* ctx, const rbf_operator* op, const double* d_f,
                                       const rbf_stopnet* net, rbf_gkb_state* st, double* d_coef,
                                       rbf_learned_info* info) {
+    RbfRange range_("rbf_learned_hkt");
     if (!ctx) return RBF_ERR_INVALID;
     if (!op || !d_f || !net || !st || !d_coef || !net->d_params)
         return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_learned_hkt: NULL argument");
@@ -232,6 +233,7 @@ extern "C" rbf_status rbf_learned_hkt(rbf_ctx* ctx, const rbf_operator* op, cons
 // fallback rule.
 extern "C" rbf_status rbf_batch_learned_hkt(rbf_ctx* ctx, rbf_batch* bt, const rbf_stopnet* net, double* d_coef,
                                             rbf_learned_info* h_info) {
+    RbfRange range_("rbf_batch_learned_hkt");
     if (!ctx) return RBF_ERR_INVALID;
     if (!bt || !net || !d_coef || !h_info || !net->d_params || bt->count < 1)
         return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_batch_learned_hkt: NULL argument");

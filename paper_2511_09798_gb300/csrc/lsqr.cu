@@ -137,6 +137,7 @@ __global__ void k_lsqr_lift(const double* __restrict__ Z, int64_t ldz, int64_t n
 
 extern "C" rbf_status rbf_lsqr(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, int k_fixed, double* d_coef,
                                double* d_curve, rbf_solve_info* info) {
+    RbfRange range_("rbf_lsqr");
     if (!ctx) return RBF_ERR_INVALID;
     if (!st || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_lsqr: NULL argument");
     const int l = st->steps_done;

@@ -378,6 +378,7 @@ rbf_status single_solve(rbf_ctx* ctx, const rbf_gkb_state* st, int method, int r
 
 extern "C" rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in,
                               double* d_coef, double* d_curve, rbf_solve_info* info) {
+    RbfRange range_("rbf_hkt");
     if (!ctx) return RBF_ERR_INVALID;
     if (!st || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_hkt: NULL argument");
     return hkt_single(ctx, st, rule, lambda_in, d_coef, info, d_curve);
@@ -396,6 +397,7 @@ rbf_status hkt_single(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double la
 
 extern "C" rbf_status rbf_ine_tsvd(rbf_ctx* ctx, const rbf_gkb_state* st, int rank, double* d_coef,
                                    double* d_curve, rbf_solve_info* info) {
+    RbfRange range_("rbf_ine_tsvd");
     if (!ctx) return RBF_ERR_INVALID;
     if (!st || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_ine_tsvd: NULL argument");
     const int l = st->steps_done;

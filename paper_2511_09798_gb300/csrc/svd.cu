@@ -425,6 +425,7 @@ rbf_status launch_projected_svd(rbf_ctx* ctx, const double* alpha, const double*
 
 extern "C" rbf_status rbf_projected_svd(rbf_ctx* ctx, const rbf_gkb_state* st, double* d_sigma,
                                         double* d_ftil, double* d_V, int64_t ldv) {
+    RbfRange range_("rbf_projected_svd");
     if (!ctx) return RBF_ERR_INVALID;
     if (!st || !d_sigma || !d_ftil || !d_V) return rbf_fail(ctx, RBF_ERR_INVALID, "NULL argument");
     const int l = st->steps_done;

@@ -721,6 +721,7 @@ rbf_status read_state(rbf_ctx* ctx) {
 
 extern "C" rbf_status rbf_svd_full(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, double* d_sigma,
                                    double* d_fhat, double* d_V, int* sweeps) {
+    RbfRange range_("rbf_svd_full");
     if (!ctx) return RBF_ERR_INVALID;
     if (!op || !d_sigma || (d_fhat && !d_f)) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_svd_full: bad argument");
     Fsvd F;
@@ -748,6 +749,7 @@ extern "C" rbf_status rbf_svd_full(rbf_ctx* ctx, const rbf_operator* op, const d
 
 extern "C" rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int rule,
                                    double lambda_in, double* d_coef, rbf_solve_info* info) {
+    RbfRange range_("rbf_tikhonov");
     if (!ctx) return RBF_ERR_INVALID;
     if (!op || !d_f || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_tikhonov: NULL argument");
     if (rule != RBF_GCV && rule != RBF_FIXED) return rbf_fail(ctx, RBF_ERR_INVALID, "rule must be RBF_GCV or RBF_FIXED");
@@ -783,6 +785,7 @@ extern "C" rbf_status rbf_tikhonov(rbf_ctx* ctx, const rbf_operator* op, const d
 
 extern "C" rbf_status rbf_tsvd(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int rank, double* d_coef,
                                rbf_solve_info* info) {
+    RbfRange range_("rbf_tsvd");
     if (!ctx) return RBF_ERR_INVALID;
     if (!op || !d_f || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_tsvd: NULL argument");
     if (rank < 0 || rank > op->n) return rbf_fail(ctx, RBF_ERR_INVALID, "rank %d outside [0, n]", rank);
