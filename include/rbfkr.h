@@ -313,7 +313,7 @@ typedef struct {
     double* d_alpha;             /* device [B][L] */
     double* d_beta;              /* device [B][L+1] */
     int* steps_done;             /* host [B], written by rbf_batch_gkb */
-    int* breakdown;              /* host [B], written by rbf_batch_gkb */
+    int* breakdown;              /* host [B], written by rbf_batch_gkb (codes as rbf_gkb_state.breakdown) */
     const int* steps_limit;      /* host [B] or NULL: instance b stops after min(steps, steps_limit[b])
                                     steps (>= 1), with beta and w of the next step written as after
                                     a full run of that length */

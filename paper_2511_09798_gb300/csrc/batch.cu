@@ -293,6 +293,13 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
                     brk = nrm <= a.factor * (double)I.n * eps * ch_new ? 2 : 0;
                 }
             }
+            // a norm that is not finite stops the instance like a breakdown of
+            // the same side (code 3)
+            const bool nonfinite = active && !isfinite(nrm);
+            if (nonfinite) {
+                brk = (a.side == 1 || a.j == 1) ? 1 : 2;
+                ch_new = ch_old;
+            }
             // the instance's step limit: step limit[b] + 1 only finalises beta and w
             const int stop = active && !brk && a.side == 0 && a.limit && a.j == a.limit[b] + 1;
             seg_act[sx] = active && !brk && !stop;
@@ -306,7 +313,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
                 if (active) {
                     if (brk) {
                         a.binfo[BI_STEPS * a.B + b] = a.j - 1;
-                        a.binfo[BI_BREAK * a.B + b] = brk;
+                        a.binfo[BI_BREAK * a.B + b] = nonfinite ? 3 : brk;
                         if (brk == 2) a.beta_all[(size_t)b * (L + 1) + a.j - 1] = 0.0;
                     } else if (a.side == 1) {
                         a.alpha_all[(size_t)b * L + a.j - 1] = nrm;
@@ -517,11 +524,12 @@ __global__ void k_final_batch(HalfBArgs a, int l) {
         const double nrm = sqrt(t);
         double* ch = a.chat_all + 2 * b;
         const double chn = fmax(ch[(l + 1) & 1], hypot(a.alpha_all[(size_t)b * a.L + l - 1], nrm));
-        ch[0] = ch[1] = chn;
-        const int brk = nrm <= a.factor * (double)I.n * DBL_EPSILON * chn ? 2 : 0;
+        const bool nonfinite = !isfinite(nrm);
+        if (!nonfinite) ch[0] = ch[1] = chn;
+        const int brk = (nrm <= a.factor * (double)I.n * DBL_EPSILON * chn || nonfinite) ? 2 : 0;
         a.beta_all[(size_t)b * (a.L + 1) + l] = brk ? 0.0 : nrm;
         a.binfo[BI_STEPS * a.B + b] = l;
-        a.binfo[BI_BREAK * a.B + b] = brk;
+        a.binfo[BI_BREAK * a.B + b] = nonfinite ? 3 : brk;
         inv_s = 1.0 / nrm;
         brk_s = brk;
     }

@@ -116,3 +116,23 @@ def test_nonfinite_inputs_stop_cleanly(R):
         assert st.steps_done == 10 and st.breakdown == 0
     finally:
         ctx.close()
+
+
+def test_batched_nonfinite_instance_stops_alone(R):
+    rng = np.random.default_rng(11)
+    sets = [w.cube_faces_random(500, 0.3, rng), w.cube_faces_random(700, 0.3, rng),
+            w.sphere_fibonacci_ball(100, 300, seed=5)]
+    cs, ks = [0.3, 0.25, 0.2], [2.0, 3.0, 4.0]
+    fs = [w.plane_wave_rhs(s, k) for s, k in zip(sets, ks)]
+    fs[1] = fs[1].copy()
+    fs[1][42] = np.nan
+    L = 12
+    ctx = R.Context(0)
+    try:
+        bt, keep = R.make_batch(torch, sets, cs, ks, fs, L, "cuda")
+        ctx.rbf_batch_gkb(bt, L)
+        assert bt.breakdown[1] == 3 and bt.steps_done[1] == 0
+        for b in (0, 2):
+            assert bt.breakdown[b] == 0 and bt.steps_done[b] == L
+    finally:
+        ctx.close()
