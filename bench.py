@@ -1020,6 +1020,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube8000")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--jsonl", default=None, help="also append the result line to this JSONL file")
     ap.add_argument("--single-solve", action="store_true",
                     help="run one untimed solve of the first case and exit (profiling target)")
     args = ap.parse_args()
@@ -1051,7 +1052,11 @@ def main():
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     if out is not None:
-        print(json.dumps(out), flush=True)
+        line = json.dumps(out)
+        print(line, flush=True)
+        if args.jsonl:
+            with open(args.jsonl, "a") as fh:
+                fh.write(line + "\n")
 
 
 if __name__ == "__main__":
