@@ -79,7 +79,7 @@ typedef struct rbf_ctx rbf_ctx;
 
 /* Options fixed at context creation.  Zero-initialised fields take defaults. */
 typedef struct {
-    int grid_j;              /* lambda grid points J (default 321) */
+    int grid_j;              /* lambda grid points J (default 321; 1 and 2 are rejected) */
     double grid_t_lo;        /* grid: lambda = s~_1 * 10^t, t in [t_lo, t_hi] (default -16) */
     double grid_t_hi;        /* (default 0; used only when t_lo < t_hi) */
     double breakdown_factor; /* tau = factor * N * eps * c_hat (default 64) */
@@ -170,7 +170,8 @@ typedef struct {
 
 /* Create a context on `device` enqueuing on `cuda_stream` (a cudaStream_t, or
  * NULL for the legacy default stream).  `opt` may be NULL (defaults).
- * Errors: RBF_ERR_INVALID (ctx NULL), RBF_ERR_CUDA (device unusable). */
+ * Errors: RBF_ERR_INVALID (ctx NULL, opt->grid_j 1 or 2), RBF_ERR_CUDA (device
+ * unusable). */
 rbf_status rbf_create(rbf_ctx** ctx, int device, void* cuda_stream, const rbf_options* opt);
 
 /* Release the context and its workspace.  NULL is accepted. */
@@ -506,12 +507,16 @@ rbf_status rbf_batch_learned_hkt(rbf_ctx* ctx, rbf_batch* batch, const rbf_stopn
  * (the partials need at least ceil(n / 4096) chunks of n doubles, so n up to
  * about 64 000), otherwise RBF_ERR_INVALID.  The first call on a device (with
  * that device current) looks up the array's device address; make that first
- * call before any stream capture.  All calls share the one array and every
- * call overwrites the partials it reads, so calls that overlap on the GPU (on
- * different streams or host threads) race and must be ordered by the caller.
- * Returns RBF_ERR_INVALID for NULL pointers or bad sizes and alignment,
- * RBF_ERR_CUDA when a CUDA call or launch fails (no message is kept: there is
- * no context). */
+ * call before any stream capture.  The address is kept for the life of the
+ * process, so no call may follow a cudaDeviceReset of that device (the reset
+ * unloads the module and the array may move).  All calls share the one array
+ * and every call overwrites the partials it reads, so calls that overlap on
+ * the GPU (on different streams or host threads) race and must be ordered by
+ * the caller.  Returns RBF_ERR_INVALID for NULL pointers or bad sizes and
+ * alignment, RBF_ERR_CUDA when a CUDA call or launch fails, and also, without
+ * launching anything, when an earlier CUDA error is still pending on this host
+ * thread (it is left in place for its owner; no message is kept: there is no
+ * context). */
 rbf_status rbf_matvec_t_noalloc(const double* d_A, int64_t lda, int64_t n, const double* d_x,
                                 double* d_y, void* cuda_stream);
 

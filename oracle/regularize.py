@@ -198,17 +198,18 @@ def tsvd_solve_proj(ps: ProjectedSVD, k):
 # methods on top of GKB
 # ----------------------------------------------------------------------------
 
-def hkt(g, rule="gcv", lam=None):
+def hkt(g, rule="gcv", lam=None, J=GRID_J):
     """Hybrid Krylov-Tikhonov (Algorithm 4) on a finished GKB run ``g``.
 
-    rule in {'gcv', 'lcurve', 'fixed'}; 'fixed' uses the given lambda.
-    Returns dict(coef = Z_l y_lambda, y, lam, index, ps, grid, curve).
+    rule in {'gcv', 'lcurve', 'fixed'}; 'fixed' uses the given lambda; J grid
+    points on the lambda grid.  Returns dict(coef = Z_l y_lambda, y, lam,
+    index, ps, grid, curve).
     """
     ps = projected_svd(g.C(), g.beta1)
     if rule == "fixed":
         lam_s, idx, grid, curve = float(lam), -1, None, None
     else:
-        lam_s, idx, grid, curve = choose_lambda_proj(ps, rule)
+        lam_s, idx, grid, curve = choose_lambda_proj(ps, rule, J)
     y = hkt_solve_proj(ps, lam_s)
     coef = g.Z_l() @ y
     return dict(coef=coef, y=y, lam=float(lam_s), index=idx, ps=ps, grid=grid, curve=curve)

@@ -583,7 +583,7 @@ struct BatchTuneState {
     double best_ms = 0.0;
     int graph_kernels = 0;               // kernels in the graph used last
     cudaGraphExec_t exec[GRAPH_SLOTS] = {};
-    uint64_t graph_key[GRAPH_SLOTS] = {};
+    std::vector<unsigned char> graph_key[GRAPH_SLOTS];  // exact bytes of what each graph bakes in
     int slot_kernels[GRAPH_SLOTS] = {};
     uint64_t last_use[GRAPH_SLOTS] = {};
     uint64_t clock = 0;
@@ -592,7 +592,7 @@ struct BatchTuneState {
         for (int i = 0; i < GRAPH_SLOTS; ++i) {
             if (exec[i]) cudaGraphExecDestroy(exec[i]);
             exec[i] = nullptr;
-            graph_key[i] = 0;
+            graph_key[i].clear();
         }
     }
 };
@@ -883,11 +883,23 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     if (hsmem > 48 * 1024)
         RBF_CUDA(ctx, cudaFuncSetAttribute(k_half_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
 
-    // ---- the step loop, captured into one graph (keyed by everything it bakes in)
-    uint64_t key = (uint64_t)(uintptr_t)ctx->ws * 1000003ull ^ (uint64_t)(uintptr_t)bt->d_W * 7919ull ^
-                   (uint64_t)(uintptr_t)bt->d_nodes * 31ull ^ (uint64_t)(uintptr_t)bt->d_f * 131ull ^
-                   (uint64_t)P.T * 4099ull ^ (uint64_t)steps * 65537ull ^ (uint64_t)cand ^
-                   (uint64_t)(uintptr_t)bt->d_alpha * 17ull ^ (uint64_t)P.L * 257ull ^ (uint64_t)form * 3ull;
+    // ---- the step loop, captured into one graph.  A cached graph is reused only
+    // when every value it bakes in is the same, compared byte for byte: the
+    // half-step arguments (all pointers, sizes and the budget), the product's
+    // grid (item count, tile candidate), the workspace slices the launches
+    // read and write, the node and input pointers, the cooperative grid, its
+    // shared memory and the step count.
+    std::vector<unsigned char> key;
+    auto put = [&key](const auto& v) {
+        const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+        key.insert(key.end(), b, b + sizeof(v));
+    };
+    put(a.inst); put(a.offs); put(a.B); put(a.T); put(a.L); put(a.factor);
+    put(a.alpha_all); put(a.beta_all); put(a.W_all); put(a.Z_all); put(a.part_all); put(a.hpart_all);
+    put(a.h_all); put(a.npart_all); put(a.binfo); put(a.limit); put(a.chat_all); put(a.stt); put(a.bar);
+    put(a.bar_group); put(a.budget); put(a.rmax);
+    put(bt->d_nodes); put(bt->d_f); put(w.items); put(w.part); put(w.vr); put(w.vp); put(w.vr32); put(w.vp32);
+    put(nit); put(cand); put(P.G); put(hsmem); put(steps); put(form); put(s);
     auto record_steps = [&](int* kernels) -> cudaError_t {
         int cnt = 0;
         for (int j = 1; j <= steps; ++j) {
@@ -953,7 +965,7 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
         if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&ts.exec[slot], graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e == cudaSuccess && ts.exec[slot]) {
-            ts.graph_key[slot] = key;
+            ts.graph_key[slot] = key;  // a copy
             ts.slot_kernels[slot] = kernels;
             ts.last_use[slot] = ++ts.clock;
             ts.graph_kernels = kernels;

@@ -73,6 +73,10 @@ rbf_status rbf_create(rbf_ctx** out, int device, void* cuda_stream, const rbf_op
     ctx->stream = (cudaStream_t)cuda_stream;
     if (opt) ctx->opt = *opt;
     if (ctx->opt.grid_j <= 0) ctx->opt.grid_j = 321;
+    if (ctx->opt.grid_j < 3) {  // the L-curve needs interior grid points, the grid step J - 1 > 0
+        delete ctx;
+        return RBF_ERR_INVALID;
+    }
     if (!(ctx->opt.grid_t_lo < ctx->opt.grid_t_hi)) {
         ctx->opt.grid_t_lo = -16.0;
         ctx->opt.grid_t_hi = 0.0;

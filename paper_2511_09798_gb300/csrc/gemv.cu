@@ -482,6 +482,9 @@ extern "C" rbf_status rbf_matvec_t_noalloc(const double* d_A, int64_t lda, int64
     if (max_chunks < min_chunks) return RBF_ERR_INVALID;  // n beyond the scratch limit
     if (ch > max_chunks) ch = (int)max_chunks;
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    // an error left pending by earlier, unrelated work is reported (and left in
+    // place for its owner) instead of being cleared and blamed on these launches
+    if (cudaPeekAtLastError() != cudaSuccess) return RBF_ERR_CUDA;
     // every (chunk, column) partial is written before it is read: nothing to clear
     k_gemv_t_f64<<<pn * ch, GT_THREADS, 0, s>>>(d_A, lda, n, d_x, pc, ch, scratch, nullptr);
     if (cudaGetLastError() != cudaSuccess) return RBF_ERR_CUDA;

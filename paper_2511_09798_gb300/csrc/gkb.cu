@@ -80,10 +80,11 @@ __global__ void k_finalize(rbf_dev_state* __restrict__ stt, const double* __rest
         int brk = 0;
         if (side == 1) {  // alpha_j
             double tau = factor * (double)n * eps * fmax(sc[SC_CHAT0], nrm);
-            if (nrm <= tau) {
+            const bool nonfinite = !isfinite(nrm);
+            if (nrm <= tau || nonfinite) {
                 brk = 1;
                 stt->info[IN_STEPS] = j - 1;
-                stt->info[IN_BREAK] = 1;
+                stt->info[IN_BREAK] = nonfinite ? 3 : 1;
                 stt->info[IN_DONE] = 1;
             } else {
                 alpha[j - 1] = nrm;
@@ -91,10 +92,11 @@ __global__ void k_finalize(rbf_dev_state* __restrict__ stt, const double* __rest
                 sc[SC_INV_ALPHA] = 1.0 / nrm;
             }
         } else if (j == 1) {  // beta_1 = |f|
-            if (!(nrm > 0.0)) {
+            const bool nonfinite = !isfinite(nrm);
+            if (!(nrm > 0.0) || nonfinite) {
                 brk = 1;
                 stt->info[IN_STEPS] = 0;
-                stt->info[IN_BREAK] = 1;
+                stt->info[IN_BREAK] = nonfinite ? 3 : 1;
                 stt->info[IN_DONE] = 1;
             } else {
                 beta[0] = nrm;

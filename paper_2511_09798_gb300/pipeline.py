@@ -56,12 +56,9 @@ def allocate(torch, ctx: R.Context, prob: Problem, steps: int, precision: int, s
     b.coef = torch.empty(prob.n, dtype=torch.float64, device=device)
     if prob.m:
         b.u = torch.empty(prob.m, dtype=torch.float64, device=device)
-    b.curve = torch.empty(max(ctx_grid_j(ctx), steps), dtype=torch.float64, device=device)
+    # GCV / curvature on the context's lambda grid, or GCV_l(k) for k = 1..l
+    b.curve = torch.empty(max(ctx.grid_j, steps), dtype=torch.float64, device=device)
     return b
-
-
-def ctx_grid_j(ctx) -> int:
-    return 321
 
 
 def solve(ctx: R.Context, prob: Problem, buf: Buffers, steps: int, precision=R.RBF_FP64,

@@ -208,7 +208,7 @@ class Context:
         for k, v in opts.items():
             setattr(o, k, v)
         o.timing = int(timing)
-        self.grid_j = o.grid_j if o.grid_j >= 3 else 321
+        self.grid_j = o.grid_j if o.grid_j > 0 else 321  # the library's default; 1 and 2 are rejected
         self.grid_t_lo, self.grid_t_hi = ((o.grid_t_lo, o.grid_t_hi) if o.grid_t_lo < o.grid_t_hi
                                           else (-16.0, 0.0))
         h = C.c_void_p()
@@ -280,19 +280,27 @@ class Context:
         self._check(self.lib.rbf_projected_svd(self.h, C.byref(state), _ptr(sigma), _ptr(ftil),
                                                _ptr(V), ldv))
 
+    @staticmethod
+    def _curve_fits(curve, need, what):
+        if curve is not None and hasattr(curve, "numel") and curve.numel() < need:
+            raise ValueError(f"{what}: curve buffer holds {curve.numel()} values, needs {need}")
+
     def rbf_hkt(self, state, rule, lambda_in, coef, curve=None):
+        self._curve_fits(curve, self.grid_j, "rbf_hkt")
         info = SolveInfo()
         self._check(self.lib.rbf_hkt(self.h, C.byref(state), rule, float(lambda_in), _ptr(coef),
                                      _ptr(curve), C.byref(info)))
         return info
 
     def rbf_ine_tsvd(self, state, rank, coef, curve=None):
+        self._curve_fits(curve, state.steps_done, "rbf_ine_tsvd")
         info = SolveInfo()
         self._check(self.lib.rbf_ine_tsvd(self.h, C.byref(state), rank, _ptr(coef), _ptr(curve),
                                           C.byref(info)))
         return info
 
     def rbf_lsqr(self, state, rule, k_fixed, coef, curve=None):
+        self._curve_fits(curve, state.steps_done, "rbf_lsqr")
         info = SolveInfo()
         self._check(self.lib.rbf_lsqr(self.h, C.byref(state), rule, int(k_fixed), _ptr(coef), _ptr(curve),
                                       C.byref(info)))

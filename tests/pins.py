@@ -146,3 +146,64 @@ def tsvd_via_eigh(A, f, k):
         u = A @ V[:, i] / s
         out += (u @ f) / s * V[:, i]
     return out
+
+
+def matrix_with_singular_values(s, rng):
+    """A = U diag(s) V^T with Haar-random orthogonal U, V (QR of Gaussians): a
+    matrix whose singular values are fixed by construction."""
+    n = len(s)
+    U, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    V, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    return (U * np.asarray(s)) @ V.T
+
+
+def pin_full_rank(full_svd, rng):
+    """Numerical rank r = #{s_i > N eps s_1} of the full SVD (Algorithm 3) on
+    matrices whose rank is known by construction.  (The eigenvalues of A^T A
+    resolve singular values only down to about sqrt(N eps) s_1, far above the
+    N eps s_1 threshold, so they cannot decide this count; the constructions
+    place every singular value far from the threshold instead.)
+      1. exactly rank-deficient products B C^T (N x r times r x N): rank r;
+      2. singular values 1 .. 1e-8 (r1 of them), then 30 N eps, then values at
+         0.03 N eps (a few eps) and exact zeros: rank r1 + 1, so a threshold of
+         eps s_1 (counting the 0.03 N eps values) or of a different scale fails."""
+    eps = np.finfo(np.float64).eps
+    for n, r in ((60, 23), (200, 150), (41, 40)):
+        A = rng.normal(size=(n, r)) @ rng.normal(size=(r, n))
+        got = full_svd(A, rng.normal(size=n)).r
+        assert got == r, (n, r, got)
+    for n, r1 in ((80, 30), (150, 97)):
+        s = np.zeros(n)
+        s[:r1] = np.logspace(0, -8, r1)
+        s[r1] = 30 * n * eps
+        s[r1 + 1:r1 + 6] = 0.03 * n * eps
+        A = matrix_with_singular_values(s, rng)
+        fs = full_svd(A, rng.normal(size=n))
+        assert fs.r == r1 + 1, (n, r1, fs.r)
+    return True
+
+
+def pin_tsvd_gcv_curve(tsvd_full, rng):
+    """The full-TSVD rank curve (reading of Algorithm 3 with eq. tsvd_solution)
+    against brute force: GCV(k) = |A x_k - f|^2 / (N - k)^2 with x_k the rank-k
+    TSVD solution applied to the dense A, for every k = 1..min(r, N - 1) (the
+    curve has exactly that many entries), and the chosen rank its argmin.  Cases:
+    full rank (r = N, so the range stops at N - 1) and an exact rank-r matrix
+    (r < N, the residual then includes f's component outside range(A))."""
+    for n, r in ((40, 40), (50, 31)):
+        s = np.zeros(n)
+        s[:r] = np.logspace(0, -6, r)
+        A = matrix_with_singular_values(s, rng)
+        f = rng.normal(size=n)
+        t = tsvd_full(A, f)
+        curve = np.asarray(t["curve"])
+        kmax = min(r, n - 1)
+        assert curve.shape == (kmax,), (curve.shape, kmax)
+        ref = np.empty(kmax)
+        for k in range(1, kmax + 1):
+            x = tsvd_full(A, f, rank=k)["coef"]
+            res = A @ x - f
+            ref[k - 1] = float(res @ res) / (n - k) ** 2
+        assert np.allclose(curve, ref, rtol=1e-8, atol=0), np.max(np.abs(curve - ref) / ref)
+        assert t["rank"] == int(np.argmin(ref)) + 1
+    return True

@@ -248,3 +248,55 @@ def test_batch_learned_hkt_decisions(ctx, R):
         assert infos[b].accepted == 0 and bt.steps_done[b] == bt2.steps_done[b]
         assert infos[b].solve.lambda_ == lam_g[b]
     assert torch.equal(coef, coef2)
+
+
+def test_batch_graph_not_reused_with_new_buffers_or_split(R):
+    """A cached step-loop graph bakes in every buffer pointer and the product's
+    grid.  A second batch that keeps W, alpha, the nodes and f but brings fresh
+    Z and beta buffers must write into the new buffers (the old ones stay
+    untouched) and give the same bits; a batch with the same total rows and
+    count but a different split of the rows must match a fresh context."""
+    sets, cs, ks, fs = _instances()
+    L = 10
+    ctx = R.Context(0)
+    bt, keep = R.make_batch(torch, sets, cs, ks, fs, L)
+    ctx.rbf_batch_gkb(bt, L)  # captures the graph
+    ref = {k: keep[k].clone() for k in ("alpha", "beta", "W", "Z")}
+    old_Z, old_beta = keep["Z"], keep["beta"]
+    old_Z.fill_(7.0)
+    old_beta.fill_(7.0)
+    keep["Z"] = torch.full_like(old_Z, float("nan"))
+    keep["beta"] = torch.full_like(old_beta, float("nan"))
+    bt.d_Z, bt.d_beta = keep["Z"].data_ptr(), keep["beta"].data_ptr()
+    ctx.rbf_batch_gkb(bt, L)
+    torch.cuda.synchronize()
+    assert torch.all(old_Z == 7.0) and torch.all(old_beta == 7.0), "stale graph wrote the old buffers"
+    for k in ("alpha", "W", "Z"):
+        assert torch.equal(keep[k], ref[k]), k
+    done = [bt.steps_done[b] for b in range(len(sets))]
+    for b in range(len(sets)):  # beta_1 .. beta_{l+1} of every instance
+        s0 = b * (L + 1)
+        assert torch.equal(keep["beta"][s0:s0 + done[b] + 1], ref["beta"][s0:s0 + done[b] + 1]), b
+    # same T and B, rows split differently: instances 0 and 2 exchange 300 rows, which changes
+    # the product's work list; W, alpha and the node and input buffers keep their pointers
+    rng = np.random.Generator(np.random.PCG64(33))
+    sets2 = list(sets)
+    sets2[0] = w.cube_faces_random(sets[0].n + 300, 0.3, rng)
+    sets2[2] = w.cube_faces_random(sets[2].n - 300, 0.3, rng)
+    fs2 = [w.plane_wave_rhs(s_, k_, w.problem.DIAG) for s_, k_ in zip(sets2, ks)]
+    bt2, keep2 = R.make_batch(torch, sets2, cs, ks, fs2, L)
+    assert int(keep2["offsets"][-1]) == int(keep["offsets"][-1])
+    for k in ("nodes", "f"):
+        keep[k].copy_(keep2[k])
+    for k in ("n", "ni"):
+        keep[k][:] = keep2[k][:]
+    ctx.rbf_batch_gkb(bt, L)
+    alpha = keep["alpha"].cpu().numpy().reshape(len(sets2), L)
+    beta = keep["beta"].cpu().numpy().reshape(len(sets2), L + 1)
+    for b in (0, 2):
+        ns = sets2[b]
+        g = OG.gkb(OM.assemble(ns.X, ns.n_interior, cs[b], ks[b]), None, fs2[b], L)
+        assert bt.steps_done[b] == g.steps_done, b
+        assert abs(alpha[b, 0] - g.alpha[0]) / g.alpha[0] < 1e-5, b
+        assert np.max(np.abs(beta[b, :2] - g.beta[:2]) / g.beta[:2]) < 1e-5, b
+    ctx.close()

@@ -106,3 +106,43 @@ def test_missing_sigma_factor_in_hkt_caught():
     ref = pins.tikhonov_lstsq(g.C(), b, lam)
     assert np.linalg.norm(bad - ref) / np.linalg.norm(ref) > 1e-3
     assert np.linalg.norm(R.hkt_solve_proj(ps, lam) - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def _tsvd_full_mutant(denominator_shift=0, stop_at_r=False):
+    """tsvd_full with one planted slip in its GCV rank curve."""
+    def bad(A, f, rank=None, fs=None):
+        fs = R.full_svd(A, f) if fs is None else fs
+        f2 = fs.fhat[: fs.r] ** 2
+        if rank is None:
+            kmax = fs.r if stop_at_r else min(fs.r, fs.n - 1)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                curve = np.array([(np.sum(f2[k:]) + fs.s_perp) / (fs.n - k + denominator_shift) ** 2
+                                  for k in range(1, kmax + 1)])
+            k = int(np.nanargmin(curve)) + 1
+        else:
+            k, curve = int(rank), None
+        coef = fs.V[:, :k] @ (fs.fhat[:k] / fs.sigma[:k])
+        return dict(coef=coef, rank=k, fs=fs, curve=curve)
+    return bad
+
+
+def test_tsvd_gcv_denominator_off_by_one_caught():
+    with pytest.raises(AssertionError):
+        pins.pin_tsvd_gcv_curve(_tsvd_full_mutant(denominator_shift=1), np.random.default_rng(14))
+
+
+def test_tsvd_gcv_range_ending_at_r_caught():
+    with pytest.raises(AssertionError):
+        pins.pin_tsvd_gcv_curve(_tsvd_full_mutant(stop_at_r=True), np.random.default_rng(14))
+
+
+def test_full_rank_threshold_without_n_caught(monkeypatch):
+    orig = R.full_svd
+
+    def bad(A, f):
+        fs = orig(A, f)
+        s = fs.sigma
+        fs.r = int(np.sum(s > R.EPS * s[0]))  # planted: drops the factor N
+        return fs
+    with pytest.raises(AssertionError):
+        pins.pin_full_rank(bad, np.random.default_rng(13))

@@ -179,3 +179,11 @@ def test_lcurve_ignores_stationary_stretch():
     below = t[1:-1] < np.log10(s_min) - 3.0
     assert np.all(np.isneginf(h["curve"][below]))
     assert t[h["index"]] > np.log10(s_min) - 3.0
+
+
+def test_full_svd_numerical_rank_by_construction():
+    assert pins.pin_full_rank(R.full_svd, np.random.default_rng(13))
+
+
+def test_full_tsvd_gcv_rank_curve_brute_force():
+    assert pins.pin_tsvd_gcv_curve(R.tsvd_full, np.random.default_rng(14))
