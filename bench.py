@@ -6,16 +6,24 @@ Workload (default ``cube8000``): the N = 8000 Halton cube (21 x 21 face grid,
 u = sin(k (x + y + z) / sqrt 3), FP64, assembled A (512 MB), 100 GKB steps, HKT
 with GCV, u at 2000 seeded test points.  One bench step = the six solves
 c in {0.1, 0.2, 0.5} x k in {2, 5}; each solve assembles A, runs GKB, the
-projected SVD, GCV, the projected solve, the lift and the reconstruction.
+projected SVD, GCV, the projected solve, the lift and the reconstruction.  The
+six solves are independent: they run concurrently on `--lanes` streams of the
+library context (rbf_gkb_many, rbf_hkt_many).
 
 value = GKB steps completed / device time (all ranks, max time over ranks).
 e2e   = the same metric through the C ABI with the step's inputs copied from
         pinned host memory and u copied back inside the timed region.
 roofline: the dominant kernel is the matrix-vector product of the GKB; its
-        launches are timed live with CUDA events on the library stream.  The
-        FP64 product is bound by the FP64 pipe (1 FMA per 8-byte entry), so the
-        bound is "alu" with the peak 152 SMs x 2 FP64 FMA/clk x 2 flop x
-        2.07 GHz = 1.259 TFLOP/s; the HBM fraction is reported beside it.
+        launches are timed live with CUDA events on the launching streams, and
+        the per-launch time is the union of the launch intervals divided by the
+        launches (concurrent products overlap).  The FP64 product is bound by
+        the FP64 pipe (1 FMA per 8-byte entry), so the bound is "alu" with the
+        measured FP64 FMA peak 1.2573 TFLOP/s (2 FMA/clk/SM at 2.07 GHz); the
+        HBM fraction is reported beside it.
+re_exact: Re = max |u - u_exact| / max |u_exact| of every solve at the test
+        points; gaussian_variant: the same solve for the cube example's
+        Gaussian exact solution (a field HKT resolves), timed one solve after
+        another.
 
 ``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
 host cores, one full solve of the same workload per step.
@@ -35,7 +43,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "GKB steps/s and time-to-HKT-solution at N (fraction of HBM/FP32 roofline)"
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # FP64 FMA pipe, max clock
+# FP64 FMA pipe of the GB300, measured by `bench.py --workload fp64-pipe-probe`
+# (1.998 FMA/clk/SM at 2070 MHz; nominal 152 x 2 FMA/clk x 2 flop x 2.07 GHz = 1.2586)
+FP64_PEAK_TFLOPS = 1.2573
+FP64_PEAK_SOURCE = ("measured: FP64 FMA probe, 1.2573 TFLOP/s = 1.998 FMA/clk/SM at 2070 MHz "
+                    "(bench.py --workload fp64-pipe-probe)")
 FP32_LANE_TOPS = 152 * 128 * 2.07e9 / 1e12  # FP32 pipe: one operation per lane per clock
 
 
@@ -133,8 +145,56 @@ def workload(name):
         raise SystemExit(f"unknown workload {name}")
     P = w.test_points(ns)
     fs = {k: w.plane_wave_rhs(ns, k) for k in sorted({k for _, k in cases})}
+    exact = {k: w.plane_wave(P, k) for k in fs}
     return dict(name=name, ns=ns, cases=cases, steps=steps, precision=prec, storage=storage,
-                points=P, fs=fs, np=np)
+                points=P, fs=fs, exact=exact, exact_name="plane wave sin(k (x + y + z) / sqrt 3)", np=np)
+
+
+def gaussian_variant(R, ctx, wl, nodes_d, pts_d, stream, dev, reps=5):
+    """The same N = 8000 FP64 assembled solve (assemble, GKB, HKT with GCV, u)
+    for the Gaussian exact solution exp(-|X|^2 / 20) of the cube example
+    (Sec. 5, Example 1) at k = 3, with c = 2: a field that HKT resolves (the
+    plane waves of the headline are not resolved by 100 GKB steps).  Device
+    time per solution over `reps` solves, and Re at the test points."""
+    import numpy as np
+    import torch
+
+    import workloads as w
+    ns, L = wl["ns"], wl["steps"]
+    n, m = ns.n, wl["points"].shape[0]
+    c, k, sigma = 2.0, 3.0, 20.0
+    f = torch.as_tensor(w.gaussian_rhs(ns, sigma, k), device=dev)
+    ue = w.gaussian(wl["points"], sigma)
+    lda = R.padded_lda(n, R.RBF_FP64)
+    A = torch.empty((n, lda), dtype=torch.float64, device=dev)
+    op = ctx.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, R.RBF_ASSEMBLED, R.RBF_FP64, R.RBF_FORM_C, A, lda)
+    st = R.make_state(torch, n, L, dev)[0]
+    coef = torch.empty(n, dtype=torch.float64, device=dev)
+    u = torch.empty(m, dtype=torch.float64, device=dev)
+
+    def solve():
+        ctx.rbf_assemble(op)
+        ctx.rbf_gkb(op, f, L, st)
+        inf = ctx.rbf_hkt(st, R.RBF_GCV, 0.0, coef)
+        ctx.rbf_evaluate(op, coef, pts_d, m, u)
+        return inf
+
+    solve()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        info = solve()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    re = float(np.max(np.abs(u.cpu().numpy() - ue)) / np.max(np.abs(ue)))
+    return {"exact": "Gaussian exp(-|X|^2 / 20)", "c": c, "k": k, "gkb_steps": st.steps_done, "rule": "gcv",
+            "solves_timed": reps, "time_to_solution_ms": round(ms / reps, 3),
+            "gkb_steps_per_s": round(st.steps_done * reps / (ms / 1e3), 1), "re_exact": round(re, 8),
+            "lambda_over_s1_log10": round(float(np.log10(info.lambda_ / info.sigma1)), 3),
+            "timing": "one solve after another through rbf_assemble / rbf_gkb / rbf_hkt / rbf_evaluate, "
+                      "CUDA events around the solves"}
 
 
 # --------------------------------------------------------------------------- clocks
@@ -216,33 +276,37 @@ def run_ours(args, rank, world, local_rank):
     pts_d = pts_h.to(dev)
     f_d = {k: v.to(dev) for k, v in f_h.items()}
     lda = R.padded_lda(n, prec)
-    A = None
-    if storage == R.RBF_ASSEMBLED:
-        A = torch.empty((n, lda), dtype=torch.float64 if prec == R.RBF_FP64 else torch.float32, device=dev)
-    st, W, Z, al, be = R.make_state(torch, n, L, dev)
-    coef = torch.empty(n, dtype=torch.float64, device=dev)
+    adt = torch.float64 if prec == R.RBF_FP64 else torch.float32
+    # one operator (and, assembled, one matrix) per (c, k) case: the cases are
+    # independent solves, run concurrently on the context's lanes
+    mats = [torch.empty((n, lda), dtype=adt, device=dev) if storage == R.RBF_ASSEMBLED else None for _ in cases]
+    ops = [ctx.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, storage, prec, R.RBF_FORM_C, Ac,
+                                 lda if Ac is not None else 0) for (c, k), Ac in zip(cases, mats)]
+    states = [R.make_state(torch, n, L, dev)[0] for _ in cases]
+    coefs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in cases]
+    fs_case = [f_d[k] for _, k in cases]
+    A = mats[0]
+    st = states[0]
+    coef = coefs[0]
     u_d = torch.empty((len(cases), m), dtype=torch.float64, device=dev)
     u_h = torch.empty((len(cases), m), dtype=torch.float64).pin_memory()
+    last_infos = []
 
     def one_step(e2e=False):
-        done = 0
         if e2e:
             nodes_d.copy_(nodes_h, non_blocking=True)
             pts_d.copy_(pts_h, non_blocking=True)
             for k in f_d:
                 f_d[k].copy_(f_h[k], non_blocking=True)
-        for ci, (c, k) in enumerate(cases):
-            op = ctx.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, storage, prec, R.RBF_FORM_C,
-                                       A, lda if A is not None else 0)
-            if A is not None:
-                ctx.rbf_assemble(op)
-            ctx.rbf_gkb(op, f_d[k], L, st)
-            done += st.steps_done
-            ctx.rbf_hkt(st, R.RBF_GCV, 0.0, coef)
-            ctx.rbf_evaluate(op, coef, pts_d, m, u_d[ci])
+        # assemble + GKB (Algorithm 1) of every case, then the projected solves
+        # (Algorithm 4, GCV) and the reconstructions
+        ctx.rbf_gkb_many(ops, fs_case, L, states, lanes=args.lanes, assemble=storage == R.RBF_ASSEMBLED)
+        last_infos[:] = ctx.rbf_hkt_many(states, R.RBF_GCV, 0.0, coefs, lanes=args.lanes)
+        for ci in range(len(cases)):
+            ctx.rbf_evaluate(ops[ci], coefs[ci], pts_d, m, u_d[ci])
         if e2e:
             u_h.copy_(u_d, non_blocking=True)
-        return done
+        return sum(s_.steps_done for s_ in states)
 
     def timed(k_steps, e2e):
         rank_barrier()
@@ -265,7 +329,14 @@ def run_ours(args, rank, world, local_rank):
     ms, done = timed(args.steps, False)
     clocks = sampler.stop() if sampler else None
     cnt = ctx.rbf_get_counters(reset=True)
+    # accuracy of the timed solves against the exact solution (eq. rel_error)
+    uh = u_d.cpu().numpy()
+    re_exact = [float(np.max(np.abs(uh[ci] - wl["exact"][k])) / np.max(np.abs(wl["exact"][k])))
+                for ci, (_, k) in enumerate(cases)]
+    t_chosen = [float(np.log10(x.lambda_ / x.sigma1)) for x in last_infos]
     ms_e2e, done_e2e = timed(args.steps, True)
+    gauss = gaussian_variant(R, ctx, wl, nodes_d, pts_d, stream, dev) if wl["name"] == "cube8000" else None
+    ctx.rbf_get_counters(reset=True)
     # phase shares (separate context with synchronising per-phase timers)
     ctx_ph = R.Context(local_rank, stream=stream, timing=1)
     phases = {}
@@ -287,12 +358,16 @@ def run_ours(args, rank, world, local_rank):
     peaks = measured_peaks()
     solves = args.steps * len(cases) * world
     value = done / (ms / 1e3)
-    # dominant kernel: the GKB products (A z and A^T w)
+    # dominant kernel: the GKB products (A z and A^T w, the same algorithmic work
+    # per launch).  Products of concurrent runs overlap, so the per-launch time
+    # is the union of all product launch intervals (CUDA events on the lanes'
+    # streams) divided by the launches: the device time the products occupied.
     p_ms, p_cnt = cnt["product_ms"], cnt["product_launches"]
     kinds = ["gemv_n (p = A z)", "gemv_t (r = A^T w)"]
     dom = 0 if p_ms[0] >= p_ms[1] else 1
-    avg_ms = p_ms[dom] / max(1, p_cnt[dom])
-    both_avg_ms = (p_ms[0] + p_ms[1]) / max(1, p_cnt[0] + p_cnt[1])
+    n_prod = max(1, p_cnt[0] + p_cnt[1])
+    both_avg_ms = (p_ms[0] + p_ms[1]) / n_prod
+    avg_ms = cnt["product_busy_ms"] / n_prod
     s = 8 if prec == R.RBF_FP64 else 4
     if storage == R.RBF_ASSEMBLED:
         alg_bytes = s * n * n
@@ -302,7 +377,7 @@ def run_ours(args, rank, world, local_rank):
             roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                     "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": None,
                     "pipe": "fp64 (2 FMA/clk/SM; 1 FMA per 8-byte entry)",
-                    "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (unit counts and max clock)",
+                    "peak_source": FP64_PEAK_SOURCE,
                     "hbm_achieved_gbs": round(gbs, 1), "hbm_peak_gbs": peaks.get("hbm_gbs"),
                     "hbm_frac": round(gbs / peaks.get("hbm_gbs", 6790.7), 4)}
         else:
@@ -312,15 +387,17 @@ def run_ours(args, rank, world, local_rank):
     elif prec == R.RBF_FP64:  # FP64 regeneration: ~16 FP64-pipe operations per entry
         ent = n * n / (avg_ms / 1e3)
         peak = 152 * 2 * 2.07e9 / 1e12
-        ops = ent * 16 / 1e12
-        roof = {"bound": "alu", "achieved": round(ops, 4), "peak": round(peak, 4), "unit": "T FP64-pipe ops/s",
-                "frac": round(ops / peak, 4), "traffic": None, "entries_per_s": ent, "ops_per_entry": 16,
+        tops = ent * 16 / 1e12
+        roof = {"bound": "alu", "achieved": round(tops, 4), "peak": round(peak, 4), "unit": "T FP64-pipe ops/s",
+                "frac": round(tops / peak, 4), "traffic": None, "entries_per_s": ent, "ops_per_entry": 16,
                 "peak_source": "152 SMs x 2 FP64 ops/clk x 2.07 GHz (unit counts and max clock)"}
     else:
         roof = mf_roofline(n, ns.n_interior, avg_ms)
     roof["traffic"] = MEASURED_TRAFFIC.get((wl["name"], dom))
-    roof.update({"kernel": kinds[dom], "avg_launch_ms": round(avg_ms, 5),
-                 "avg_launch_ms_both": round(both_avg_ms, 5), "launches_timed": int(p_cnt[0] + p_cnt[1]),
+    roof.update({"kernel": "gemv_n (p = A z) and gemv_t (r = A^T w)", "avg_launch_ms": round(avg_ms, 5),
+                 "avg_launch_ms_how": "union of the product launch intervals / launches (CUDA events on the "
+                                      "launching streams, timed region)",
+                 "avg_launch_ms_events": round(both_avg_ms, 5), "launches_timed": int(p_cnt[0] + p_cnt[1]),
                  "algorithmic_per_launch": (f"{s * n * n} bytes, {2 * n * n} flop" if storage == R.RBF_ASSEMBLED
                                             else f"{n * n} entries")})
     h2d = nodes_h.numel() * 8 + pts_h.numel() * 8 + sum(v.numel() * 8 for v in f_h.values())
@@ -334,9 +411,16 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl["name"], "n": n, "n_interior": ns.n_interior, "gkb_steps": L,
                    "cases_c_k": cases, "solves_per_step": len(cases), "precision": wl["precision"],
                    "storage": wl["storage"], "rule": "gcv", "test_points": m,
-                   "parallelism": f"replicas x{world}",
+                   "parallelism": f"replicas x{world}; the step's independent solves on "
+                                  f"{args.lanes or min(len(cases), 8)} streams",
                    "l2": "inputs larger than L2 (A or node set streamed each product)"},
+        # amortized: the step's device time over its solves (solves run concurrently)
         "time_to_solution_ms": round(ms / (args.steps * len(cases)), 3),
+        "lanes": args.lanes or min(len(cases), 8),
+        "re_exact": {"per_case": [round(x, 6) for x in re_exact], "max": round(max(re_exact), 6),
+                     "exact": wl["exact_name"], "test_points": m},
+        "lambda_over_s1_log10": [round(x, 3) for x in t_chosen],
+        "gaussian_variant": gauss,
         "gkb_steps_done": done, "solves": solves,
         "roofline": roof,
         "e2e": {"value": round(done_e2e / (ms_e2e / 1e3), 2), "unit": "GKB steps/s",
@@ -816,6 +900,51 @@ def run_paper_sweep(args, rank, world, local_rank):
             "rows": rows}
 
 
+# --------------------------------------------------------------------------- FP64 pipe probe
+def run_fp64_probe(args, rank, world, local_rank):
+    """Measured FP64 throughput of this GPU (the peak the FP64 products are
+    reported against): FP64 FMA alone, FP64 MMA (mma.sync m8n8k4) alone, and
+    both issued by every warp, each on one resident wave of CTAs for about
+    0.5 s, with the SM clock sampled by nvidia-smi during the runs."""
+    import torch
+
+    from paper_2511_09798_gb300 import rbfkr as R
+    torch.cuda.set_device(local_rank)
+    dev = f"cuda:{local_rank}"
+    ctx = R.Context(local_rank, stream=torch.cuda.current_stream())
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    scratch = torch.empty(sms * 8 * 256, dtype=torch.float64, device=dev)
+    names = {0: "fp64_fma", 1: "fp64_mma_m8n8k4", 2: "fma_and_mma"}
+    out = {}
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    for mode in (0, 1, 2):
+        iters = 1 << 12
+        ms, fl = ctx.rbf_probe_fp64(mode, iters, scratch)  # warm-up and size
+        iters = max(1, int(iters * 500.0 / max(ms, 1e-3)))
+        best = None
+        for _ in range(3):
+            ms, fl = ctx.rbf_probe_fp64(mode, iters, scratch)
+            if best is None or ms < best[0]:
+                best = (ms, fl)
+        out[names[mode]] = {"tflops": round(best[1] / (best[0] / 1e3) / 1e12, 4), "ms": round(best[0], 2),
+                            "iters": iters}
+    clocks = sampler.stop() if sampler else None
+    ctx.close()
+    if rank != 0:
+        return None
+    mhz = clocks["sm_mhz"] if clocks else 2070.0
+    for v in out.values():
+        v["flop_per_clk_per_sm"] = round(v["tflops"] * 1e12 / (sms * mhz * 1e6), 3)
+    fma = out["fp64_fma"]
+    return {"metric": "FP64 pipe throughput (roofline peak of the FP64 products)", "value": fma["tflops"],
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": 3, "warmup": 1, "ms_per_step": fma["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fp64-pipe-probe", "sms": sms}, "probes": out,
+            "fma_per_clk_per_sm": round(fma["flop_per_clk_per_sm"] / 2, 3), "clocks": clocks}
+
+
 # --------------------------------------------------------------------------- oracle
 def oracle_solve(wl, c, k, steps):
     from oracle import evaluate as OE
@@ -1019,6 +1148,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cube8000")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="streams for the independent (c, k) solves of a step (0 = one per solve, 1 = serial)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--jsonl", default=None, help="also append the result line to this JSONL file")
     ap.add_argument("--single-solve", action="store_true",
@@ -1042,6 +1173,8 @@ def main():
         out = run_learned(args, rank, world, local_rank)
     elif args.workload == "paper-sweep":
         out = run_paper_sweep(args, rank, world, local_rank)
+    elif args.workload == "fp64-pipe-probe":
+        out = run_fp64_probe(args, rank, world, local_rank)
     else:
         out = run_ours(args, rank, world, local_rank)
         if out is not None and not args.no_cpu_baseline:

@@ -164,6 +164,10 @@ typedef struct {
     int64_t launches;           /* every kernel launch issued by the library */
     int64_t product_launches[2];/* timed product launches (A, A^T) */
     double product_ms[2];       /* their summed device time, milliseconds */
+    double product_busy_ms;     /* length of the union of those launch intervals: the time
+                                   during which at least one product ran (equal to the sum
+                                   when products never overlap; smaller when products of
+                                   concurrent runs, rbf_gkb_many, overlap) */
 } rbf_counters;
 
 /* ---- context --------------------------------------------------------- */
@@ -226,6 +230,40 @@ rbf_status rbf_gkb(rbf_ctx* ctx, const rbf_operator* op, const double* d_f, int 
  * operator); a state that already broke down is returned unchanged. */
 rbf_status rbf_gkb_resume(rbf_ctx* ctx, const rbf_operator* op, rbf_gkb_state* st, int more_steps);
 
+/* Checkpoint of a GKB state in host memory: copies w_1..w_{l+1} into h_W
+ * (n x (l+1), column-major, ld n), z_1..z_l into h_Z (n x l), alpha_1..alpha_l
+ * and beta_1..beta_{l+1}, with l = st->steps_done (0 <= l <= capacity); the
+ * scalars steps_done, breakdown and c_hat stay in *st for the caller to keep.
+ * Synchronises.  RBF_ERR_INVALID for NULL pointers or an inconsistent state. */
+rbf_status rbf_gkb_snapshot(rbf_ctx* ctx, const rbf_gkb_state* st, double* h_W, double* h_Z, double* h_alpha,
+                            double* h_beta);
+
+/* Restore a checkpoint written by rbf_gkb_snapshot into the device buffers of
+ * *st (capacity >= steps_done >= 1, the same n) and set its scalars, so that
+ * rbf_gkb_resume continues exactly as the run it was taken from would have.
+ * Synchronises (the host arrays may be released on return).
+ * RBF_ERR_INVALID for NULL pointers or values out of range. */
+rbf_status rbf_gkb_restore(rbf_ctx* ctx, rbf_gkb_state* st, const double* h_W, const double* h_Z,
+                           const double* h_alpha, const double* h_beta, int steps_done, int breakdown, double c_hat);
+
+/* Several independent GKB runs at once (Algorithm 1 for each): run i applies
+ * ops[i] to d_f[i] for `steps` steps into states[i], exactly as rbf_gkb would
+ * (same kernels, so each run's results are bitwise those of rbf_gkb).  The
+ * runs are spread over `lanes` child streams of the context (at most 8; 0 =
+ * one lane per run up to 8; reduced when the half-step kernels of that many
+ * runs would not fit on the SMs together), run i on lane i mod lanes, enqueued one GKB
+ * step per lane in turn, so that one run's latency-bound reorthogonalization
+ * kernels overlap another run's matrix-vector products.  Each lane owns its
+ * own workspace (opt.workspace_cap applies per lane) and device state.  With
+ * `assemble` non-zero each assembled operator is first filled by its lane
+ * (rbf_assemble), so runs must then not share a matrix buffer.  The lanes
+ * start after the work already enqueued on the context stream, and the
+ * context stream waits for all of them before later work.  Synchronises once;
+ * fills every state's steps_done, breakdown and c_hat.  Errors as rbf_gkb,
+ * for the first failing run. */
+rbf_status rbf_gkb_many(rbf_ctx* ctx, int count, const rbf_operator* ops, const double* const* d_f, int steps,
+                        rbf_gkb_state* states, int lanes, int assemble);
+
 /* ---- projected problem (Algorithms 2 and 4) -------------------------- */
 
 /* SVD of the (l+1) x l lower bidiagonal C_l of *st (l = st->steps_done):
@@ -242,6 +280,13 @@ rbf_status rbf_projected_svd(rbf_ctx* ctx, const rbf_gkb_state* st, double* d_si
  * fills *info (eta and rho at the chosen lambda). */
 rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in,
                    double* d_coef, double* d_curve, rbf_solve_info* info);
+
+/* rbf_hkt for `count` finished states at once (same rule and lambda_in for all,
+ * no GCV curve output): d_coef[i] receives Z_l y_lambda of states[i], infos[i]
+ * (optional) its solve information.  Spread over `lanes` child streams as in
+ * rbf_gkb_many; synchronises once; results are bitwise those of rbf_hkt. */
+rbf_status rbf_hkt_many(rbf_ctx* ctx, int count, const rbf_gkb_state* states, int rule, double lambda_in,
+                        double* const* d_coef, rbf_solve_info* infos, int lanes);
 
 /* Inexpensive TSVD (Algorithm 2): rank by GCV_l(k) when rank == 0, else the
  * given rank (1..l); d_coef[n] = Z_l V~_k S~_k^{-1} f~_{1:k}.  d_curve
@@ -456,6 +501,36 @@ typedef struct {
                                   (inputs like the training set's); 0 = no bound */
 } rbf_stopnet;
 
+/* Floats of the device buffer that rbf_stopnet_init / rbf_stopnet_load fill:
+ * the parameters, then the feature mean and std (20 floats each). */
+#define RBF_STOPNET_DEVICE_FLOATS (RBF_MLP_PARAMS + 2 * RBF_MLP_IN)
+
+/* Make a stop network from host arrays: the parameters h_params
+ * (RBF_MLP_PARAMS floats, layout above) and the feature standardisation
+ * h_feat_mean, h_feat_std (20 floats each, or both NULL for none) are copied
+ * into the caller-owned device buffer d_storage (RBF_STOPNET_DEVICE_FLOATS
+ * floats), and *net is filled to point at it; h_out = {out_mean[0],
+ * out_mean[1], out_std[0], out_std[1]} (std > 0), h_rules = {l_min, l_max,
+ * window, fallback_rule} (10 <= l_min <= l_max <= 1023; RBF_GCV or
+ * RBF_LCURVE), h_tols = {accept_tol, t_min, t_max, z_max}; feat_steps = 10.
+ * Synchronises (the host arrays may be released on return).  RBF_ERR_INVALID
+ * for NULL arguments or rules out of range. */
+rbf_status rbf_stopnet_init(rbf_ctx* ctx, rbf_stopnet* net, float* d_storage, const float* h_params,
+                            const float* h_feat_mean, const float* h_feat_std, const float* h_out, const int* h_rules,
+                            const double* h_tols);
+
+/* Write *net (parameters, standardisation, output scaling, acceptance rules
+ * and feat_steps) to the file `path` in the library's binary layout (magic
+ * "RBFSTOP1", native little-endian; see stopnet.cu).  Synchronises.
+ * RBF_ERR_INVALID when the file cannot be written. */
+rbf_status rbf_stopnet_save(rbf_ctx* ctx, const rbf_stopnet* net, const char* path);
+
+/* Read a file written by rbf_stopnet_save and initialise *net on d_storage
+ * (RBF_STOPNET_DEVICE_FLOATS floats, caller-owned) as rbf_stopnet_init does.
+ * RBF_ERR_INVALID for a missing file, a wrong magic or size, trailing bytes or
+ * rules out of range. */
+rbf_status rbf_stopnet_load(rbf_ctx* ctx, const char* path, rbf_stopnet* net, float* d_storage);
+
 typedef struct {
     int l_pred;          /* predicted stopping index after clamping (0 when no prediction was made) */
     double t_pred;       /* predicted log10(lambda / s~_1) */
@@ -489,6 +564,18 @@ rbf_status rbf_learned_hkt(rbf_ctx* ctx, const rbf_operator* op, const double* d
  * solve.steps filled).  Synchronises. */
 rbf_status rbf_batch_learned_hkt(rbf_ctx* ctx, rbf_batch* batch, const rbf_stopnet* net, double* d_coef,
                                  rbf_learned_info* h_info);
+
+/* ---- measurement (not part of the method) ------------------------------- */
+
+/* Throughput probe of the FP64 units (the roofline peak of the FP64
+ * matrix-vector products): mode 0 FP64 FMA (8 independent chains per
+ * thread), 1 FP64 MMA (mma.sync m8n8k4, 4 independent accumulators per warp),
+ * 2 both in every warp; `iters` iterations per thread on one resident wave of
+ * CTAs.  *ms receives the CUDA-event time on the context stream, *flops the
+ * floating-point operations (an FMA counts 2, an m8n8k4 MMA 512).  d_out:
+ * device scratch of (SMs x 8 x 256) doubles, never written in practice.
+ * Synchronises.  RBF_ERR_INVALID for other modes, iters < 1 or NULL outputs. */
+rbf_status rbf_probe_fp64(rbf_ctx* ctx, int mode, long long iters, double* d_out, double* ms, double* flops);
 
 /* ---- allocation-free product (no counterpart in the paper) ------------- */
 

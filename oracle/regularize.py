@@ -241,9 +241,19 @@ class FullSVD:
     n: int
 
 
-def full_svd(A, f) -> FullSVD:
-    """Economy SVD of A, f^ = U^T f, s_perp = sum_{i>r} f^_i^2 (Alg. 3 steps 1-2)."""
-    U, s, Vt = np.linalg.svd(A, full_matrices=False)
+def full_svd(A, f, driver="gesdd") -> FullSVD:
+    """Economy SVD of A, f^ = U^T f, s_perp = sum_{i>r} f^_i^2 (Alg. 3 steps 1-2).
+
+    driver: the LAPACK routine, "gesdd" (divide and conquer, through NumPy) or
+    "gesvd" (QR iteration, through SciPy): two backward-stable SVDs whose
+    difference measures how much a result depends on rounding alone."""
+    if driver == "gesdd":
+        U, s, Vt = np.linalg.svd(A, full_matrices=False)
+    elif driver == "gesvd":
+        import scipy.linalg
+        U, s, Vt = scipy.linalg.svd(A, full_matrices=False, lapack_driver="gesvd")
+    else:
+        raise ValueError(driver)
     n = A.shape[0]
     r = int(np.sum(s > n * EPS * s[0])) if s[0] > 0 else 0
     fhat = U.T @ f

@@ -1,6 +1,9 @@
 // Context, workspace, errors, timings and operator validation.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 
@@ -37,17 +40,88 @@ rbf_status rbf_ws_reserve(rbf_ctx* ctx, size_t bytes) {
     return RBF_OK;
 }
 
+// Product-launch timing: a lane records on its own stream into its owner's
+// event slots (the owner's base event precedes every lane's work, see
+// rbf_lanes_fork), so that busy intervals of all lanes share one time origin.
 int rbf_prod_begin(rbf_ctx* ctx, int trans) {
-    ctx->ptotal[trans]++;
-    if (!(ctx->opt.timing & 2) || !ctx->pev || ctx->pcount[trans] >= rbf_ctx::PMAX) return -1;
-    const int slot = ctx->pcount[trans]++;
-    cudaEventRecord(ctx->pev[((size_t)trans * rbf_ctx::PMAX + slot) * 2], ctx->stream);
+    rbf_ctx* o = ctx->owner ? ctx->owner : ctx;
+    o->ptotal[trans]++;
+    if (!(o->opt.timing & 2) || !o->pev || o->pcount[trans] >= rbf_ctx::PMAX) return -1;
+    if (!o->pbase_set) {
+        cudaEventRecord(o->pbase, ctx->stream);
+        o->pbase_set = true;
+    }
+    const int slot = o->pcount[trans]++;
+    cudaEventRecord(o->pev[((size_t)trans * rbf_ctx::PMAX + slot) * 2], ctx->stream);
     return slot;
 }
 
 void rbf_prod_end(rbf_ctx* ctx, int trans, int slot) {
     if (slot < 0) return;
-    cudaEventRecord(ctx->pev[((size_t)trans * rbf_ctx::PMAX + slot) * 2 + 1], ctx->stream);
+    rbf_ctx* o = ctx->owner ? ctx->owner : ctx;
+    cudaEventRecord(o->pev[((size_t)trans * rbf_ctx::PMAX + slot) * 2 + 1], ctx->stream);
+}
+
+rbf_status rbf_lane(rbf_ctx* ctx, int i, rbf_ctx** out) {
+    if (!ctx->lane[i]) {
+        rbf_options o = ctx->opt;
+        o.timing = 0;  // a lane's product timings go to its owner; no per-phase timers
+        cudaStream_t s = nullptr;
+        RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+        RBF_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        rbf_ctx* l = nullptr;
+        if (rbf_create(&l, ctx->device, s, &o) != RBF_OK) {
+            cudaStreamDestroy(s);
+            return rbf_fail(ctx, RBF_ERR_CUDA, "creating lane %d failed", i);
+        }
+        l->own_stream = true;
+        l->owner = ctx;
+        ctx->lane[i] = l;
+    }
+    *out = ctx->lane[i];
+    return RBF_OK;
+}
+
+rbf_status rbf_many_slots(rbf_ctx* ctx, int count) {
+    if (count <= ctx->h_many_cap) return RBF_OK;
+    if (ctx->h_many) {
+        RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaFreeHost(ctx->h_many);
+        ctx->h_many = nullptr;
+        ctx->h_many_cap = 0;
+    }
+    RBF_CUDA(ctx, cudaMallocHost(&ctx->h_many, sizeof(rbf_dev_state) * (size_t)count));
+    ctx->h_many_cap = count;
+    return RBF_OK;
+}
+
+rbf_status rbf_lanes_fork(rbf_ctx* ctx, int lanes) {
+    if (ctx->pev && !ctx->pbase_set) {  // product timing: the origin precedes all lanes
+        RBF_CUDA(ctx, cudaEventRecord(ctx->pbase, ctx->stream));
+        ctx->pbase_set = true;
+    }
+    RBF_CUDA(ctx, cudaEventRecord(ctx->sync_ev, ctx->stream));
+    for (int i = 0; i < lanes; ++i) {
+        rbf_ctx* l = nullptr;
+        RBF_TRY(rbf_lane(ctx, i, &l));
+        RBF_CUDA(ctx, cudaStreamWaitEvent(l->stream, ctx->sync_ev, 0));
+    }
+    return RBF_OK;
+}
+
+rbf_status rbf_lanes_join(rbf_ctx* ctx, int lanes) {
+    rbf_status st = RBF_OK;
+    for (int i = 0; i < lanes; ++i) {
+        rbf_ctx* l = ctx->lane[i];
+        if (!l) continue;
+        ctx->launches += l->launches;
+        l->launches = 0;
+        cudaError_t e = cudaEventRecord(l->sync_ev, l->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, l->sync_ev, 0);
+        if (e != cudaSuccess && st == RBF_OK)
+            st = rbf_fail(ctx, RBF_ERR_CUDA, "joining lane %d failed: %s", i, cudaGetErrorString(e));
+    }
+    return st;
 }
 
 void rbf_timer_start(rbf_ctx* ctx) {
@@ -91,6 +165,8 @@ rbf_status rbf_create(rbf_ctx** out, int device, void* cuda_stream, const rbf_op
     if (e == cudaSuccess) e = cudaMemset(ctx->d_state, 0, sizeof(rbf_dev_state));
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev[1]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->pbase);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->sync_ev, cudaEventDisableTiming);
     if (e == cudaSuccess && (ctx->opt.timing & 2)) {
         const size_t ne = (size_t)2 * rbf_ctx::PMAX * 2;
         ctx->pev = new cudaEvent_t[ne]();
@@ -112,26 +188,52 @@ rbf_status rbf_get_counters(rbf_ctx* ctx, rbf_counters* out, int reset) {
         out->product_launches[t] = ctx->pcount[t];
         out->product_ms[t] = 0.0;
     }
+    out->product_busy_ms = 0.0;
     if (ctx->pev && (ctx->pcount[0] || ctx->pcount[1])) {
         RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int i = 0; i < rbf_ctx::MAX_LANES; ++i)
+            if (ctx->lane[i]) RBF_CUDA(ctx, cudaStreamSynchronize(ctx->lane[i]->stream));
+        std::vector<std::pair<double, double>> iv;
+        iv.reserve((size_t)ctx->pcount[0] + ctx->pcount[1]);
         for (int t = 0; t < 2; ++t)
             for (int i = 0; i < ctx->pcount[t]; ++i) {
-                float ms = 0.f;
+                float ms = 0.f, t0 = 0.f, t1 = 0.f;
                 const size_t b = ((size_t)t * rbf_ctx::PMAX + i) * 2;
                 RBF_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->pev[b], ctx->pev[b + 1]));
+                RBF_CUDA(ctx, cudaEventElapsedTime(&t0, ctx->pbase, ctx->pev[b]));
+                RBF_CUDA(ctx, cudaEventElapsedTime(&t1, ctx->pbase, ctx->pev[b + 1]));
                 out->product_ms[t] += ms;
+                iv.emplace_back((double)t0, (double)t1);
             }
+        // union of the launch intervals: time during which any product ran
+        std::sort(iv.begin(), iv.end());
+        double cs = iv[0].first, ce = iv[0].second;
+        for (size_t i = 1; i < iv.size(); ++i) {
+            if (iv[i].first > ce) {
+                out->product_busy_ms += ce - cs;
+                cs = iv[i].first;
+                ce = iv[i].second;
+            } else if (iv[i].second > ce) {
+                ce = iv[i].second;
+            }
+        }
+        out->product_busy_ms += ce - cs;
     }
     if (reset) {
         ctx->launches = 0;
         ctx->pcount[0] = ctx->pcount[1] = 0;
         ctx->ptotal[0] = ctx->ptotal[1] = 0;
+        ctx->pbase_set = false;
     }
     return RBF_OK;
 }
 
 rbf_status rbf_destroy(rbf_ctx* ctx) {
     if (!ctx) return RBF_OK;
+    for (auto& l : ctx->lane) {
+        rbf_destroy(l);
+        l = nullptr;
+    }
     if (ctx->stream || ctx->d_state) cudaStreamSynchronize(ctx->stream);
     rbf_batch_state_free(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
@@ -139,6 +241,10 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
     for (auto& ev : ctx->ev)
         if (ev) cudaEventDestroy(ev);
+    if (ctx->pbase) cudaEventDestroy(ctx->pbase);
+    if (ctx->sync_ev) cudaEventDestroy(ctx->sync_ev);
+    if (ctx->h_many) cudaFreeHost(ctx->h_many);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     if (ctx->pev) {
         for (size_t i = 0; i < (size_t)2 * rbf_ctx::PMAX * 2; ++i)
             if (ctx->pev[i]) cudaEventDestroy(ctx->pev[i]);

@@ -22,6 +22,7 @@
 // breakdown is found a device flag makes every later kernel return at once.
 #include <algorithm>
 #include <cfloat>
+#include <vector>
 
 #include "common.cuh"
 #include "internal.h"
@@ -421,6 +422,16 @@ __global__ void k_reset_state(rbf_dev_state* stt, int steps_done, double beta_no
 // the 227 KB a CTA may opt into, less about 2 KB of static shared memory
 constexpr size_t HALF_SMEM_STAGE_MAX = 224 * 1024;
 
+// Dynamic shared memory up to which the half-step kernel stages its Q slab.  A
+// context whose work runs on several lanes (rbf_gkb_many) keeps each half-step
+// CTA small enough that one CTA of every lane fits on an SM at once, so that
+// the lanes' cooperative grids can always be resident together.
+static size_t half_stage_limit(const rbf_ctx* ctx) {
+    const int lanes = ctx->owner ? ctx->owner->lane_count : 1;
+    if (lanes <= 1) return HALF_SMEM_STAGE_MAX;
+    return (size_t)200 * 1024 / (size_t)lanes - 4 * 1024;
+}
+
 static size_t half_smem_bytes(bool stage, int mcount, int chunks, int rmax) {
     const size_t scratch = std::max((size_t)SPLIT * rmax, (size_t)(SPLIT + 1) * mcount);
     return ((stage ? (size_t)mcount * rmax : 0) + (size_t)chunks * rmax + (size_t)3 * rmax + scratch) * sizeof(double);
@@ -477,85 +488,103 @@ static rbf_status gkb_product(rbf_ctx* ctx, const rbf_operator* op, int trans, c
     return st;
 }
 
-rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_begin, int j_end,
-                   rbf_gkb_state* st) {
-    const int64_t n = op->n;
-    const int G = slab_grid(ctx, n);
-    if ((n + G - 1) / G > SL_MAX_ROWS) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large for slab kernels");
-    if (st->capacity + 1 > 1024) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "capacity above 1023 steps");
-    RBF_TRY(rbf_ws_reserve(ctx, gkb_ws_bytes(ctx, n, st->capacity, op->precision)));
-    WsCarve wc(ctx->ws);
-    const int chT = product_chunks(ctx, op, 1), chN = product_chunks(ctx, op, 0);
-    double* part = wc.take<double>((size_t)(chT > chN ? chT : chN) * n);
-    double* vr = wc.take<double>((size_t)n);
-    double* vp = wc.take<double>((size_t)n);
-    float* vr32 = wc.take<float>((size_t)n);
-    float* vp32 = wc.take<float>((size_t)n);
-    double* hpart = wc.take<double>((size_t)(st->capacity + 2) * G);
-    int bar_group = 1;
-    while (bar_group * bar_group < G) ++bar_group;
-    const int bar_k = (G + bar_group - 1) / bar_group;
-    double* gpart = wc.take<double>((size_t)2 * (st->capacity + 2) * G);
-    unsigned* bar = wc.take<unsigned>((size_t)(bar_k + 2) * BAR_STRIDE);
-    RBF_CUDA(ctx, cudaMemsetAsync(bar, 0, (size_t)(bar_k + 2) * BAR_STRIDE * sizeof(unsigned), ctx->stream));
-    // shared-memory plan of the half-step kernel: stage the Q slab when it fits
-    const int rmax = (int)((n + G - 1) / G) | 1;
-    const int chmax = chT > chN ? chT : chN;
-    // The Q slab is staged in every half-step whose slab fits (mcount grows with
-    // the step, so long runs on large N stage their early steps only); the
-    // unstaged kernel must fit for the largest basis.
-    {
-        const size_t need = half_smem_bytes(false, st->capacity + 1, chmax, rmax);
-        if (need > HALF_SMEM_STAGE_MAX)
-            return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "half-step shared memory too large (%zu bytes)", need);
-        if (need > 48 * 1024)
-            RBF_CUDA(ctx, cudaFuncSetAttribute((const void*)k_half<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)need));
-        RBF_CUDA(ctx, cudaFuncSetAttribute((const void*)k_half<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)HALF_SMEM_STAGE_MAX));
-    }
-    double* npart = wc.take<double>((size_t)G);
-    rbf_dev_state* dst = ctx->d_state;
-    const int* done = &dst->info[IN_DONE];
-    const bool mixed = op->precision == RBF_MIXED;
-    const double factor = ctx->opt.breakdown_factor;
-    cudaStream_t s = ctx->stream;
-    double* W = st->d_W;
-    double* Z = st->d_Z;
-    const int64_t ldw = st->ldw, ldz = st->ldz;
-
-    // q_raw for the first r-side: f (fresh run) or the stored w_{j_begin} (resume)
-    const double* q_raw = vp;
-    if (j_begin == 1) {
-        k_reset_state<<<1, 32, 0, s>>>(dst, 0, 0.0, 0.0, 0);
-        RBF_LAUNCHED(ctx, "k_reset_state");
-        k_norm_partials<<<G, SL_THREADS, 0, s>>>(n, f, npart, vp, mixed ? vp32 : nullptr);
-        RBF_LAUNCHED(ctx, "k_norm_partials");
-    } else {
-        // resume: beta_{j_begin} and w_{j_begin} are stored in the state
-        double beta_now = 0.0;
-        RBF_CUDA(ctx, cudaMemcpyAsync(&beta_now, st->d_beta + (j_begin - 1), sizeof(double),
-                                      cudaMemcpyDeviceToHost, s));
-        RBF_CUDA(ctx, cudaStreamSynchronize(s));
-        k_reset_state<<<1, 32, 0, s>>>(dst, j_begin - 1, beta_now, st->c_hat, 1);
-        RBF_LAUNCHED(ctx, "k_reset_state");
-        q_raw = W + (int64_t)(j_begin - 1) * ldw;
-        k_norm_partials<<<G, SL_THREADS, 0, s>>>(n, q_raw, npart, vp, mixed ? vp32 : nullptr);
-        RBF_LAUNCHED(ctx, "k_norm_partials");
-        q_raw = vp;
-    }
+// One GKB run split into its launch sequence, so that several independent runs
+// can be enqueued step by step on different streams (rbf_gkb_many): begin()
+// prepares the workspace and the first r-side input, step(j) enqueues the
+// four launches of step j, end() closes with beta_{l+1} and w_{l+1}.  Nothing
+// here synchronises except the resume path, which reads beta_{j_begin}.
+struct GkbRun {
+    rbf_ctx* ctx = nullptr;
+    const rbf_operator* op = nullptr;
+    rbf_gkb_state* st = nullptr;
+    int64_t n = 0;
+    int G = 0, chT = 0, chN = 0, rmax = 0, bar_group = 0, bar_k = 0, j_begin = 1;
+    double *part = nullptr, *vr = nullptr, *vp = nullptr, *hpart = nullptr, *gpart = nullptr, *npart = nullptr;
+    float *vr32 = nullptr, *vp32 = nullptr;
+    unsigned* bar = nullptr;
+    const double* q_raw = nullptr;
     unsigned epochs = 0;  // barriers on `bar` since it was zeroed
-    auto half = [&](int side, int j, int resume, const double* u, const double* qr, double* bout,
-                    double* v, float* v32, const double* Q, int64_t ldq, int mcount, int chunks) -> rbf_status {
+    bool mixed = false;
+
+    rbf_status begin(rbf_ctx* c, const rbf_operator* o, const double* f, int jb, rbf_gkb_state* s_) {
+        ctx = c;
+        op = o;
+        st = s_;
+        j_begin = jb;
+        n = op->n;
+        G = slab_grid(ctx, n);
+        if ((n + G - 1) / G > SL_MAX_ROWS) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large for slab kernels");
+        if (st->capacity + 1 > 1024) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "capacity above 1023 steps");
+        RBF_TRY(rbf_ws_reserve(ctx, gkb_ws_bytes(ctx, n, st->capacity, op->precision)));
+        WsCarve wc(ctx->ws);
+        chT = product_chunks(ctx, op, 1);
+        chN = product_chunks(ctx, op, 0);
+        part = wc.take<double>((size_t)(chT > chN ? chT : chN) * n);
+        vr = wc.take<double>((size_t)n);
+        vp = wc.take<double>((size_t)n);
+        vr32 = wc.take<float>((size_t)n);
+        vp32 = wc.take<float>((size_t)n);
+        hpart = wc.take<double>((size_t)(st->capacity + 2) * G);
+        bar_group = 1;
+        while (bar_group * bar_group < G) ++bar_group;
+        bar_k = (G + bar_group - 1) / bar_group;
+        gpart = wc.take<double>((size_t)2 * (st->capacity + 2) * G);
+        bar = wc.take<unsigned>((size_t)(bar_k + 2) * BAR_STRIDE);
+        cudaStream_t s = ctx->stream;
+        RBF_CUDA(ctx, cudaMemsetAsync(bar, 0, (size_t)(bar_k + 2) * BAR_STRIDE * sizeof(unsigned), s));
+        // shared-memory plan of the half-step kernel: stage the Q slab when it fits
+        rmax = (int)((n + G - 1) / G) | 1;
+        const int chmax = chT > chN ? chT : chN;
+        // The Q slab is staged in every half-step whose slab fits (mcount grows with
+        // the step, so long runs on large N stage their early steps only); the
+        // unstaged kernel must fit for the largest basis.
+        {
+            const size_t need = half_smem_bytes(false, st->capacity + 1, chmax, rmax);
+            if (need > HALF_SMEM_STAGE_MAX)
+                return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "half-step shared memory too large (%zu bytes)", need);
+            if (need > 48 * 1024)
+                RBF_CUDA(ctx, cudaFuncSetAttribute((const void*)k_half<false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+            RBF_CUDA(ctx, cudaFuncSetAttribute((const void*)k_half<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)HALF_SMEM_STAGE_MAX));
+        }
+        npart = wc.take<double>((size_t)G);
+        mixed = op->precision == RBF_MIXED;
+        rbf_dev_state* dst = ctx->d_state;
+        epochs = 0;
+        // q_raw for the first r-side: f (fresh run) or the stored w_{j_begin} (resume)
+        q_raw = vp;
+        if (j_begin == 1) {
+            k_reset_state<<<1, 32, 0, s>>>(dst, 0, 0.0, 0.0, 0);
+            RBF_LAUNCHED(ctx, "k_reset_state");
+            k_norm_partials<<<G, SL_THREADS, 0, s>>>(n, f, npart, vp, mixed ? vp32 : nullptr);
+            RBF_LAUNCHED(ctx, "k_norm_partials");
+        } else {
+            // resume: beta_{j_begin} and w_{j_begin} are stored in the state
+            double beta_now = 0.0;
+            RBF_CUDA(ctx, cudaMemcpyAsync(&beta_now, st->d_beta + (j_begin - 1), sizeof(double),
+                                          cudaMemcpyDeviceToHost, s));
+            RBF_CUDA(ctx, cudaStreamSynchronize(s));
+            k_reset_state<<<1, 32, 0, s>>>(dst, j_begin - 1, beta_now, st->c_hat, 1);
+            RBF_LAUNCHED(ctx, "k_reset_state");
+            const double* w = st->d_W + (int64_t)(j_begin - 1) * st->ldw;
+            k_norm_partials<<<G, SL_THREADS, 0, s>>>(n, w, npart, vp, mixed ? vp32 : nullptr);
+            RBF_LAUNCHED(ctx, "k_norm_partials");
+        }
+        return RBF_OK;
+    }
+
+    rbf_status half(int side, int j, int resume, const double* u, const double* qr, double* bout, double* v,
+                    float* v32, const double* Q, int64_t ldq, int mcount, int chunks) {
         HalfArgs a;
-        a.stt = dst;
+        a.stt = ctx->d_state;
         a.n = n;
         a.chunks = chunks;
         a.part = part;
         a.side = side;
         a.j = j;
         a.resume = resume;
-        a.factor = factor;
+        a.factor = ctx->opt.breakdown_factor;
         a.alpha = st->d_alpha;
         a.beta = st->d_beta;
         a.u = u;
@@ -575,17 +604,22 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
         a.epoch0 = epochs;
         a.budget = ctx->opt.wait_budget;
         void* args[] = {&a};
-        const bool stage = half_smem_bytes(true, mcount, chunks, rmax) <= HALF_SMEM_STAGE_MAX;
+        const bool stage = half_smem_bytes(true, mcount, chunks, rmax) <= half_stage_limit(ctx);
         const size_t smem = half_smem_bytes(stage, mcount, chunks, rmax);
         cudaError_t e = cudaLaunchCooperativeKernel(stage ? (const void*)k_half<true> : (const void*)k_half<false>,
-                                                    dim3(G), dim3(SL_THREADS), args, smem, s);
+                                                    dim3(G), dim3(SL_THREADS), args, smem, ctx->stream);
         ctx->launches++;
         if (e != cudaSuccess)
             return rbf_fail(ctx, RBF_ERR_CUDA, "cooperative launch of k_half failed: %s", cudaGetErrorString(e));
         epochs += mcount > 0 ? 2 : 1;  // two reorthogonalization barriers, or one plain barrier
         return RBF_OK;
-    };
-    for (int j = j_begin; j <= j_end; ++j) {
+    }
+
+    rbf_status step(int j) {
+        const int* done = &ctx->d_state->info[IN_DONE];
+        double* W = st->d_W;
+        double* Z = st->d_Z;
+        const int64_t ldw = st->ldw, ldz = st->ldz;
         // ---------------- r-side: r = A^T w_j - beta_j z_{j-1} ----------------
         RBF_TRY(gkb_product(ctx, op, 1, q_raw, vp32, part, done));
         RBF_TRY(half(0, j, (j == j_begin && j_begin > 1) ? 1 : 0, j >= 2 ? Z + (int64_t)(j - 2) * ldz : nullptr,
@@ -595,15 +629,28 @@ rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_
         RBF_TRY(half(1, j, 0, W + (int64_t)(j - 1) * ldw, vr, Z + (int64_t)(j - 1) * ldz, vp,
                      mixed ? vp32 : nullptr, W, ldw, j, chN));
         q_raw = vp;
+        return RBF_OK;
     }
-    // beta_{l+1} and w_{l+1}
-    k_finalize<<<1, 256, 0, s>>>(dst, npart, G, 0, j_end + 1, n, factor, st->d_alpha, st->d_beta,
-                                 W + (int64_t)j_end * ldw, 1);
-    RBF_LAUNCHED(ctx, "k_finalize");
-    k_write_basis<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dst, n, SC_INV_BETA, vp,
-                                                              W + (int64_t)j_end * ldw);
-    RBF_LAUNCHED(ctx, "k_write_basis");
-    return RBF_OK;
+
+    rbf_status end(int j_end) {
+        cudaStream_t s = ctx->stream;
+        double* wl = st->d_W + (int64_t)j_end * st->ldw;
+        // beta_{l+1} and w_{l+1}
+        k_finalize<<<1, 256, 0, s>>>(ctx->d_state, npart, G, 0, j_end + 1, n, ctx->opt.breakdown_factor,
+                                     st->d_alpha, st->d_beta, wl, 1);
+        RBF_LAUNCHED(ctx, "k_finalize");
+        k_write_basis<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctx->d_state, n, SC_INV_BETA, vp, wl);
+        RBF_LAUNCHED(ctx, "k_write_basis");
+        return RBF_OK;
+    }
+};
+
+rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_begin, int j_end,
+                   rbf_gkb_state* st) {
+    GkbRun r;
+    RBF_TRY(r.begin(ctx, op, f, j_begin, st));
+    for (int j = j_begin; j <= j_end; ++j) RBF_TRY(r.step(j));
+    return r.end(j_end);
 }
 
 static rbf_status check_state(rbf_ctx* ctx, const rbf_operator* op, const rbf_gkb_state* st, int steps) {
@@ -662,5 +709,162 @@ extern "C" rbf_status rbf_gkb_resume(rbf_ctx* ctx, const rbf_operator* op, rbf_g
     RBF_TRY(read_back(ctx, st));
     ctx->tim.gkb_ms = rbf_timer_stop(ctx);
     ctx->tim.gkb_steps = st->steps_done - l0;
+    return RBF_OK;
+}
+
+// Several independent GKB runs, spread over lanes (child contexts with their
+// own streams) and enqueued one step at a time per lane, so that one run's
+// latency-bound half-step kernels and launch gaps overlap another run's
+// products.  Each lane runs its share of the runs one after another.
+extern "C" rbf_status rbf_gkb_many(rbf_ctx* ctx, int count, const rbf_operator* ops, const double* const* d_f,
+                                   int steps, rbf_gkb_state* states, int lanes, int assemble) {
+    RbfRange range_("rbf_gkb_many");
+    if (!ctx) return RBF_ERR_INVALID;
+    if (count < 1 || !ops || !d_f || !states) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_gkb_many: bad arguments");
+    if (lanes < 0 || lanes > rbf_ctx::MAX_LANES)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "lanes must be 0 (default) or 1..%d", rbf_ctx::MAX_LANES);
+    for (int i = 0; i < count; ++i) {
+        if (!d_f[i]) return rbf_fail(ctx, RBF_ERR_INVALID, "d_f[%d] is NULL", i);
+        RBF_TRY(check_state(ctx, &ops[i], &states[i], steps));
+    }
+    int L = lanes == 0 ? rbf_ctx::MAX_LANES : lanes;
+    if (L > count) L = count;
+    // every lane's half-step grid must fit on the SMs beside the other lanes'
+    // (they are cooperative and wait for one another's CTAs only within a grid)
+    for (int i = 0; i < count && L > 1; ++i) {
+        const int64_t n = ops[i].n;
+        const int G = slab_grid(ctx, n);
+        const int rmax = (int)((n + G - 1) / G) | 1;
+        const int chmax = std::max(product_chunks(ctx, &ops[i], 0), product_chunks(ctx, &ops[i], 1));
+        const size_t need = half_smem_bytes(false, states[i].capacity + 1, chmax, rmax);
+        if (need > HALF_SMEM_STAGE_MAX) continue;  // the run itself is refused with RBF_ERR_UNSUPPORTED below
+        int per_sm = 0;
+        if (need > 48 * 1024)
+            RBF_CUDA(ctx, cudaFuncSetAttribute((const void*)k_half<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)need));
+        RBF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_half<false>, SL_THREADS,
+                                                                    need));
+        const int64_t fit = (int64_t)per_sm * ctx->sm_count / G;
+        if (fit < L) L = fit < 1 ? 1 : (int)fit;
+    }
+    ctx->lane_count = L;
+    RBF_TRY(rbf_many_slots(ctx, count));
+    RBF_TRY(rbf_lanes_fork(ctx, L));
+    rbf_timer_start(ctx);
+    std::vector<rbf_ctx*> lane(L);
+    for (int l = 0; l < L; ++l) RBF_TRY(rbf_lane(ctx, l, &lane[l]));
+    // workspace sized once per lane for the largest of its runs (growing it
+    // between runs would synchronise the lane)
+    for (int l = 0; l < L; ++l) {
+        size_t need = 0;
+        for (int i = l; i < count; i += L)
+            need = std::max(need, gkb_ws_bytes(lane[l], ops[i].n, states[i].capacity, ops[i].precision));
+        rbf_status e = rbf_ws_reserve(lane[l], need);
+        if (e != RBF_OK) {
+            rbf_lanes_join(ctx, L);
+            return rbf_fail(ctx, e, "lane %d: %s", l, rbf_last_error(lane[l]));
+        }
+    }
+    std::vector<GkbRun> run(count);
+    std::vector<int> cur(L), jnext(L, 0);  // lane l: its current run and the next step (0 = not begun)
+    for (int l = 0; l < L; ++l) cur[l] = l;
+    rbf_status err = RBF_OK;
+    for (bool busy = true; busy && err == RBF_OK;) {
+        busy = false;
+        for (int l = 0; l < L && err == RBF_OK; ++l) {
+            const int i = cur[l];
+            if (i >= count) continue;
+            busy = true;
+            rbf_ctx* c = lane[l];
+            if (jnext[l] == 0) {
+                if (assemble && ops[i].storage == RBF_ASSEMBLED) err = launch_assemble(c, &ops[i]);
+                if (err == RBF_OK) err = run[i].begin(c, &ops[i], d_f[i], 1, &states[i]);
+                jnext[l] = 1;
+            }
+            if (err == RBF_OK) err = run[i].step(jnext[l]++);
+            if (err == RBF_OK && jnext[l] > steps) {
+                err = run[i].end(steps);
+                if (err == RBF_OK) {
+                    cudaError_t e = cudaMemcpyAsync(&ctx->h_many[i], c->d_state, sizeof(rbf_dev_state),
+                                                    cudaMemcpyDeviceToHost, c->stream);
+                    if (e != cudaSuccess)
+                        err = rbf_fail(c, RBF_ERR_CUDA, "state copy failed: %s", cudaGetErrorString(e));
+                }
+                cur[l] += L;
+                jnext[l] = 0;
+            }
+            if (err != RBF_OK) rbf_fail(ctx, err, "lane %d, run %d: %s", l, i, rbf_last_error(c));
+        }
+    }
+    rbf_status je = rbf_lanes_join(ctx, L);
+    if (err != RBF_OK) return err;
+    RBF_TRY(je);
+    RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    RBF_CUDA(ctx, cudaGetLastError());
+    int total = 0;
+    for (int i = 0; i < count; ++i) {
+        const rbf_dev_state& h = ctx->h_many[i];
+        states[i].steps_done = h.info[IN_STEPS];
+        states[i].breakdown = h.info[IN_BREAK];
+        states[i].c_hat = std::max(h.scal[SC_CHAT0], h.scal[SC_CHAT1]);
+        total += states[i].steps_done;
+        if (h.info[IN_ERR] != 0)
+            return rbf_fail(ctx, (rbf_status)h.info[IN_ERR],
+                            "run %d: a bounded device-side wait gave up (grid barrier of the GKB half-step)", i);
+    }
+    ctx->tim.gkb_ms = rbf_timer_stop(ctx);
+    ctx->tim.gkb_steps = total;
+    return RBF_OK;
+}
+
+// Host snapshot of a GKB state (checkpoint/resume through host memory): the
+// first l+1 columns of W, l of Z, alpha[l] and beta[l+1], packed with leading
+// dimension n on the host.
+extern "C" rbf_status rbf_gkb_snapshot(rbf_ctx* ctx, const rbf_gkb_state* st, double* h_W, double* h_Z,
+                                       double* h_alpha, double* h_beta) {
+    RbfRange range_("rbf_gkb_snapshot");
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!st || !h_W || !h_Z || !h_alpha || !h_beta || !st->d_W || !st->d_Z || !st->d_alpha || !st->d_beta)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_gkb_snapshot: NULL argument");
+    const int l = st->steps_done;
+    const int64_t n = st->n;
+    if (l < 0 || l > st->capacity || n < 1 || st->ldw < n || st->ldz < n)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_gkb_snapshot: inconsistent state");
+    cudaStream_t s = ctx->stream;
+    RBF_CUDA(ctx, cudaMemcpy2DAsync(h_W, n * sizeof(double), st->d_W, st->ldw * sizeof(double), n * sizeof(double),
+                                    (size_t)l + 1, cudaMemcpyDeviceToHost, s));
+    if (l > 0) {
+        RBF_CUDA(ctx, cudaMemcpy2DAsync(h_Z, n * sizeof(double), st->d_Z, st->ldz * sizeof(double),
+                                        n * sizeof(double), (size_t)l, cudaMemcpyDeviceToHost, s));
+        RBF_CUDA(ctx, cudaMemcpyAsync(h_alpha, st->d_alpha, (size_t)l * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    RBF_CUDA(ctx, cudaMemcpyAsync(h_beta, st->d_beta, ((size_t)l + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RBF_CUDA(ctx, cudaStreamSynchronize(s));
+    return RBF_OK;
+}
+
+extern "C" rbf_status rbf_gkb_restore(rbf_ctx* ctx, rbf_gkb_state* st, const double* h_W, const double* h_Z,
+                                      const double* h_alpha, const double* h_beta, int steps_done, int breakdown,
+                                      double c_hat) {
+    RbfRange range_("rbf_gkb_restore");
+    if (!ctx) return RBF_ERR_INVALID;
+    if (!st || !h_W || !h_Z || !h_alpha || !h_beta || !st->d_W || !st->d_Z || !st->d_alpha || !st->d_beta)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_gkb_restore: NULL argument");
+    const int l = steps_done;
+    const int64_t n = st->n;
+    if (l < 1 || l > st->capacity || n < 1 || st->ldw < n || st->ldz < n || breakdown < 0 || breakdown > 3 ||
+        !(c_hat >= 0.0))
+        return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_gkb_restore: steps_done outside [1, capacity] or bad scalars");
+    cudaStream_t s = ctx->stream;
+    RBF_CUDA(ctx, cudaMemcpy2DAsync(st->d_W, st->ldw * sizeof(double), h_W, n * sizeof(double), n * sizeof(double),
+                                    (size_t)l + 1, cudaMemcpyHostToDevice, s));
+    RBF_CUDA(ctx, cudaMemcpy2DAsync(st->d_Z, st->ldz * sizeof(double), h_Z, n * sizeof(double), n * sizeof(double),
+                                    (size_t)l, cudaMemcpyHostToDevice, s));
+    RBF_CUDA(ctx, cudaMemcpyAsync(st->d_alpha, h_alpha, (size_t)l * sizeof(double), cudaMemcpyHostToDevice, s));
+    RBF_CUDA(ctx, cudaMemcpyAsync(st->d_beta, h_beta, ((size_t)l + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+    RBF_CUDA(ctx, cudaStreamSynchronize(s));  // the host arrays may be released on return
+    st->steps_done = l;
+    st->breakdown = breakdown;
+    st->c_hat = c_hat;
     return RBF_OK;
 }

@@ -61,8 +61,30 @@ struct rbf_ctx {
     int pcount[2] = {0, 0};       // recorded pairs per product kind
     int64_t ptotal[2] = {0, 0};   // launches per product kind
     void* batch_state = nullptr;  // batched GKB: tuning choice, captured graph, stream
+    cudaEvent_t pbase = nullptr;  // origin of the product-launch intervals since the last reset
+    bool pbase_set = false;
+    // Lanes: child contexts with their own stream, device state and workspace on
+    // which rbf_gkb_many / rbf_hkt_many run independent problems concurrently.
+    // A lane records its product timings into its owner's counters.
+    static constexpr int MAX_LANES = 8;
+    rbf_ctx* lane[MAX_LANES] = {};
+    int lane_count = 1;              // lanes in use by the current multi-run call
+    rbf_ctx* owner = nullptr;        // set on a lane: the context it belongs to
+    bool own_stream = false;         // a lane owns (and destroys) its stream
+    cudaEvent_t sync_ev = nullptr;   // fork (owner) or join (lane) event, no timing
+    rbf_dev_state* h_many = nullptr; // pinned copies of the device state, one per run
+    int h_many_cap = 0;
 };
 void rbf_batch_state_free(rbf_ctx* ctx);
+// Lane i of ctx (created on first use).  Errors: RBF_ERR_CUDA.
+rbf_status rbf_lane(rbf_ctx* ctx, int i, rbf_ctx** out);
+// Pinned host slots for `count` device-state copies.
+rbf_status rbf_many_slots(rbf_ctx* ctx, int count);
+// Order every lane in [0, lanes) after the work enqueued so far on ctx->stream
+// (fork) and ctx->stream after everything enqueued on those lanes (join); the
+// lanes' kernel-launch counts are added to ctx's.
+rbf_status rbf_lanes_fork(rbf_ctx* ctx, int lanes);
+rbf_status rbf_lanes_join(rbf_ctx* ctx, int lanes);
 
 // ---- error helpers ---------------------------------------------------------
 rbf_status rbf_fail(rbf_ctx* ctx, rbf_status st, const char* fmt, ...);

@@ -344,34 +344,52 @@ size_t select_ws_bytes_batch(const rbf_ctx* ctx, int L, int B) {
 
 namespace {
 
+void info_from_state(const rbf_dev_state* h, int l, rbf_solve_info* info) {
+    info->lambda = h->scal[SC_LAMBDA];
+    info->index = h->info[IN_INDEX];
+    info->rank = h->info[IN_RANK];
+    info->steps = l;
+    info->sigma1 = h->scal[SC_SIGMA1];
+    info->eta = h->scal[SC_ETA];
+    info->rho = h->scal[SC_RHO];
+}
+
 rbf_status read_info(rbf_ctx* ctx, rbf_solve_info* info, int l) {
     RBF_CUDA(ctx, cudaMemcpyAsync(ctx->h_state, ctx->d_state, sizeof(rbf_dev_state),
                                   cudaMemcpyDeviceToHost, ctx->stream));
     RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     RBF_CUDA(ctx, cudaGetLastError());
-    if (info) {
-        info->lambda = ctx->h_state->scal[SC_LAMBDA];
-        info->index = ctx->h_state->info[IN_INDEX];
-        info->rank = ctx->h_state->info[IN_RANK];
-        info->steps = l;
-        info->sigma1 = ctx->h_state->scal[SC_SIGMA1];
-        info->eta = ctx->h_state->scal[SC_ETA];
-        info->rho = ctx->h_state->scal[SC_RHO];
-    }
+    if (info) info_from_state(ctx->h_state, l, info);
     return RBF_OK;
 }
 
-rbf_status single_solve(rbf_ctx* ctx, const rbf_gkb_state* st, int method, int rule, double lambda_in, int rank,
-                        double* d_coef, double* d_curve, rbf_solve_info* info) {
+// Enqueue the projected solve of one state (no synchronisation).
+rbf_status enqueue_solve(rbf_ctx* ctx, const rbf_gkb_state* st, int method, int rule, double lambda_in, int rank,
+                         double* d_coef, double* d_curve) {
     const int l = st->steps_done;
     if (l < 1) return rbf_fail(ctx, RBF_ERR_INVALID, "state has no completed step");
     if (l > 1023) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "projected dimension above 1023");
     RBF_TRY(rbf_ws_reserve(ctx, select_ws_bytes_batch(ctx, l, 1)));
     ProjDims d{1, l, l, nullptr};
     LiftDims ld{nullptr, nullptr, nullptr, st->n, st->ldz, st->n};
-    RBF_TRY(launch_select_batch(ctx, d, method, rule, lambda_in, rank, st->d_alpha, st->d_beta, st->d_Z, ld,
-                                d_coef, d_curve, ctx->ws, nullptr, nullptr, nullptr, true));
-    return read_info(ctx, info, l);
+    return launch_select_batch(ctx, d, method, rule, lambda_in, rank, st->d_alpha, st->d_beta, st->d_Z, ld, d_coef,
+                               d_curve, ctx->ws, nullptr, nullptr, nullptr, true);
+}
+
+rbf_status single_solve(rbf_ctx* ctx, const rbf_gkb_state* st, int method, int rule, double lambda_in, int rank,
+                        double* d_coef, double* d_curve, rbf_solve_info* info) {
+    RBF_TRY(enqueue_solve(ctx, st, method, rule, lambda_in, rank, d_coef, d_curve));
+    return read_info(ctx, info, st->steps_done);
+}
+
+rbf_status check_rule(rbf_ctx* ctx, int rule, double lambda_in) {
+    if (rule != RBF_GCV && rule != RBF_LCURVE && rule != RBF_FIXED && rule != RBF_FIXED_T)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "unknown rule %d", rule);
+    if (rule == RBF_FIXED && !(lambda_in >= 0.0))
+        return rbf_fail(ctx, RBF_ERR_INVALID, "fixed lambda must be >= 0");
+    if (rule == RBF_FIXED_T && !(lambda_in >= -300.0 && lambda_in <= 300.0))
+        return rbf_fail(ctx, RBF_ERR_INVALID, "fixed t must be finite and within [-300, 300]");
+    return RBF_OK;
 }
 
 }  // namespace
@@ -386,13 +404,48 @@ extern "C" rbf_status rbf_hkt(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, d
 
 rbf_status hkt_single(rbf_ctx* ctx, const rbf_gkb_state* st, int rule, double lambda_in, double* d_coef,
                       rbf_solve_info* info, double* d_curve) {
-    if (rule != RBF_GCV && rule != RBF_LCURVE && rule != RBF_FIXED && rule != RBF_FIXED_T)
-        return rbf_fail(ctx, RBF_ERR_INVALID, "unknown rule %d", rule);
-    if (rule == RBF_FIXED && !(lambda_in >= 0.0))
-        return rbf_fail(ctx, RBF_ERR_INVALID, "fixed lambda must be >= 0");
-    if (rule == RBF_FIXED_T && !(lambda_in >= -300.0 && lambda_in <= 300.0))
-        return rbf_fail(ctx, RBF_ERR_INVALID, "fixed t must be finite and within [-300, 300]");
+    RBF_TRY(check_rule(ctx, rule, lambda_in));
     return single_solve(ctx, st, 0, rule, lambda_in, 0, d_coef, d_curve, info);
+}
+
+// HKT for several finished GKB states at once, spread over the context's lanes
+// (each lane solves its share one after another; the projected SVD and the
+// lambda sweep are single-CTA, latency-bound kernels, so independent solves
+// overlap); one synchronisation at the end.
+extern "C" rbf_status rbf_hkt_many(rbf_ctx* ctx, int count, const rbf_gkb_state* states, int rule,
+                                   double lambda_in, double* const* d_coef, rbf_solve_info* infos, int lanes) {
+    RbfRange range_("rbf_hkt_many");
+    if (!ctx) return RBF_ERR_INVALID;
+    if (count < 1 || !states || !d_coef) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_hkt_many: bad arguments");
+    if (lanes < 0 || lanes > rbf_ctx::MAX_LANES)
+        return rbf_fail(ctx, RBF_ERR_INVALID, "lanes must be 0 (default) or 1..%d", rbf_ctx::MAX_LANES);
+    RBF_TRY(check_rule(ctx, rule, lambda_in));
+    for (int i = 0; i < count; ++i)
+        if (!d_coef[i]) return rbf_fail(ctx, RBF_ERR_INVALID, "d_coef[%d] is NULL", i);
+    int L = lanes == 0 ? rbf_ctx::MAX_LANES : lanes;
+    if (L > count) L = count;
+    RBF_TRY(rbf_many_slots(ctx, count));
+    RBF_TRY(rbf_lanes_fork(ctx, L));
+    rbf_status err = RBF_OK;
+    for (int i = 0; i < count && err == RBF_OK; ++i) {
+        rbf_ctx* c = nullptr;
+        err = rbf_lane(ctx, i % L, &c);
+        if (err == RBF_OK) err = enqueue_solve(c, &states[i], 0, rule, lambda_in, 0, d_coef[i], nullptr);
+        if (err == RBF_OK) {
+            cudaError_t e = cudaMemcpyAsync(&ctx->h_many[i], c->d_state, sizeof(rbf_dev_state),
+                                            cudaMemcpyDeviceToHost, c->stream);
+            if (e != cudaSuccess) err = rbf_fail(c, RBF_ERR_CUDA, "state copy failed: %s", cudaGetErrorString(e));
+        }
+        if (err != RBF_OK) rbf_fail(ctx, err, "run %d: %s", i, c ? rbf_last_error(c) : "lane");
+    }
+    rbf_status je = rbf_lanes_join(ctx, L);
+    if (err != RBF_OK) return err;
+    RBF_TRY(je);
+    RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    RBF_CUDA(ctx, cudaGetLastError());
+    if (infos)
+        for (int i = 0; i < count; ++i) info_from_state(&ctx->h_many[i], states[i].steps_done, &infos[i]);
+    return RBF_OK;
 }
 
 extern "C" rbf_status rbf_ine_tsvd(rbf_ctx* ctx, const rbf_gkb_state* st, int rank, double* d_coef,

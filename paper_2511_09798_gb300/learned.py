@@ -95,6 +95,23 @@ class StopNet:
                    **kw)
 
 
+def write_stopnet_file(npz_path: str, out_path: str) -> None:
+    """Write a saved network (StopNet.save's .npz) in the library's binary
+    layout, which rbf_stopnet_load reads from C: magic "RBFSTOP1"; int32 n_in,
+    n_hidden, n_out, n_params, feat_steps; float32 params, feat_mean, feat_std,
+    out_mean[2], out_std[2]; int32 l_min, l_max, window, fallback_rule;
+    float64 accept_tol, t_min, t_max, z_max (little-endian)."""
+    z = np.load(npz_path)
+    rules = [int(x) for x in z["rules"]]
+    with open(out_path, "wb") as fh:
+        fh.write(b"RBFSTOP1")
+        fh.write(np.array([N_IN, N_HID, N_OUT, N_PARAMS, FEAT_STEPS], "<i4").tobytes())
+        for key in ("params", "feat_mean", "feat_std", "out_mean", "out_std"):
+            fh.write(np.asarray(z[key], "<f4").tobytes())
+        fh.write(np.array(rules, "<i4").tobytes())
+        fh.write(np.asarray(z["tols"], "<f8").tobytes())
+
+
 # --------------------------------------------------------------------------
 # training runs and labels
 # --------------------------------------------------------------------------

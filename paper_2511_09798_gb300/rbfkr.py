@@ -62,7 +62,7 @@ class LearnedInfo(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [("launches", C.c_int64), ("product_launches", C.c_int64 * 2),
-                ("product_ms", C.c_double * 2)]
+                ("product_ms", C.c_double * 2), ("product_busy_ms", C.c_double)]
 
 
 class Batch(C.Structure):
@@ -106,6 +106,14 @@ EXPORTS = {
     "rbf_matvec": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_int, C.c_void_p, C.c_void_p]),
     "rbf_gkb": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.c_void_p, C.c_int, C.POINTER(GkbState)]),
     "rbf_gkb_resume": (C.c_int, [C.c_void_p, C.POINTER(Operator), C.POINTER(GkbState), C.c_int]),
+    "rbf_gkb_snapshot": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p]),
+    "rbf_gkb_restore": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_int, C.c_int, C.c_double]),
+    "rbf_gkb_many": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Operator), C.POINTER(C.c_void_p), C.c_int,
+                               C.POINTER(GkbState), C.c_int, C.c_int]),
+    "rbf_hkt_many": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(GkbState), C.c_int, C.c_double,
+                               C.POINTER(C.c_void_p), C.POINTER(SolveInfo), C.c_int]),
     "rbf_projected_svd": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_int64]),
     "rbf_hkt": (C.c_int, [C.c_void_p, C.POINTER(GkbState), C.c_int, C.c_double, C.c_void_p,
@@ -148,10 +156,18 @@ EXPORTS = {
                                         C.c_void_p]),
     "rbf_matvec_t_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                        C.c_void_p]),
+    "rbf_stopnet_init": (C.c_int, [C.c_void_p, C.POINTER(StopNet), C.c_void_p, C.POINTER(C.c_float),
+                                   C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "rbf_stopnet_save": (C.c_int, [C.c_void_p, C.POINTER(StopNet), C.c_char_p]),
+    "rbf_stopnet_load": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(StopNet), C.c_void_p]),
+    "rbf_probe_fp64": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_void_p, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double)]),
 }
 
 RBF_MLP_IN, RBF_MLP_HIDDEN, RBF_MLP_OUT = 20, 128, 2
 RBF_MLP_PARAMS = 20 * 128 + 128 + 128 * 128 + 128 + 128 * 2 + 2
+RBF_STOPNET_DEVICE_FLOATS = RBF_MLP_PARAMS + 2 * RBF_MLP_IN
 
 RBF_NOALLOC_SCRATCH_DOUBLES = 1 << 20
 
@@ -252,7 +268,7 @@ class Context:
         c = Counters()
         self._check(self.lib.rbf_get_counters(self.h, C.byref(c), 1 if reset else 0))
         return {"launches": c.launches, "product_launches": list(c.product_launches),
-                "product_ms": list(c.product_ms)}
+                "product_ms": list(c.product_ms), "product_busy_ms": c.product_busy_ms}
 
     def rbf_operator_init(self, nodes, n, n_interior, c, k, storage=RBF_ASSEMBLED, precision=RBF_FP64,
                           form=RBF_FORM_C, A=None, lda=0):
@@ -275,6 +291,74 @@ class Context:
     def rbf_gkb_resume(self, op, state, more):
         self._check(self.lib.rbf_gkb_resume(self.h, C.byref(op), C.byref(state), more))
         return state.steps_done
+
+    def rbf_gkb_snapshot(self, state):
+        """Host checkpoint (numpy arrays) of a GKB state: W (l+1, n), Z (l, n), alpha, beta and scalars."""
+        import numpy as np
+        n, l = state.n, state.steps_done
+        W = np.empty((l + 1, n))
+        Z = np.empty((max(l, 1), n))
+        al = np.empty(max(l, 1))
+        be = np.empty(l + 1)
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        self._check(self.lib.rbf_gkb_snapshot(self.h, C.byref(state), p(W), p(Z), p(al), p(be)))
+        return {"W": W, "Z": Z[:l], "alpha": al[:l], "beta": be, "steps_done": l, "breakdown": state.breakdown,
+                "c_hat": state.c_hat}
+
+    def rbf_gkb_restore(self, state, snap):
+        import numpy as np
+        arrs = [np.ascontiguousarray(snap[k], np.float64) for k in ("W", "Z", "alpha", "beta")]
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        self._check(self.lib.rbf_gkb_restore(self.h, C.byref(state), *[p(a) for a in arrs], int(snap["steps_done"]),
+                                             int(snap["breakdown"]), float(snap["c_hat"])))
+
+    def rbf_gkb_many(self, ops, fs, steps, states, lanes=0, assemble=False):
+        """Independent GKB runs on the context's lanes; states are updated in place."""
+        cnt = len(ops)
+        if not (len(fs) == len(states) == cnt):
+            raise ValueError("rbf_gkb_many: ops, fs and states must have the same length")
+        op_arr = (Operator * cnt)(*ops)
+        st_arr = (GkbState * cnt)(*states)
+        f_arr = (C.c_void_p * cnt)(*[_ptr(f) for f in fs])
+        st = self.lib.rbf_gkb_many(self.h, cnt, op_arr, f_arr, steps, st_arr, lanes, 1 if assemble else 0)
+        for i in range(cnt):  # the C call wrote its copies: bring the host fields back
+            for name in ("steps_done", "breakdown", "c_hat"):
+                setattr(states[i], name, getattr(st_arr[i], name))
+        self._check(st)
+        return [s_.steps_done for s_ in states]
+
+    def rbf_hkt_many(self, states, rule, lambda_in, coefs, lanes=0):
+        cnt = len(states)
+        st_arr = (GkbState * cnt)(*states)
+        c_arr = (C.c_void_p * cnt)(*[_ptr(c) for c in coefs])
+        infos = (SolveInfo * cnt)()
+        self._check(self.lib.rbf_hkt_many(self.h, cnt, st_arr, rule, float(lambda_in), c_arr, infos, lanes))
+        return list(infos)
+
+    def rbf_stopnet_load(self, path, storage):
+        """A stop network read by the library from a file written by rbf_stopnet_save;
+        storage: float32 CUDA tensor of RBF_STOPNET_DEVICE_FLOATS (keep it alive)."""
+        net = StopNet()
+        self._check(self.lib.rbf_stopnet_load(self.h, os.fsencode(path), C.byref(net), _ptr(storage)))
+        return net
+
+    def rbf_stopnet_save(self, net, path):
+        self._check(self.lib.rbf_stopnet_save(self.h, C.byref(net), os.fsencode(path)))
+
+    def rbf_stopnet_init(self, storage, params, feat_mean, feat_std, out, rules, tols):
+        import numpy as np
+        net = StopNet()
+        fp = lambda a: None if a is None else np.ascontiguousarray(a, np.float32).ctypes.data_as(C.POINTER(C.c_float))
+        keep = [np.ascontiguousarray(a, np.float32) if a is not None else None for a in (params, feat_mean, feat_std, out)]
+        r = (C.c_int * 4)(*[int(x) for x in rules])
+        t = (C.c_double * 4)(*[float(x) for x in tols])
+        self._check(self.lib.rbf_stopnet_init(self.h, C.byref(net), _ptr(storage), *[fp(a) for a in keep], r, t))
+        return net
+
+    def rbf_probe_fp64(self, mode, iters, scratch):
+        ms, flops = C.c_double(), C.c_double()
+        self._check(self.lib.rbf_probe_fp64(self.h, mode, int(iters), _ptr(scratch), C.byref(ms), C.byref(flops)))
+        return ms.value, flops.value
 
     def rbf_projected_svd(self, state, sigma, ftil, V, ldv):
         self._check(self.lib.rbf_projected_svd(self.h, C.byref(state), _ptr(sigma), _ptr(ftil),

@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import math
 import sys
 import time
@@ -171,6 +172,8 @@ def main(argv=None):
     print(json.dumps(summ, indent=1))
     if a.out:
         net.save(a.out)
+        # the same network in the layout the library reads from C (rbf_stopnet_load)
+        learned.write_stopnet_file(a.out, os.path.splitext(a.out)[0] + ".bin")
     if a.summary:
         with open(a.summary, "w") as fh:
             json.dump({"summary": summ, "rows": rows}, fh, indent=1)

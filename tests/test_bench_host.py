@@ -1,10 +1,14 @@
 """Host-side parts of the benchmark that run without a GPU: the record of the
 host the CPU baseline ran on, and the oracle baseline scaled from a row-block
 sample (used where the FP64 matrix is too large for the host oracle)."""
+import os
+
 import numpy as np
 
 import bench
 import workloads as w
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_host_info_fields():
@@ -29,3 +33,28 @@ def test_mf_ops_per_entry_mix():
     assert bench.mf_ops_per_entry(10, 10) == 11
     assert bench.mf_ops_per_entry(10, 0) == 8
     assert bench.mf_ops_per_entry(4, 1) == (11 + 3 * 8) / 4
+
+
+def test_shipped_stopnet_file_matches_the_npz(tmp_path):
+    """The binary stop-network file read by rbf_stopnet_load holds exactly the
+    arrays of the shipped .npz, in the documented layout."""
+    import numpy as np
+
+    from paper_2511_09798_gb300 import learned
+    pkg = os.path.join(ROOT, "paper_2511_09798_gb300")
+    out = str(tmp_path / "w.bin")
+    learned.write_stopnet_file(os.path.join(pkg, "stopnet_weights.npz"), out)
+    raw = open(out, "rb").read()
+    assert raw == open(os.path.join(pkg, "stopnet_weights.bin"), "rb").read()
+    assert raw[:8] == b"RBFSTOP1"
+    dims = np.frombuffer(raw[8:28], "<i4")
+    assert list(dims) == [20, 128, 2, learned.N_PARAMS, 10]
+    z = np.load(os.path.join(pkg, "stopnet_weights.npz"))
+    off = 28
+    for key, cnt in (("params", learned.N_PARAMS), ("feat_mean", 20), ("feat_std", 20), ("out_mean", 2),
+                     ("out_std", 2)):
+        assert np.array_equal(np.frombuffer(raw[off:off + 4 * cnt], "<f4"), z[key])
+        off += 4 * cnt
+    assert list(np.frombuffer(raw[off:off + 16], "<i4")) == [int(x) for x in z["rules"]]
+    assert np.array_equal(np.frombuffer(raw[off + 16:off + 48], "<f8"), z["tols"])
+    assert len(raw) == off + 48
