@@ -597,6 +597,53 @@ def run_batch(args, rank, world, local_rank):
                 "algorithmic_per_launch": f"{sum(s_.n * s_.n for s_ in inst)} entries, "
                                           f"{ops // 2} FP32-pipe ops (11 per PDE entry, 8 per Dirichlet entry)",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts and max clock)"}
+    # per-kernel times of one batch, launched directly with CUDA events around
+    # every launch (a context with launch timing does not replay the graph):
+    # the half-step kernel's roofline, and how much of the graph-replayed batch
+    # is not kernel time (what a single persistent kernel could at most save)
+    kern = None
+    if not learned_arm:
+        ctx_t = R.Context(local_rank, stream=torch.cuda.current_stream(), timing=2)
+        ctx_t.rbf_batch_gkb(bt, L)  # tunes on this context (untimed)
+        ctx_t.rbf_get_counters(reset=True)
+        torch.cuda.synchronize()
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record()
+        ctx_t.rbf_batch_gkb(bt, L)
+        k1.record()
+        torch.cuda.synchronize()
+        ct = ctx_t.rbf_get_counters(reset=True)
+        ctx_t.close()
+        ms_direct = k0.elapsed_time(k1)
+        nh = max(1, ct["reorth_launches"])
+        half_ms = ct["reorth_ms"] / nh
+        prod_ms = sum(ct["product_ms"])
+        done_b = [bt.steps_done[b] for b in range(len(inst))]
+        # algorithmic bytes of one batched half-step, averaged over the run: one
+        # read of every active instance's basis (sum over the run of 8 n_b
+        # (j - 1) + 8 n_b j = 8 n_b l_b^2) plus the vectors each half-step must
+        # read and write (product partials, q, the new vector: ~5 x 8 n_b)
+        basis = sum(8 * s_.n * l_b * l_b for s_, l_b in zip(inst, done_b))
+        vec = sum(2 * l_b * 5 * 8 * s_.n for s_, l_b in zip(inst, done_b))
+        alg = (basis + vec) / (2 * L)
+        peak_hbm = measured_peaks().get("hbm_gbs", 6801.7)
+        gbs = alg / (half_ms / 1e3) / 1e9
+        kern = {"half_step_roofline": {
+                    "kernel": "k_half_batch", "bound": "hbm", "achieved": round(gbs, 1), "peak": peak_hbm,
+                    "unit": "GB/s", "frac": round(gbs / peak_hbm, 4), "traffic": None,
+                    "avg_launch_ms": round(half_ms, 5), "launches_timed": int(ct["reorth_launches"]),
+                    "algorithmic_per_launch": f"{alg:.4g} bytes (one read of each active basis + vectors, "
+                                              f"averaged over the {2 * L} half-steps)",
+                    "design_traffic_per_launch": f"{(4 * basis + vec) / (2 * L):.4g} bytes (the kernel reads "
+                                                 f"each basis 4 times: 2 dot passes, 2 update passes)",
+                    "design_traffic_gbs": round((4 * basis + vec) / (2 * L) / (half_ms / 1e3) / 1e9, 1),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+                "batch_ms_graph": round(ms / args.steps, 2),
+                "batch_gkb_ms_direct_timed": round(ms_direct, 2),
+                "kernel_ms_sum": round(prod_ms + ct["reorth_ms"], 2),
+                "products_ms": round(prod_ms, 2), "half_steps_ms": round(ct["reorth_ms"], 2),
+                "timing": "a context with launch timing: the step loop launched directly, CUDA events around "
+                          "each launch on the batch stream"}
     other = None
     if learned_arm:  # the same instances by the other forms, once each, for comparison
         torch.cuda.synchronize()
@@ -665,7 +712,7 @@ def run_batch(args, rank, world, local_rank):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": round(ms_e2e / args.steps, 2)},
             "gpu_launches": int(cnt["launches"]),
-            "tuning": tune, "clocks": clocks,
+            "tuning": tune, "clocks": clocks, "kernel_times": kern,
             "cpu_baseline": None if args.no_cpu_baseline else cpu_baseline_batch(inst, fs, pts, L)}
 
 

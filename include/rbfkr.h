@@ -157,9 +157,12 @@ typedef struct {
 } rbf_timings;
 
 /* Counters since creation or the last reset: kernel launches made by the
- * library, and (when bit 1 of opt.timing is set) the device time of the GKB matrix-vector
- * product launches, measured with CUDA events recorded on the context stream
- * around each product (index 0: p = A z, index 1: r = A^T w). */
+ * library, and (when bit 1 of opt.timing is set) the device time of the GKB
+ * matrix-vector product launches (index 0: p = A z, index 1: r = A^T w) and of
+ * the half-step (reorthogonalization) kernels, measured with CUDA events
+ * recorded around each launch on the stream it is launched on.  With this bit
+ * set the batched GKB launches its step loop directly instead of replaying a
+ * captured graph, so that every launch can be timed. */
 typedef struct {
     int64_t launches;           /* every kernel launch issued by the library */
     int64_t product_launches[2];/* timed product launches (A, A^T) */
@@ -168,6 +171,8 @@ typedef struct {
                                    during which at least one product ran (equal to the sum
                                    when products never overlap; smaller when products of
                                    concurrent runs, rbf_gkb_many, overlap) */
+    int64_t reorth_launches;    /* timed half-step (reorthogonalization) kernel launches */
+    double reorth_ms;           /* their summed device time, milliseconds */
 } rbf_counters;
 
 /* ---- context --------------------------------------------------------- */

@@ -900,6 +900,9 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     put(a.bar_group); put(a.budget); put(a.rmax);
     put(bt->d_nodes); put(bt->d_f); put(w.items); put(w.part); put(w.vr); put(w.vp); put(w.vr32); put(w.vp32);
     put(nit); put(cand); put(P.G); put(hsmem); put(steps); put(form); put(s);
+    // per-launch timing (opt.timing bit 1): the loop is launched directly, each
+    // launch between CUDA events on the batch stream
+    const bool timed = (ctx->opt.timing & 2) != 0;
     auto record_steps = [&](int* kernels) -> cudaError_t {
         int cnt = 0;
         for (int j = 1; j <= steps; ++j) {
@@ -909,10 +912,12 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
                 int* dout = w.binfo + (half & 1 ? BI_DONE0 : BI_DONE1) * P.B;
                 const int trans = side == 0 ? 1 : 0;
                 const float* x32 = side == 0 ? w.vp32 : w.vr32;
+                const int pslot = timed ? rbf_prod_begin(ctx, trans, s) : -1;
                 if (trans)
                     launch_mf_cand<1>(cand, nit, s, w.items, w.inst, bt->d_nodes, x32, w.part, din);
                 else
                     launch_mf_cand<0>(cand, nit, s, w.items, w.inst, bt->d_nodes, x32, w.part, din);
+                rbf_prod_end(ctx, trans, pslot, s);
                 cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) return e;
                 HalfBArgs h = a;
@@ -924,7 +929,9 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
                 h.done_in = din;
                 h.done_out = dout;
                 void* args[] = {&h};
+                const int rslot = timed ? rbf_prod_begin(ctx, 2, s) : -1;
                 e = cudaLaunchCooperativeKernel((const void*)k_half_batch, dim3(P.G), dim3(HB_THREADS), args, hsmem, s);
+                rbf_prod_end(ctx, 2, rslot, s);
                 if (e != cudaSuccess) return e;
                 cnt += 2;
             }
@@ -936,7 +943,9 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     int slot = -1;
     for (int i = 0; i < GRAPH_SLOTS; ++i)
         if (ts.exec[i] && ts.graph_key[i] == key) slot = i;
-    if (slot >= 0) {
+    if (timed) {
+        ts.graph_kernels = 0;  // launched directly below
+    } else if (slot >= 0) {
         ts.last_use[slot] = ++ts.clock;
         ts.graph_kernels = ts.slot_kernels[slot];
         RBF_CUDA(ctx, cudaGraphLaunch(ts.exec[slot], s));

@@ -43,23 +43,24 @@ rbf_status rbf_ws_reserve(rbf_ctx* ctx, size_t bytes) {
 // Product-launch timing: a lane records on its own stream into its owner's
 // event slots (the owner's base event precedes every lane's work, see
 // rbf_lanes_fork), so that busy intervals of all lanes share one time origin.
-int rbf_prod_begin(rbf_ctx* ctx, int trans) {
+int rbf_prod_begin(rbf_ctx* ctx, int kind, cudaStream_t s) {
     rbf_ctx* o = ctx->owner ? ctx->owner : ctx;
-    o->ptotal[trans]++;
-    if (!(o->opt.timing & 2) || !o->pev || o->pcount[trans] >= rbf_ctx::PMAX) return -1;
+    if (!s) s = ctx->stream;
+    o->ptotal[kind]++;
+    if (!(o->opt.timing & 2) || !o->pev || o->pcount[kind] >= rbf_ctx::PMAX) return -1;
     if (!o->pbase_set) {
-        cudaEventRecord(o->pbase, ctx->stream);
+        cudaEventRecord(o->pbase, s);
         o->pbase_set = true;
     }
-    const int slot = o->pcount[trans]++;
-    cudaEventRecord(o->pev[((size_t)trans * rbf_ctx::PMAX + slot) * 2], ctx->stream);
+    const int slot = o->pcount[kind]++;
+    cudaEventRecord(o->pev[((size_t)kind * rbf_ctx::PMAX + slot) * 2], s);
     return slot;
 }
 
-void rbf_prod_end(rbf_ctx* ctx, int trans, int slot) {
+void rbf_prod_end(rbf_ctx* ctx, int kind, int slot, cudaStream_t s) {
     if (slot < 0) return;
     rbf_ctx* o = ctx->owner ? ctx->owner : ctx;
-    cudaEventRecord(o->pev[((size_t)trans * rbf_ctx::PMAX + slot) * 2 + 1], ctx->stream);
+    cudaEventRecord(o->pev[((size_t)kind * rbf_ctx::PMAX + slot) * 2 + 1], s ? s : ctx->stream);
 }
 
 rbf_status rbf_lane(rbf_ctx* ctx, int i, rbf_ctx** out) {
@@ -168,7 +169,7 @@ rbf_status rbf_create(rbf_ctx** out, int device, void* cuda_stream, const rbf_op
     if (e == cudaSuccess) e = cudaEventCreate(&ctx->pbase);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->sync_ev, cudaEventDisableTiming);
     if (e == cudaSuccess && (ctx->opt.timing & 2)) {
-        const size_t ne = (size_t)2 * rbf_ctx::PMAX * 2;
+        const size_t ne = (size_t)rbf_ctx::PKINDS * rbf_ctx::PMAX * 2;
         ctx->pev = new cudaEvent_t[ne]();
         for (size_t i = 0; i < ne && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->pev[i]);
     }
@@ -189,10 +190,25 @@ rbf_status rbf_get_counters(rbf_ctx* ctx, rbf_counters* out, int reset) {
         out->product_ms[t] = 0.0;
     }
     out->product_busy_ms = 0.0;
+    out->reorth_launches = ctx->pcount[2];
+    out->reorth_ms = 0.0;
+    if (ctx->pev && ctx->pcount[2]) {
+        RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int i = 0; i < rbf_ctx::MAX_LANES; ++i)
+            if (ctx->lane[i]) RBF_CUDA(ctx, cudaStreamSynchronize(ctx->lane[i]->stream));
+        if (ctx->batch_state) RBF_CUDA(ctx, cudaDeviceSynchronize());  // the batched driver's own stream
+        for (int i = 0; i < ctx->pcount[2]; ++i) {
+            float ms = 0.f;
+            const size_t b = ((size_t)2 * rbf_ctx::PMAX + i) * 2;
+            RBF_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->pev[b], ctx->pev[b + 1]));
+            out->reorth_ms += ms;
+        }
+    }
     if (ctx->pev && (ctx->pcount[0] || ctx->pcount[1])) {
         RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         for (int i = 0; i < rbf_ctx::MAX_LANES; ++i)
             if (ctx->lane[i]) RBF_CUDA(ctx, cudaStreamSynchronize(ctx->lane[i]->stream));
+        if (ctx->batch_state) RBF_CUDA(ctx, cudaDeviceSynchronize());
         std::vector<std::pair<double, double>> iv;
         iv.reserve((size_t)ctx->pcount[0] + ctx->pcount[1]);
         for (int t = 0; t < 2; ++t)
@@ -221,8 +237,7 @@ rbf_status rbf_get_counters(rbf_ctx* ctx, rbf_counters* out, int reset) {
     }
     if (reset) {
         ctx->launches = 0;
-        ctx->pcount[0] = ctx->pcount[1] = 0;
-        ctx->ptotal[0] = ctx->ptotal[1] = 0;
+        for (int t = 0; t < rbf_ctx::PKINDS; ++t) ctx->pcount[t] = 0, ctx->ptotal[t] = 0;
         ctx->pbase_set = false;
     }
     return RBF_OK;
@@ -246,7 +261,7 @@ rbf_status rbf_destroy(rbf_ctx* ctx) {
     if (ctx->h_many) cudaFreeHost(ctx->h_many);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     if (ctx->pev) {
-        for (size_t i = 0; i < (size_t)2 * rbf_ctx::PMAX * 2; ++i)
+        for (size_t i = 0; i < (size_t)rbf_ctx::PKINDS * rbf_ctx::PMAX * 2; ++i)
             if (ctx->pev[i]) cudaEventDestroy(ctx->pev[i]);
         delete[] ctx->pev;
     }

@@ -606,8 +606,10 @@ struct GkbRun {
         void* args[] = {&a};
         const bool stage = half_smem_bytes(true, mcount, chunks, rmax) <= half_stage_limit(ctx);
         const size_t smem = half_smem_bytes(stage, mcount, chunks, rmax);
+        const int slot = rbf_prod_begin(ctx, 2);
         cudaError_t e = cudaLaunchCooperativeKernel(stage ? (const void*)k_half<true> : (const void*)k_half<false>,
                                                     dim3(G), dim3(SL_THREADS), args, smem, ctx->stream);
+        rbf_prod_end(ctx, 2, slot);
         ctx->launches++;
         if (e != cudaSuccess)
             return rbf_fail(ctx, RBF_ERR_CUDA, "cooperative launch of k_half failed: %s", cudaGetErrorString(e));

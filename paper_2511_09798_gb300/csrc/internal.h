@@ -57,9 +57,10 @@ struct rbf_ctx {
     // counters
     int64_t launches = 0;
     static constexpr int PMAX = 8192;
-    cudaEvent_t* pev = nullptr;   // [2][PMAX][2] product start/stop events
-    int pcount[2] = {0, 0};       // recorded pairs per product kind
-    int64_t ptotal[2] = {0, 0};   // launches per product kind
+    static constexpr int PKINDS = 3;  // 0: A x, 1: A^T x, 2: reorthogonalization (half-step) kernels
+    cudaEvent_t* pev = nullptr;   // [PKINDS][PMAX][2] start/stop events
+    int pcount[PKINDS] = {0, 0, 0};     // recorded pairs per kind
+    int64_t ptotal[PKINDS] = {0, 0, 0}; // launches per kind
     void* batch_state = nullptr;  // batched GKB: tuning choice, captured graph, stream
     cudaEvent_t pbase = nullptr;  // origin of the product-launch intervals since the last reset
     bool pbase_set = false;
@@ -132,9 +133,10 @@ struct WsCarve {
 inline size_t ws_align(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // ---- timing ------------------------------------------------------------------
-// Product-launch timing (opt.timing >= 2): returns the slot or -1.
-int rbf_prod_begin(rbf_ctx* ctx, int trans);
-void rbf_prod_end(rbf_ctx* ctx, int trans, int slot);
+// Launch timing (opt.timing bit 1) of kind 0 (A x), 1 (A^T x) or 2 (half-step
+// kernels), recorded on `s` (default: the context stream): returns the slot or -1.
+int rbf_prod_begin(rbf_ctx* ctx, int kind, cudaStream_t s = nullptr);
+void rbf_prod_end(rbf_ctx* ctx, int kind, int slot, cudaStream_t s = nullptr);
 void rbf_timer_start(rbf_ctx* ctx);
 double rbf_timer_stop(rbf_ctx* ctx);  // ms, synchronises when timing is on
 

@@ -62,7 +62,8 @@ class LearnedInfo(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [("launches", C.c_int64), ("product_launches", C.c_int64 * 2),
-                ("product_ms", C.c_double * 2), ("product_busy_ms", C.c_double)]
+                ("product_ms", C.c_double * 2), ("product_busy_ms", C.c_double),
+                ("reorth_launches", C.c_int64), ("reorth_ms", C.c_double)]
 
 
 class Batch(C.Structure):
@@ -268,7 +269,8 @@ class Context:
         c = Counters()
         self._check(self.lib.rbf_get_counters(self.h, C.byref(c), 1 if reset else 0))
         return {"launches": c.launches, "product_launches": list(c.product_launches),
-                "product_ms": list(c.product_ms), "product_busy_ms": c.product_busy_ms}
+                "product_ms": list(c.product_ms), "product_busy_ms": c.product_busy_ms,
+                "reorth_launches": c.reorth_launches, "reorth_ms": c.reorth_ms}
 
     def rbf_operator_init(self, nodes, n, n_interior, c, k, storage=RBF_ASSEMBLED, precision=RBF_FP64,
                           form=RBF_FORM_C, A=None, lda=0):
