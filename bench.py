@@ -23,7 +23,9 @@ roofline: the dominant kernel is the matrix-vector product of the GKB; its
 re_exact: Re = max |u - u_exact| / max |u_exact| of every solve at the test
         points; gaussian_variant: the same solve for the cube example's
         Gaussian exact solution (a field HKT resolves), timed one solve after
-        another.
+        another; forms_comparison: 24 uneven instances with Gaussian exact
+        solutions solved by every form (FP64, mixed, batched, learned stop):
+        time to solution and error against the exact solution.
 
 ``--impl reference`` times the FP64 CPU oracle (test infrastructure) on the
 host cores, one full solve of the same workload per step.
@@ -337,6 +339,9 @@ def run_ours(args, rank, world, local_rank):
     ms_e2e, done_e2e = timed(args.steps, True)
     gauss = gaussian_variant(R, ctx, wl, nodes_d, pts_d, stream, dev) if wl["name"] == "cube8000" else None
     ctx.rbf_get_counters(reset=True)
+    # the forms of the method on uneven instances whose field HKT resolves:
+    # time to solution and error against the exact solution (after the timed region)
+    forms = forms_comparison(local_rank) if wl["name"] == "cube8000" and not args.no_forms else None
     # phase shares (separate context with synchronising per-phase timers)
     ctx_ph = R.Context(local_rank, stream=stream, timing=1)
     phases = {}
@@ -421,6 +426,7 @@ def run_ours(args, rank, world, local_rank):
                      "exact": wl["exact_name"], "test_points": m},
         "lambda_over_s1_log10": [round(x, 3) for x in t_chosen],
         "gaussian_variant": gauss,
+        "forms_comparison": forms,
         "gkb_steps_done": done, "solves": solves,
         "roofline": roof,
         "e2e": {"value": round(done_e2e / (ms_e2e / 1e3), 2), "unit": "GKB steps/s",
@@ -603,6 +609,13 @@ def run_batch(args, rank, world, local_rank):
     # is not kernel time (what a single persistent kernel could at most save)
     kern = None
     if not learned_arm:
+        torch.cuda.synchronize()  # the GKB alone as the graph replays it
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record()
+        ctx.rbf_batch_gkb(bt, L)
+        q1.record()
+        torch.cuda.synchronize()
+        ms_graph_gkb = q0.elapsed_time(q1)
         ctx_t = R.Context(local_rank, stream=torch.cuda.current_stream(), timing=2)
         ctx_t.rbf_batch_gkb(bt, L)  # tunes on this context (untimed)
         ctx_t.rbf_get_counters(reset=True)
@@ -638,7 +651,8 @@ def run_batch(args, rank, world, local_rank):
                                                  f"each basis 4 times: 2 dot passes, 2 update passes)",
                     "design_traffic_gbs": round((4 * basis + vec) / (2 * L) / (half_ms / 1e3) / 1e9, 1),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
-                "batch_ms_graph": round(ms / args.steps, 2),
+                "batch_ms_graph_with_solve_and_u": round(ms / args.steps, 2),
+                "batch_gkb_ms_graph": round(ms_graph_gkb, 2),
                 "batch_gkb_ms_direct_timed": round(ms_direct, 2),
                 "kernel_ms_sum": round(prod_ms + ct["reorth_ms"], 2),
                 "products_ms": round(prod_ms, 2), "half_steps_ms": round(ct["reorth_ms"], 2),
@@ -947,6 +961,132 @@ def run_paper_sweep(args, rank, world, local_rank):
             "rows": rows}
 
 
+# --------------------------------------------------------------------------- forms at equal error
+def forms_comparison(local_rank, count=24, L=150, m=500, reps=1):
+    """Time to solution and error against the exact solution of the same
+    uneven instances by each form of the method: plain FP64 HKT (assembled,
+    one instance after another, and all instances on concurrent lanes), mixed
+    precision (FP32 matrix-free products, FP64 elsewhere), the batched mixed
+    form, and the batched mixed form with the learned stop (GCV fallback).
+
+    Instances: the held-out draws of the learned stop's generator (cube or
+    sphere, N ~ U{2000..16000}, c log-uniform in [0.05, 1], k ~ U[1, 20]) with
+    the paper's Gaussian exact solution exp(-|X - X0|^2 / sigma) (sigma
+    log-uniform in [0.05, 10]): fields HKT resolves, so equal error is a real
+    test (plane waves at k up to 20 are not resolved by 150 GKB steps).  All
+    GKB runs take L steps (the learned stop fewer); rule GCV; u at m test
+    points per instance; device time by CUDA events around each form."""
+    import numpy as np
+    import torch
+
+    import workloads as w
+    from paper_2511_09798_gb300 import learned
+    from paper_2511_09798_gb300 import rbfkr as R
+    dev = f"cuda:{local_rank}"
+    inst = w.stop_instances(count, 2000, 16000, seed0=w.nodes.BASE_SEED + 50000, gauss_share=1.0)
+    fs = [w.instance_rhs(s_) for s_ in inst]
+    pts = [w.test_points(s_, m, seed=s_.params["seed"] + 7) for s_ in inst]
+    ue = [w.instance_field(s_, P) for s_, P in zip(inst, pts)]
+    stream = torch.cuda.current_stream()
+    ctx = R.Context(local_rank, stream=stream)
+    nodes = [torch.as_tensor(s_.soa(), device=dev) for s_ in inst]
+    f_d = [torch.as_tensor(f, device=dev) for f in fs]
+    P_d = [torch.as_tensor(np.ascontiguousarray(P.T), device=dev) for P in pts]
+    u_d = [torch.empty(m, dtype=torch.float64, device=dev) for _ in inst]
+    coefs = [torch.empty(s_.n, dtype=torch.float64, device=dev) for s_ in inst]
+
+    def errs():
+        return [float(np.max(np.abs(u.cpu().numpy() - e)) / np.max(np.abs(e))) for u, e in zip(u_d, ue)]
+
+    def timed(fn):
+        fn()  # warm-up (workspace, tuning, graph capture)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, errs()
+
+    out = {}
+    # plain FP64, assembled, one instance after another
+    mats = [torch.empty((s_.n, R.padded_lda(s_.n, R.RBF_FP64)), dtype=torch.float64, device=dev) for s_ in inst]
+    ops64 = [ctx.rbf_operator_init(nd, s_.n, s_.n_interior, s_.params["c"], s_.params["k"], R.RBF_ASSEMBLED,
+                                   R.RBF_FP64, R.RBF_FORM_C, A, A.shape[1]) for nd, s_, A in zip(nodes, inst, mats)]
+    sts = [R.make_state(torch, s_.n, L, dev)[0] for s_ in inst]
+
+    def fp64_serial():
+        for b in range(count):
+            ctx.rbf_assemble(ops64[b])
+            ctx.rbf_gkb(ops64[b], f_d[b], L, sts[b])
+            ctx.rbf_hkt(sts[b], R.RBF_GCV, 0.0, coefs[b])
+            ctx.rbf_evaluate(ops64[b], coefs[b], P_d[b], m, u_d[b])
+
+    def fp64_lanes():
+        ctx.rbf_gkb_many(ops64, f_d, L, sts, assemble=True)
+        ctx.rbf_hkt_many(sts, R.RBF_GCV, 0.0, coefs)
+        for b in range(count):
+            ctx.rbf_evaluate(ops64[b], coefs[b], P_d[b], m, u_d[b])
+
+    out["fp64_single"] = timed(fp64_serial)
+    out["fp64_lanes"] = timed(fp64_lanes)
+    del mats, ops64
+    torch.cuda.empty_cache()
+    opsm = [ctx.rbf_operator_init(nd, s_.n, s_.n_interior, s_.params["c"], s_.params["k"], R.RBF_MATRIX_FREE,
+                                  R.RBF_MIXED) for nd, s_ in zip(nodes, inst)]
+
+    def mixed_serial():
+        for b in range(count):
+            ctx.rbf_gkb(opsm[b], f_d[b], L, sts[b])
+            ctx.rbf_hkt(sts[b], R.RBF_GCV, 0.0, coefs[b])
+            ctx.rbf_evaluate(opsm[b], coefs[b], P_d[b], m, u_d[b])
+
+    out["mixed_single"] = timed(mixed_serial)
+    bt, keep = R.make_batch(torch, inst, [s_.params["c"] for s_ in inst], [s_.params["k"] for s_ in inst], fs, L, dev)
+    T = int(keep["offsets"][-1])
+    coef_b = torch.empty(T, dtype=torch.float64, device=dev)
+    P_all = torch.as_tensor(np.concatenate([P.T.ravel() for P in pts]), device=dev)
+    u_all = torch.empty(m * count, dtype=torch.float64, device=dev)
+
+    def scatter():
+        for b in range(count):
+            u_d[b].copy_(u_all[b * m:(b + 1) * m])
+
+    def mixed_batched():
+        ctx.rbf_batch_gkb(bt, L)
+        ctx.rbf_batch_hkt(bt, R.RBF_GCV, coef_b)
+        ctx.rbf_batch_evaluate(bt, coef_b, P_all, [m] * count, u_all)
+        scatter()
+
+    out["mixed_batched"] = timed(mixed_batched)
+    net = learned.StopNet.load(torch, os.path.join(ROOT, "paper_2511_09798_gb300", "stopnet_weights.npz"), device=dev)
+    snet = net.c_struct()
+    steps_learned = []
+
+    def mixed_batched_learned():
+        ctx.rbf_batch_learned_hkt(bt, snet, coef_b)
+        ctx.rbf_batch_evaluate(bt, coef_b, P_all, [m] * count, u_all)
+        scatter()
+        steps_learned[:] = [bt.steps_done[b] for b in range(count)]
+
+    out["mixed_batched_learned"] = timed(mixed_batched_learned)
+    ctx.close()
+    ref = np.array(out["fp64_single"][1])
+    res = {}
+    for name, (ms, e) in out.items():
+        e = np.array(e)
+        res[name] = {"ms": round(ms, 2), "ms_per_instance": round(ms / count, 3),
+                     "re_median": float(np.median(e)), "re_q90": float(np.quantile(e, 0.9)),
+                     "re_max": float(np.max(e)),
+                     "err_not_worse_than_fp64_frac": float(np.mean(e <= 1.05 * ref)),
+                     "speedup_vs_fp64_single": round(out["fp64_single"][0] / ms, 2)}
+    res["mixed_batched_learned"]["mean_gkb_steps"] = float(np.mean(steps_learned))
+    return {"instances": count, "gkb_steps": L, "exact": "Gaussian exp(-|X - X0|^2 / sigma)", "rule": "gcv",
+            "test_points_per_instance": m, "n_range": [min(s_.n for s_ in inst), max(s_.n for s_ in inst)],
+            "forms": res}
+
+
 # --------------------------------------------------------------------------- FP64 pipe probe
 def run_fp64_probe(args, rank, world, local_rank):
     """Measured FP64 throughput of this GPU (the peak the FP64 products are
@@ -1198,6 +1338,7 @@ def main():
     ap.add_argument("--lanes", type=int, default=0,
                     help="streams for the independent (c, k) solves of a step (0 = one per solve, 1 = serial)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the forms comparison of the default workload")
     ap.add_argument("--jsonl", default=None, help="also append the result line to this JSONL file")
     ap.add_argument("--single-solve", action="store_true",
                     help="run one untimed solve of the first case and exit (profiling target)")
@@ -1222,6 +1363,18 @@ def main():
         out = run_paper_sweep(args, rank, world, local_rank)
     elif args.workload == "fp64-pipe-probe":
         out = run_fp64_probe(args, rank, world, local_rank)
+    elif args.workload == "forms-gauss":
+        import torch
+        torch.cuda.set_device(local_rank)
+        t0 = time.perf_counter()
+        fc = forms_comparison(local_rank)
+        out = None if rank != 0 else {
+            "metric": "time to HKT solution of 24 uneven Gaussian instances, per form", "value":
+                fc["forms"]["mixed_batched_learned"]["speedup_vs_fp64_single"], "unit": "x plain FP64 HKT",
+            "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": fc["forms"]["mixed_batched_learned"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic", "config": {"workload": "forms-gauss"}, "comparison": fc,
+            "wall_s": round(time.perf_counter() - t0, 1)}
     else:
         out = run_ours(args, rank, world, local_rank)
         if out is not None and not args.no_cpu_baseline:

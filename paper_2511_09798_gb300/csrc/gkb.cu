@@ -458,12 +458,10 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
     fake.storage = RBF_MATRIX_FREE;
     int ch = mf_chunks(ctx, &fake);
     fake.storage = RBF_ASSEMBLED;
-    int ch2 = gemv_t_chunks(ctx, &fake);
-    fake.precision = RBF_FP64;
-    int ch3 = gemv_t_chunks(ctx, &fake);
-    if (ch2 > ch) ch = ch2;
-    if (ch3 > ch) ch = ch3;
-    if (ch < 8) ch = 8;  // partial-sum rows of the FP64 A x (at most 8)
+    for (int prec : {RBF_MIXED, RBF_FP64}) {  // the assembled products' partial-sum rows
+        fake.precision = prec;
+        ch = std::max(ch, std::max(gemv_t_chunks(ctx, &fake), gemv_n_chunks(ctx, &fake)));
+    }
     const int G = slab_grid(ctx, n);
     size_t b = 0;
     b += ws_align((size_t)ch * n * 8);                // partials

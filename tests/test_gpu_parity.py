@@ -93,9 +93,10 @@ def _products(ctx, R, op, n, seed):
     return x, y0.cpu().numpy(), y1.cpu().numpy()
 
 
-# n = 1, 2, 5: one warp takes the whole matrix; n = 1116: rows split into up to
-# 6 warp pieces (the most for this grid); 4099: ragged against every tile size
-@pytest.mark.parametrize("n", [1, 2, 5, 64, 257, 1003, 1116, 4099])
+# n = 1, 2, 5: one warp takes the whole matrix; 31, 33, 95, 129: ragged 32-row
+# groups and 32 / 64-column tiles; 1116, 2049: row groups and column tiles
+# shared by several warps (many partial slots); 4099: ragged against every tile
+@pytest.mark.parametrize("n", [1, 2, 5, 31, 33, 64, 95, 129, 257, 1003, 1116, 2049, 4099])
 def test_matvec_fp64(ctx, R, n):
     ns = random_nodes(n, (2 * n) // 3, n + 1)
     op, _, _ = gpu_matrix(ctx, R, ns, 0.2, 4.0)
@@ -187,6 +188,7 @@ def test_gkb_fp64_parity(ctx, R, n, ni, steps):
     st, W, Z, al, be = run_gkb(ctx, R, op, f, steps, n)
     assert st.steps_done == g.steps_done and st.breakdown == g.breakdown
     m = max(1, ls)
+    print(f"GKB scalars compared to rel 1e-10 for j <= l_stable = {ls} of {g.steps_done} steps (n = {n})")
     assert np.max(np.abs(al[:m] - g.alpha[:m]) / g.alpha[:m]) < 1e-10
     assert np.max(np.abs(be[:m + 1] - g.beta[:m + 1]) / g.beta[:m + 1]) < 1e-10
     # Algorithm 1 relations hold for the GPU's own bases
@@ -470,6 +472,7 @@ def test_cube8000_fp64_parity(ctx, R):
     al = np.empty(0)
     st2, W, Z, al, be = run_gkb(ctx, R, op, f, steps, ns.n)
     m = max(1, ls)
+    print(f"cube8000: GKB scalars compared to rel 1e-10 for j <= l_stable = {ls} of {steps} steps")
     assert np.max(np.abs(al[:m] - g.alpha[:m]) / g.alpha[:m]) < 1e-10
     P = w.test_points(ns)
     coef = torch.empty(ns.n, dtype=torch.float64, device="cuda")
