@@ -1,17 +1,14 @@
-// Assembled matrix-vector products of Algorithm 1: p = A z and r = A^T w.
-// FP64: tiles of 32 rows x 32 columns (A z, one row per lane through a
-// shared-memory tile) or 32 rows x 64 columns (A^T w, two columns per lane),
-// an equal number of tiles per warp, partials per (row or column, warp);
-// FP32: balanced (row, column-segment) units per warp for A z, row chunks x
-// column panels for A^T w.  Every partial sum is reduced in a fixed order by
-// the consumer, so results are deterministic.
+// Assembled matrix-vector products of Algorithm 1: p = A z (row-major GEMV;
+// FP64: an equal share of the entries per warp, partials per row piece; FP32:
+// balanced (row, column-segment) units per warp, partials per segment) and
+// r = A^T w (GEMV^T by row chunks); every partial sum is reduced in a fixed
+// order by the consumer, so results are deterministic.
 //
-// A is streamed once per product with coalesced loads (evict-first), the input
-// vector is read through L1.  FP64 operators use FP64 FMAs (on GB300 the FP64
-// pipe, 2 FMA/clk/SM, and not HBM bounds this product) and no FP64 work beyond
-// the n^2 FMAs but one sum per partial.  FP32 (mixed) operators multiply in
-// FP32 and add short FP32 runs of products into FP64 accumulators.
-#include <algorithm>
+// A is streamed once per product with 16-byte vector loads (evict-first), the
+// input vector is read through L1.  FP64 operators use FP64 FMAs (on GB300 the
+// FP64 pipe, 2 FMA/clk/SM, and not HBM bounds this product).  FP32 (mixed)
+// operators multiply in FP32 and add short FP32 runs of products into FP64
+// accumulators.
 #include <mutex>
 
 #include "common.cuh"
@@ -27,143 +24,64 @@ __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 
 // ---------------------------------------------------------------------------
-// FP64 A x by 32 x 32 tiles, one matrix row per lane.  The matrix is cut into
-// row groups of 32 rows and column tiles of 32 columns; the units (group,
-// tile) are numbered group-major and warp w of W owns the contiguous units
-// [U w / W, U (w+1) / W), so every warp does the same number of tiles to
-// within one.  A tile is read row by row with coalesced loads (32 lanes x 8
-// bytes of one row per instruction) into the warp's shared-memory tile (pitch
-// 33 doubles: the column reads below hit 16 distinct bank pairs per half
-// warp), then lane l accumulates row l's 32 products with x (x[c] broadcast
-// by a shuffle from the lane that loaded it).  No cross-lane reduction: each
-// lane keeps its row's sum and writes one partial per (row, warp) into
-// part[slot][row], slot = w minus the first warp of the row group; the warp
-// that ends a row group zeroes the group's remaining slots, so
-// part[0 .. chunks-1][row] always sum to (A x)_row.  Rows and columns at or
-// beyond n are never loaded (padding columns of A may hold anything).
+// FP64 A x by a flat split of the matrix: warp w (of W active warps) owns the
+// row-major elements [b_w, b_{w+1}) with b_w = floor(n^2 w / W), its column
+// rounded down to even (16-byte aligned double2 loads), so every warp streams
+// the same number of entries to within two.  Each row piece of a warp is
+// reduced across the warp and written to part[slot][row], slot = w minus the
+// first warp that touches the row; the warp holding the end of a row writes
+// zeros into the row's remaining slots, so part[0 .. chunks-1][row] always sum
+// to (A x)_row.  n^2 W stays far below 2^63 for any matrix that fits in
+// device memory.
 // ---------------------------------------------------------------------------
-constexpr int TR_WARPS = 8;
-constexpr int TR = 32;
-
-__device__ __forceinline__ double ld_stream1(const double* p) { return __ldcs(p); }
-
-__global__ void __launch_bounds__(TR_WARPS * 32) k_gemv_rows_f64(
-    const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x, int64_t W, int chunks,
-    double* __restrict__ part, const int* __restrict__ done) {
-    if (gkb_done(done)) return;
-    __shared__ double tile[TR_WARPS][TR][TR + 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * TR_WARPS + warp;
-    if (w >= W) return;
-    double(*T)[TR + 1] = tile[warp];
-    const int64_t nt = (n + TR - 1) / TR;  // column tiles per row group
-    const int64_t U = nt * nt;             // units; W <= U, so every warp owns at least one
-    const int64_t u0 = U * w / W, u1 = U * (w + 1) / W;
-    for (int64_t u = u0; u < u1;) {
-        const int64_t g = u / nt;
-        const int64_t ue = min(u1, (g + 1) * nt);
-        const int64_t r0 = g * TR;
-        const int rows = (int)min((int64_t)TR, n - r0);
-        // first warp whose range meets row group g: the largest wf with U wf / W <= g nt
-        const int64_t wf = ((g * nt + 1) * W + U - 1) / U - 1;
-        const int slot = (int)(w - wf);
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        for (; u < ue; ++u) {
-            const int64_t col = (u - g * nt) * TR + lane;
-            const bool cok = col < n;
-            const double xv = cok ? __ldg(x + col) : 0.0;
-            const double* src = A + r0 * lda + col;
-#pragma unroll
-            for (int r = 0; r < TR; ++r) T[r][lane] = (cok && r < rows) ? ld_stream1(src + (int64_t)r * lda) : 0.0;
-            __syncwarp();
-#pragma unroll
-            for (int c = 0; c < TR; c += 4) {
-                a0 = fma(T[lane][c], __shfl_sync(RBF_FULL_MASK, xv, c), a0);
-                a1 = fma(T[lane][c + 1], __shfl_sync(RBF_FULL_MASK, xv, c + 1), a1);
-                a2 = fma(T[lane][c + 2], __shfl_sync(RBF_FULL_MASK, xv, c + 2), a2);
-                a3 = fma(T[lane][c + 3], __shfl_sync(RBF_FULL_MASK, xv, c + 3), a3);
-            }
-            __syncwarp();
-        }
-        if (lane < rows) {
-            const int64_t row = r0 + lane;
-            part[(int64_t)slot * n + row] = (a0 + a1) + (a2 + a3);
-            if (ue == (g + 1) * nt)  // this warp ends the row group
-                for (int s2 = slot + 1; s2 < chunks; ++s2) part[(int64_t)s2 * n + row] = 0.0;
-        }
-    }
+__device__ __forceinline__ int64_t flat_bound(int64_t n, int64_t W, int64_t w) {
+    if (w >= W) return n * n;
+    const int64_t b = n * n * w / W;
+    const int64_t r = b / n;
+    return r * n + ((b - r * n) & ~(int64_t)1);
 }
 
-// ---------------------------------------------------------------------------
-// FP64 A^T x by 32-row x 64-column tiles, two matrix columns per lane.  Units
-// (column tile of 64, row block of 32) are numbered column-tile-major and
-// split over the warps like k_gemv_rows_f64, so a warp walks down the row
-// blocks of a column tile.  Lane l loads A[r][c0 + 2l .. c0 + 2l + 1] (one
-// 16-byte load; 512 contiguous bytes per warp instruction) for the 32 rows of
-// a block and accumulates x[r] times them (x[r] broadcast by a shuffle); at
-// the end of its part of a column tile it writes one partial per column into
-// part[slot][col], and the warp that ends a column tile zeroes the tile's
-// remaining slots.
-// ---------------------------------------------------------------------------
-constexpr int TC = 64;
-
-__global__ void __launch_bounds__(TR_WARPS * 32) k_gemv_cols_f64(
+__global__ void __launch_bounds__(GN_THREADS) k_gemv_flat_f64(
     const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x, int64_t W, int chunks,
     double* __restrict__ part, const int* __restrict__ done) {
     if (gkb_done(done)) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t w = (int64_t)blockIdx.x * TR_WARPS + warp;
+    const int64_t w = (int64_t)blockIdx.x * (GN_THREADS / 32) + warp;
     if (w >= W) return;
-    const int64_t nb = (n + TR - 1) / TR;  // row blocks per column tile
-    const int64_t nct = (n + TC - 1) / TC;
-    const int64_t U = nct * nb;
-    const int64_t u0 = U * w / W, u1 = U * (w + 1) / W;
-    for (int64_t u = u0; u < u1;) {
-        const int64_t t = u / nb;
-        const int64_t ue = min(u1, (t + 1) * nb);
-        const int64_t c = t * TC + 2 * lane;
-        const bool c0ok = c < n, c1ok = c + 1 < n;
-        const int64_t wf = ((t * nb + 1) * W + U - 1) / U - 1;
+    const int64_t e0 = flat_bound(n, W, w), e1 = flat_bound(n, W, w + 1);
+    if (e1 <= e0) return;
+    const int64_t r0 = e0 / n, r1 = (e1 - 1) / n;
+    for (int64_t r = r0; r <= r1; ++r) {
+        const int64_t cs = r == r0 ? e0 - r * n : 0;
+        const int64_t ce = r == r1 ? e1 - r * n : n;
+        int64_t wf = w;  // first warp of the row
+        while (wf > 0 && flat_bound(n, W, wf) > r * n) --wf;
         const int slot = (int)(w - wf);
-        double ax0 = 0.0, ay0 = 0.0, ax1 = 0.0, ay1 = 0.0;
-        for (; u < ue; ++u) {
-            const int64_t r0 = (u - t * nb) * TR;
-            const int rows = (int)min((int64_t)TR, n - r0);
-            const double xv = lane < rows ? __ldg(x + r0 + lane) : 0.0;
-            if (rows == TR && c1ok) {
-                const double2* src = reinterpret_cast<const double2*>(A + r0 * lda + c);
-#pragma unroll
-                for (int r = 0; r < TR; r += 2) {
-                    const double2 m0 = ld_stream(src + (int64_t)r * (lda >> 1));
-                    const double2 m1 = ld_stream(src + (int64_t)(r + 1) * (lda >> 1));
-                    const double x0 = __shfl_sync(RBF_FULL_MASK, xv, r);
-                    const double x1 = __shfl_sync(RBF_FULL_MASK, xv, r + 1);
-                    ax0 = fma(m0.x, x0, ax0);
-                    ay0 = fma(m0.y, x0, ay0);
-                    ax1 = fma(m1.x, x1, ax1);
-                    ay1 = fma(m1.y, x1, ay1);
-                }
-            } else {  // ragged block or column pair: guarded scalar loads
-                for (int r = 0; r < TR; ++r) {
-                    const double xr = __shfl_sync(RBF_FULL_MASK, xv, r);
-                    if (r < rows) {
-                        const double* rowp = A + (r0 + r) * lda + c;
-                        if (c0ok) ax0 = fma(rowp[0], xr, ax0);
-                        if (c1ok) ay0 = fma(rowp[1], xr, ay0);
-                    }
-                }
-            }
+        const double2* __restrict__ row = reinterpret_cast<const double2*>(A + r * lda + cs);
+        const double2* __restrict__ xv = reinterpret_cast<const double2*>(x + cs);
+        const int64_t nvec = (ce - cs) >> 1;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int64_t v = lane;
+        for (; v + 96 < nvec; v += 128) {
+            double2 m0 = ld_stream(row + v), m1 = ld_stream(row + v + 32);
+            double2 m2 = ld_stream(row + v + 64), m3 = ld_stream(row + v + 96);
+            double2 x0 = __ldg(xv + v), x1 = __ldg(xv + v + 32);
+            double2 x2 = __ldg(xv + v + 64), x3 = __ldg(xv + v + 96);
+            a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
+            a1 = fma(m1.x, x1.x, a1); a1 = fma(m1.y, x1.y, a1);
+            a2 = fma(m2.x, x2.x, a2); a2 = fma(m2.y, x2.y, a2);
+            a3 = fma(m3.x, x3.x, a3); a3 = fma(m3.y, x3.y, a3);
         }
-        const bool last = ue == (t + 1) * nb;  // this warp ends the column tile
-        if (c0ok) {
-            part[(int64_t)slot * n + c] = ax0 + ax1;
-            if (last)
-                for (int s2 = slot + 1; s2 < chunks; ++s2) part[(int64_t)s2 * n + c] = 0.0;
+        for (; v < nvec; v += 32) {
+            double2 m0 = ld_stream(row + v), x0 = __ldg(xv + v);
+            a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
         }
-        if (c1ok) {
-            part[(int64_t)slot * n + c + 1] = ay0 + ay1;
-            if (last)
-                for (int s2 = slot + 1; s2 < chunks; ++s2) part[(int64_t)s2 * n + c + 1] = 0.0;
+        if (((ce - cs) & 1) && lane == 0) a1 = fma(A[r * lda + ce - 1], __ldg(x + ce - 1), a1);
+        const double acc = warp_sum((a0 + a1) + (a2 + a3));
+        if (lane == 0) {
+            part[(int64_t)slot * n + r] = acc;
+            if (ce == n)
+                for (int s2 = slot + 1; s2 < chunks; ++s2) part[(int64_t)s2 * n + r] = 0.0;
         }
     }
 }
@@ -342,71 +260,30 @@ static void plan_t(const rbf_ctx* ctx, int64_t n, int vec, int* panel_cols, int*
     plan_t_sms(ctx->sm_count, n, vec, panel_cols, panels, chunks);
 }
 
-// Plan of the tiled FP64 products: W warps (one resident wave, at least 4
-// units each) over U units of `per_group` units per row group (A x) or column
-// tile (A^T x); `chunks` bounds the warps that meet one group: every warp
-// but the last owns at least floor(U / W) units.
-struct TilePlan {
-    int grid;
-    int64_t W;
-    int chunks;
-};
-
-static int tiled_occupancy(const rbf_ctx* ctx, bool rows) {
-    static int occ[2][64] = {{0}};
-    const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
-    int& o = occ[rows ? 0 : 1][dev];
-    if (!o) {
-        int a = 0;
-        const cudaError_t e =
-            rows ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_rows_f64, TR_WARPS * 32, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_cols_f64, TR_WARPS * 32, 0);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            a = 2;
-        }
-        o = a < 1 ? 1 : a;
-    }
-    return o;
-}
-
-static TilePlan tiled_plan(const rbf_ctx* ctx, int64_t n, bool rows) {
-    const int64_t groups = rows ? (n + TR - 1) / TR : (n + TC - 1) / TC;
-    const int64_t per_group = (n + TR - 1) / TR;
-    const int64_t U = groups * per_group;
-    int64_t W = (int64_t)ctx->sm_count * tiled_occupancy(ctx, rows) * TR_WARPS;
-    if (W > U / 4) W = U / 4;  // at least 4 units per warp: few partials per row or column
-    if (W < 1) W = 1;
-    const int64_t per = U / W;  // >= 1
-    TilePlan p;
-    p.W = W;
-    p.grid = (int)((W + TR_WARPS - 1) / TR_WARPS);
-    p.chunks = (int)std::min<int64_t>(W, (per_group + per - 1) / per + 1);
-    return p;
-}
-
 size_t gemv_ws_bytes(const rbf_ctx* ctx, int64_t n) {
+    int pc, pn, ch;
+    plan_t(ctx, n, 2, &pc, &pn, &ch);
     int pc4, pn4, ch4;
     plan_t(ctx, n, 4, &pc4, &pn4, &ch4);
-    int c = std::max(ch4, std::max(tiled_plan(ctx, n, true).chunks, tiled_plan(ctx, n, false).chunks));
-    if (c < 8) c = 8;  // partial-sum rows of the FP32 A x (at most 8)
+    int c = ch > ch4 ? ch : ch4;
+    if (c < 8) c = 8;  // partial-sum rows of the FP64 A x (at most 8)
     return ws_align((size_t)c * n * sizeof(double)) + ws_align((size_t)n * sizeof(float));
 }
 
 int gemv_t_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
-    if (op->precision == RBF_FP64) return tiled_plan(ctx, op->n, false).chunks;
     int pc, pn, ch;
-    plan_t(ctx, op->n, 4, &pc, &pn, &ch);
+    plan_t(ctx, op->n, op->precision == RBF_FP64 ? 2 : 4, &pc, &pn, &ch);
     return ch;
 }
 
-static int gemv_n_occupancy(const rbf_ctx* ctx) {
-    static int occ[64] = {0};
+static int gemv_n_occupancy(const rbf_ctx* ctx, bool fp64) {
+    static int occ[2][64] = {{0}};
     const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
-    int& o = occ[dev];
+    int& o = occ[fp64 ? 0 : 1][dev];
     if (!o) {
         int a = 0;
-        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_nseg_f32, GN_THREADS, 0);
+        const cudaError_t e = fp64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_flat_f64, GN_THREADS, 0)
+                                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_gemv_nseg_f32, GN_THREADS, 0);
         if (e != cudaSuccess) {
             cudaGetLastError();
             a = 4;
@@ -416,11 +293,32 @@ static int gemv_n_occupancy(const rbf_ctx* ctx) {
     return o;
 }
 
+// FP64 A x (flat split): W active warps, at most one wave of resident CTAs,
+// at least 256 entries per warp, and few enough warps that no row is split
+// into more than 8 pieces (the partial-sum rows the workspace provides).  A
+// row of n entries meets at most ceil(n / (per - 2)) + 1 warp ranges, per =
+// floor(n^2 / W) (each boundary is rounded down by at most one entry).
+static void gemv_flat_plan(const rbf_ctx* ctx, int64_t n, int* grid, int64_t* W_out, int* chunks) {
+    const int64_t e = n * n;
+    int64_t W = (int64_t)ctx->sm_count * gemv_n_occupancy(ctx, true) * (GN_THREADS / 32);
+    if (W > e / 256) W = e / 256;
+    if (W < 1) W = 1;
+    auto pieces = [&](int64_t w) -> int64_t {
+        if (w <= 1) return 1;
+        const int64_t per = e / w;
+        return (n + per - 3) / (per - 2) + 1;
+    };
+    while (W > 1 && pieces(W) > 8) --W;
+    *W_out = W;
+    *grid = (int)((W + GN_THREADS / 32 - 1) / (GN_THREADS / 32));
+    *chunks = (int)pieces(W);
+}
+
 // FP32 A x: grid = one wave of resident CTAs; S column segments per row chosen
 // so that the n S units divide as evenly as possible over the grid's warps
 // (efficiency x / ceil(x) with x = n S / warps), segments of >= 256 columns.
 static void gemv_nseg_plan(const rbf_ctx* ctx, int64_t n, int* grid, int* S, int64_t* seglen) {
-    int64_t g = (int64_t)ctx->sm_count * gemv_n_occupancy(ctx);
+    int64_t g = (int64_t)ctx->sm_count * gemv_n_occupancy(ctx, false);
     const int64_t rows_min = (n + 7) / 8;
     if (g > rows_min) g = rows_min;
     if (g < 1) g = 1;
@@ -445,7 +343,11 @@ static void gemv_nseg_plan(const rbf_ctx* ctx, int64_t n, int* grid, int* S, int
 
 int gemv_n_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
     int g, S;
-    if (op->precision == RBF_FP64) return tiled_plan(ctx, op->n, true).chunks;
+    if (op->precision == RBF_FP64) {
+        int64_t W;
+        gemv_flat_plan(ctx, op->n, &g, &W, &S);
+        return S;
+    }
     int64_t len;
     gemv_nseg_plan(ctx, op->n, &g, &S, &len);
     return S;
@@ -455,10 +357,11 @@ rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, 
                          const int* done) {
     int g, S;
     if (op->precision == RBF_FP64) {
-        const TilePlan p = tiled_plan(ctx, op->n, true);
-        k_gemv_rows_f64<<<p.grid, TR_WARPS * 32, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x, p.W,
-                                                                   p.chunks, part, done);
-        RBF_LAUNCHED(ctx, "k_gemv_rows_f64");
+        int64_t W;
+        gemv_flat_plan(ctx, op->n, &g, &W, &S);
+        k_gemv_flat_f64<<<g, GN_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x, W, S, part,
+                                                           done);
+        RBF_LAUNCHED(ctx, "k_gemv_flat_f64");
     } else {
         int64_t len;
         gemv_nseg_plan(ctx, op->n, &g, &S, &len);
@@ -473,10 +376,10 @@ rbf_status launch_gemv_t_partial(rbf_ctx* ctx, const rbf_operator* op, const dou
                                  const float* x32, double* part, const int* done) {
     int pc, pn, ch;
     if (op->precision == RBF_FP64) {
-        const TilePlan p = tiled_plan(ctx, op->n, false);
-        k_gemv_cols_f64<<<p.grid, TR_WARPS * 32, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n, x, p.W,
-                                                                   p.chunks, part, done);
-        RBF_LAUNCHED(ctx, "k_gemv_cols_f64");
+        plan_t(ctx, op->n, 2, &pc, &pn, &ch);
+        k_gemv_t_f64<<<pn * ch, GT_THREADS, 0, ctx->stream>>>((const double*)op->d_A, op->lda, op->n,
+                                                              x, pc, ch, part, done);
+        RBF_LAUNCHED(ctx, "k_gemv_t_f64");
     } else {
         plan_t(ctx, op->n, 4, &pc, &pn, &ch);
         k_gemv_t_f32<<<pn * ch, GT_THREADS, 0, ctx->stream>>>((const float*)op->d_A, op->lda, op->n,
