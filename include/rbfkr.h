@@ -570,6 +570,29 @@ rbf_status rbf_learned_hkt(rbf_ctx* ctx, const rbf_operator* op, const double* d
 rbf_status rbf_batch_learned_hkt(rbf_ctx* ctx, rbf_batch* batch, const rbf_stopnet* net, double* d_coef,
                                  rbf_learned_info* h_info);
 
+/* ---- bounds-checked build (diagnostics, not part of the method) -------------
+ *
+ * The library can be built with -DRBFKR_CHECKED (librbfkr_checked.so): every
+ * device index whose range follows from the host's planning (partial-sum
+ * slots, shared-memory slab sizes, dot-partial and group-sum offsets, matrix
+ * columns within lda) is tested before use; a failed test skips the access and
+ * records the source line, and the next synchronising call (or rbf_check)
+ * returns RBF_ERR_INTERNAL with the file and line in rbf_last_error.  The
+ * normal build compiles the tests away. */
+
+/* 1 for the bounds-checked build, 0 otherwise. */
+int rbf_checked_build(void);
+
+/* Synchronise the device and return RBF_ERR_INTERNAL if a device index check
+ * failed since the last report (always RBF_OK in the normal build, apart from
+ * CUDA errors). */
+rbf_status rbf_check(rbf_ctx* ctx);
+
+/* Enqueue one index test that fails by construction and touches no memory, so
+ * that the next rbf_check of a bounds-checked build reports RBF_ERR_INTERNAL
+ * (the normal build reports nothing): a test of the reporting path itself. */
+rbf_status rbf_check_selftest(rbf_ctx* ctx);
+
 /* ---- measurement (not part of the method) ------------------------------- */
 
 /* Throughput probe of the FP64 units (the roofline peak of the FP64

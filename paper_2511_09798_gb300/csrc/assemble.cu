@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(SY_T * SY_ROWS) k_assemble_sym_f64(const doubl
                 eij *= scale;
                 eji *= scale;
             }
-            A[i * lda + j] = eij;
+            if (RBF_IN_RANGE(j, lda)) A[i * lda + j] = eij;
         }
         tr[li][tx] = eji;
     }
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(SY_T * SY_ROWS) k_assemble_sym_f64(const doubl
     for (int rr = 0; rr < SY_T / SY_ROWS; ++rr) {
         const int lj = ty + SY_ROWS * rr;
         const int64_t jr = J0 + lj, ic = I0 + tx;
-        if (jr < n && ic < n) A[jr * lda + ic] = tr[tx][lj];
+        if (jr < n && ic < n && RBF_IN_RANGE(ic, lda)) A[jr * lda + ic] = tr[tx][lj];
     }
 }
 
@@ -199,3 +199,5 @@ rbf_status launch_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* c
     RBF_LAUNCHED(ctx, "k_evaluate_partial");
     return launch_reduce_partials(ctx, m, (int)chunks, part, u);
 }
+
+RBF_CHECK_READER(assemble)

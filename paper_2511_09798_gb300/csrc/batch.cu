@@ -68,6 +68,8 @@ __global__ void __launch_bounds__(TH) k_mf_batch(const MfItem* __restrict__ item
     const MfItem it = items[blockIdx.x];
     if (done && done[it.b]) return;
     const BInst I = inst[it.b];
+    // the item's summation chunk and output tile lie inside its instance
+    if (!RBF_IN_RANGE(it.chunk, I.chunks) || !RBF_IN_RANGE((int64_t)it.tile * (TH * RO), I.n)) return;
     const double* __restrict__ X = nodes_all + 3 * I.off;
     const int64_t n = I.n, ni = I.ni;
     const float* __restrict__ x32 = x32_all + I.off;
@@ -263,7 +265,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
             ++ns;
         }
         nseg = ns;
-        nrows = base;
+        // the slab's rows must fit the shared-memory vector of rmax rows
+        nrows = RBF_IN_RANGE(base, a.rmax + 1) ? base : a.rmax;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -357,7 +360,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
             if (q < I.chunks) p0 += part[(int64_t)q * n + i];
             double v = (p0 + p1) * inv;
             if (u) v = fma(-nrm, u[i], v);
-            vs[seg_base[sx] + (i - seg_i0[sx])] = v;
+            const int64_t vi = seg_base[sx] + (i - seg_i0[sx]);
+            if (RBF_IN_RANGE(vi, a.rmax)) vs[vi] = v;
             bout[i] = qr[i] * inv;
         }
     }
@@ -385,7 +389,8 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
                 }
                 if (i < rows) a0 = fma(q[i], v[i], a0);
                 const double t = warp_sum(a0 + a1);
-                if (lane == 0) a.hpart_all[I.hoff + (int64_t)m * I.ncta + cslot] = t;
+                if (lane == 0 && RBF_IN_RANGE(cslot, I.ncta) && RBF_IN_RANGE(m, L + 2))
+                    a.hpart_all[I.hoff + (int64_t)m * I.ncta + cslot] = t;
             }
         }
         if (!grid_sync_b(a.stt, a.bar, a.bar_group, a.budget)) return;
@@ -1008,6 +1013,7 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     RBF_CUDA(ctx, cudaMemcpyAsync(&err, &dst->info[IN_ERR], sizeof(int), cudaMemcpyDeviceToHost, s));
     RBF_CUDA(ctx, cudaStreamSynchronize(s));
     RBF_CUDA(ctx, cudaGetLastError());
+    RBF_TRY(rbf_check_all(ctx));
     for (int b = 0; b < P.B; ++b) {
         bt->steps_done[b] = info[BI_STEPS * P.B + b];
         bt->breakdown[b] = info[BI_BREAK * P.B + b];
@@ -1108,3 +1114,5 @@ extern "C" rbf_status rbf_batch_evaluate(rbf_ctx* ctx, const rbf_batch* bt, int 
     }
     return RBF_OK;
 }
+
+RBF_CHECK_READER(batch)

@@ -47,3 +47,37 @@ __device__ __forceinline__ double grid_t(int idx, int J, double t_lo, double t_h
     const double step = __ddiv_rn(t_hi - t_lo, (double)(J - 1));
     return __dadd_rn(__dmul_rn((double)idx, step), t_lo);
 }
+
+// ---- bounds-checked build ---------------------------------------------------
+// A library built with -DRBFKR_CHECKED evaluates RBF_IN_RANGE(i, n) as the test
+// 0 <= i < n; a failed test records its source line in a device word of the
+// translation unit (the first failure is kept) and yields false, so that the
+// caller skips the access.  The host collects the words at its synchronisation
+// points (rbf_check_take_<unit>, rbf_check_all) and reports RBF_ERR_INTERNAL.
+// The checks guard the indexes whose range follows from a planning invariant
+// rather than from a test in the kernel (partial-sum slots, shared-memory slab
+// sizes, dot-partial and group-sum offsets).  In the normal build the macro is
+// `true` and costs nothing.
+#ifdef RBFKR_CHECKED
+static __device__ unsigned rbf_check_line;
+__device__ __forceinline__ bool rbf_in_range(long long i, long long n, unsigned line) {
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&rbf_check_line, 0u, line);
+    return false;
+}
+#define RBF_IN_RANGE(i, n) rbf_in_range((long long)(i), (long long)(n), __LINE__)
+#define RBF_CHECK_READER(unit)                                                              \
+    unsigned rbf_check_take_##unit() {                                                      \
+        unsigned v = 0, z = 0;                                                              \
+        if (cudaMemcpyFromSymbol(&v, rbf_check_line, sizeof(v)) != cudaSuccess) {          \
+            cudaGetLastError();                                                             \
+            return 0;                                                                       \
+        }                                                                                   \
+        if (v) cudaMemcpyToSymbol(rbf_check_line, &z, sizeof(z));                           \
+        return v;                                                                           \
+    }
+#else
+#define RBF_IN_RANGE(i, n) true
+#define RBF_CHECK_READER(unit) \
+    unsigned rbf_check_take_##unit() { return 0; }
+#endif

@@ -5,6 +5,7 @@
 #include <utility>
 #include <vector>
 
+#include "common.cuh"
 #include "internal.h"
 
 rbf_status rbf_fail(rbf_ctx* ctx, rbf_status st, const char* fmt, ...) {
@@ -138,7 +139,57 @@ double rbf_timer_stop(rbf_ctx* ctx) {
     return (double)ms;
 }
 
+RBF_CHECK_READER(ctx)
+
+rbf_status rbf_check_all(rbf_ctx* ctx) {
+    struct Unit {
+        const char* name;
+        unsigned (*take)();
+    };
+    const Unit units[] = {{"ctx.cu", rbf_check_take_ctx},         {"gemv.cu", rbf_check_take_gemv},
+                          {"gkb.cu", rbf_check_take_gkb},         {"batch.cu", rbf_check_take_batch},
+                          {"select.cu", rbf_check_take_select},   {"assemble.cu", rbf_check_take_assemble}};
+    rbf_status st = RBF_OK;
+    for (const Unit& u : units) {
+        const unsigned line = u.take();
+        if (line && st == RBF_OK)
+            st = rbf_fail(ctx, RBF_ERR_INTERNAL, "device index check failed in %s at line %u", u.name, line);
+    }
+    return st;
+}
+
+namespace {
+// Exercises the checked-build plumbing: one index test that fails by
+// construction (5 outside [0, 3)); no memory is accessed either way.
+__global__ void k_check_selftest(int* out) {
+    if (!RBF_IN_RANGE(5, 3)) out[0] = 1;
+}
+}  // namespace
+
 extern "C" {
+
+int rbf_checked_build(void) {
+#ifdef RBFKR_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+rbf_status rbf_check(rbf_ctx* ctx) {
+    RbfRange range_("rbf_check");
+    if (!ctx) return RBF_ERR_INVALID;
+    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
+    RBF_CUDA(ctx, cudaDeviceSynchronize());  // every stream of the context, its lanes and the batch driver
+    return rbf_check_all(ctx);
+}
+
+rbf_status rbf_check_selftest(rbf_ctx* ctx) {
+    if (!ctx) return RBF_ERR_INVALID;
+    k_check_selftest<<<1, 1, 0, ctx->stream>>>(&ctx->d_state->info[IN_SCRATCH]);
+    RBF_LAUNCHED(ctx, "k_check_selftest");
+    return RBF_OK;
+}
 
 rbf_status rbf_create(rbf_ctx** out, int device, void* cuda_stream, const rbf_options* opt) {
     if (!out) return RBF_ERR_INVALID;

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(GN_THREADS) k_gemv_flat_f64(
         }
         if (((ce - cs) & 1) && lane == 0) a1 = fma(A[r * lda + ce - 1], __ldg(x + ce - 1), a1);
         const double acc = warp_sum((a0 + a1) + (a2 + a3));
-        if (lane == 0) {
+        if (lane == 0 && RBF_IN_RANGE(slot, chunks)) {
             part[(int64_t)slot * n + r] = acc;
             if (ce == n)
                 for (int s2 = slot + 1; s2 < chunks; ++s2) part[(int64_t)s2 * n + r] = 0.0;
@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f64(
     const int q = blockIdx.x % chunks;
     const int pnl = blockIdx.x / chunks;
     const int64_t i0 = n * (int64_t)q / chunks;  // balanced row chunks
-    const int64_t i1 = n * (int64_t)(q + 1) / chunks;
+    int64_t i1 = n * (int64_t)(q + 1) / chunks;
+    if (!RBF_IN_RANGE(i1 - i0, GT_MAX_CHUNK_ROWS + 1)) i1 = i0 + GT_MAX_CHUNK_ROWS;  // the x slab in shared memory
     for (int64_t i = i0 + threadIdx.x; i < i1; i += GT_THREADS) xs[i - i0] = x[i];
     __syncthreads();
     const int64_t c = (int64_t)pnl * panel_cols + 2 * threadIdx.x;
@@ -492,3 +493,5 @@ extern "C" rbf_status rbf_matvec_t_noalloc(const double* d_A, int64_t lda, int64
     if (cudaGetLastError() != cudaSuccess) return RBF_ERR_CUDA;
     return RBF_OK;
 }
+
+RBF_CHECK_READER(gemv)

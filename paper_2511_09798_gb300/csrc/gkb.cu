@@ -161,6 +161,8 @@ struct HalfArgs {
     int mcount;
     double* hpart;        // [mcount][G] dot partials
     double* gpart;        // 2 x [mcount][barrier groups] group sums (by barrier parity)
+    int64_t hpart_len;    // elements of hpart and of gpart (bounds-checked build)
+    int64_t gpart_len;
     double* npart;        // in: |q_raw|^2 partials; out: |v|^2 partials
     int rmax;             // slab rows held in shared memory (odd: conflict-free strides)
     unsigned* bar;        // barrier counters (see grid_reduce_sync)
@@ -191,8 +193,9 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
     rbf_dev_state* stt = a.stt;
     if (*(volatile int*)&stt->info[IN_DONE]) return;
     const Slab s = slab_of(a.n);
-    const int R = (int)(s.r1 - s.r0);
     const int RM = a.rmax;
+    int R = (int)(s.r1 - s.r0);
+    if (!RBF_IN_RANGE(R, RM + 1)) R = RM;  // the slab must fit its shared-memory rows
     const int M = a.mcount;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* Qs = dsm;                                 // [M][RM]   (STAGE)
@@ -315,10 +318,13 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
                 d4[(size_t)k * M + m] = c0 + c1;
             }
             __syncthreads();
-            for (int m = threadIdx.x; m < M; m += SL_THREADS)
-                a.hpart[(int64_t)m * gridDim.x + blockIdx.x] = (d4[m] + d4[M + m]) + (d4[2 * M + m] + d4[3 * M + m]);
+            for (int m = threadIdx.x; m < M; m += SL_THREADS) {
+                const int64_t hi = (int64_t)m * gridDim.x + blockIdx.x;
+                if (RBF_IN_RANGE(hi, a.hpart_len)) a.hpart[hi] = (d4[m] + d4[M + m]) + (d4[2 * M + m] + d4[3 * M + m]);
+            }
             // hs = Q^T v': one grid barrier that also sums the partials (fixed order)
-            if (!grid_reduce_sync(stt, a.bar, a.bar_group, a.budget, a.epoch0 + pass + 1, a.hpart, a.gpart, hs, M))
+            if (!grid_reduce_sync(stt, a.bar, a.bar_group, a.budget, a.epoch0 + pass + 1, a.hpart, a.gpart, hs, M,
+                                  a.gpart_len))
                 return;
             // v' -= Q hs: thread (row, group of basis vectors), two chains each
             const int row = threadIdx.x % UPD_ROWS;
@@ -346,7 +352,8 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
                 __syncthreads();
             }
         }
-    } else if (!grid_reduce_sync(stt, a.bar, a.bar_group, a.budget, a.epoch0 + 1, a.hpart, a.gpart, hs, 0)) {
+    } else if (!grid_reduce_sync(stt, a.bar, a.bar_group, a.budget, a.epoch0 + 1, a.hpart, a.gpart, hs, 0,
+                                 a.gpart_len)) {
         // nothing to reorthogonalize against: a plain barrier, so that no CTA
         // overwrites npart below while another still reads it above
         return;
@@ -595,6 +602,8 @@ struct GkbRun {
         a.mcount = mcount;
         a.hpart = hpart;
         a.gpart = gpart;
+        a.hpart_len = (int64_t)(st->capacity + 2) * G;
+        a.gpart_len = (int64_t)2 * (st->capacity + 2) * G;
         a.npart = npart;
         a.rmax = rmax;
         a.bar = bar;
@@ -675,6 +684,7 @@ static rbf_status read_back(rbf_ctx* ctx, rbf_gkb_state* st) {
     st->breakdown = ctx->h_state->info[IN_BREAK];
     st->c_hat = ctx->h_state->scal[SC_CHAT0] > ctx->h_state->scal[SC_CHAT1] ? ctx->h_state->scal[SC_CHAT0]
                                                                            : ctx->h_state->scal[SC_CHAT1];
+    RBF_TRY(rbf_check_all(ctx));
     if (ctx->h_state->info[IN_ERR] != 0)
         return rbf_fail(ctx, (rbf_status)ctx->h_state->info[IN_ERR],
                         "a bounded device-side wait gave up (grid barrier of the GKB half-step)");
@@ -801,6 +811,7 @@ extern "C" rbf_status rbf_gkb_many(rbf_ctx* ctx, int count, const rbf_operator* 
     RBF_TRY(je);
     RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     RBF_CUDA(ctx, cudaGetLastError());
+    RBF_TRY(rbf_check_all(ctx));
     int total = 0;
     for (int i = 0; i < count; ++i) {
         const rbf_dev_state& h = ctx->h_many[i];
@@ -868,3 +879,5 @@ extern "C" rbf_status rbf_gkb_restore(rbf_ctx* ctx, rbf_gkb_state* st, const dou
     st->c_hat = c_hat;
     return RBF_OK;
 }
+
+RBF_CHECK_READER(gkb)

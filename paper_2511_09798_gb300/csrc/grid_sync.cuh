@@ -2,6 +2,7 @@
 // a cooperative launch).
 #pragma once
 
+#include "common.cuh"
 #include "internal.h"
 
 // ---------------------------------------------------------------------------
@@ -87,7 +88,8 @@ static __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 static __device__ bool grid_reduce_sync(rbf_dev_state* __restrict__ stt, unsigned* __restrict__ bar, int group,
                                         long long budget, unsigned epoch, const double* __restrict__ part,
-                                        double* __restrict__ gpart, double* __restrict__ hs, int M) {
+                                        double* __restrict__ gpart, double* __restrict__ hs, int M,
+                                        int64_t gpart_len) {
     __shared__ int role;
     __shared__ int ok;
     const int G = gridDim.x;
@@ -114,7 +116,7 @@ static __device__ bool grid_reduce_sync(rbf_dev_state* __restrict__ stt, unsigne
                 s1 += __ldcg(p + b + 1);
             }
             if (b < members) s0 += __ldcg(p + b);
-            gp[(int64_t)m * K + grp] = s0 + s1;
+            if (RBF_IN_RANGE((gp - gpart) + (int64_t)m * K + grp, gpart_len)) gp[(int64_t)m * K + grp] = s0 + s1;
         }
         __syncthreads();
         if (threadIdx.x == 0) {

@@ -30,7 +30,7 @@ enum {
     SC_ETA = 9,     // |y| of the last projected solve
     SC_RHO = 10,    // projected residual of the last projected solve
 };
-enum { IN_STEPS = 0, IN_BREAK = 1, IN_DONE = 2, IN_ERR = 3, IN_INDEX = 4, IN_RANK = 5 };
+enum { IN_STEPS = 0, IN_BREAK = 1, IN_DONE = 2, IN_ERR = 3, IN_INDEX = 4, IN_RANK = 5, IN_SCRATCH = 7 };
 
 // Named NVTX range around a library call, shown on Nsight timelines; a
 // no-op unless a profiling tool is attached.  Scoped, so that a call that
@@ -89,6 +89,17 @@ rbf_status rbf_lanes_join(rbf_ctx* ctx, int lanes);
 
 // ---- error helpers ---------------------------------------------------------
 rbf_status rbf_fail(rbf_ctx* ctx, rbf_status st, const char* fmt, ...);
+
+// Bounds-checked build: the line of the first failed index check of each
+// instrumented translation unit (0 = none; always 0 in the normal build), and
+// their collection into RBF_ERR_INTERNAL (call after the work has completed).
+unsigned rbf_check_take_ctx();
+unsigned rbf_check_take_gemv();
+unsigned rbf_check_take_gkb();
+unsigned rbf_check_take_batch();
+unsigned rbf_check_take_select();
+unsigned rbf_check_take_assemble();
+rbf_status rbf_check_all(rbf_ctx* ctx);
 
 #define RBF_CUDA(ctx, call)                                                             \
     do {                                                                                \

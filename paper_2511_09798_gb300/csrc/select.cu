@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(128) k_lift(ProjDims d, const double* __restri
     const double* Z = Z_all + (ld.zoff ? ld.zoff[b] : 0);
     double* coef = coef_all + (ld.coff ? ld.coff[b] : 0);
     const double* y = y_all + (size_t)b * d.L;
-    for (int m = threadIdx.x; m < l; m += 128) ys[m] = y[m];
+    for (int m = threadIdx.x; m < l; m += 128)
+        if (RBF_IN_RANGE(m, 1024)) ys[m] = y[m];  // the projected dimension fits the shared copy
     __syncthreads();
     const int row = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * 32 + row;
@@ -359,6 +360,7 @@ rbf_status read_info(rbf_ctx* ctx, rbf_solve_info* info, int l) {
                                   cudaMemcpyDeviceToHost, ctx->stream));
     RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     RBF_CUDA(ctx, cudaGetLastError());
+    RBF_TRY(rbf_check_all(ctx));
     if (info) info_from_state(ctx->h_state, l, info);
     return RBF_OK;
 }
@@ -443,6 +445,7 @@ extern "C" rbf_status rbf_hkt_many(rbf_ctx* ctx, int count, const rbf_gkb_state*
     RBF_TRY(je);
     RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     RBF_CUDA(ctx, cudaGetLastError());
+    RBF_TRY(rbf_check_all(ctx));
     if (infos)
         for (int i = 0; i < count; ++i) info_from_state(&ctx->h_many[i], states[i].steps_done, &infos[i]);
     return RBF_OK;
@@ -457,3 +460,5 @@ extern "C" rbf_status rbf_ine_tsvd(rbf_ctx* ctx, const rbf_gkb_state* st, int ra
     if (rank < 0 || rank > l) return rbf_fail(ctx, RBF_ERR_INVALID, "rank %d outside [0, l=%d]", rank, l);
     return single_solve(ctx, st, 1, RBF_GCV, 0.0, rank, d_coef, d_curve, info);
 }
+
+RBF_CHECK_READER(select)

@@ -162,6 +162,9 @@ EXPORTS = {
                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "rbf_stopnet_save": (C.c_int, [C.c_void_p, C.POINTER(StopNet), C.c_char_p]),
     "rbf_stopnet_load": (C.c_int, [C.c_void_p, C.c_char_p, C.POINTER(StopNet), C.c_void_p]),
+    "rbf_checked_build": (C.c_int, []),
+    "rbf_check": (C.c_int, [C.c_void_p]),
+    "rbf_check_selftest": (C.c_int, [C.c_void_p]),
     "rbf_probe_fp64": (C.c_int, [C.c_void_p, C.c_int, C.c_longlong, C.c_void_p, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
 }
@@ -190,9 +193,10 @@ def load(path: str | None = None):
     if _lib is not None:
         return _lib
     from . import build as _build
-    p = path or LIB_PATH
+    checked = os.environ.get("RBFKR_CHECKED", "") == "1"
+    p = path or (_build.LIB_CHECKED if checked else LIB_PATH)
     if path is None:
-        _build.build()
+        _build.build(checked=checked)
     if not os.path.exists(p):
         raise RuntimeError(f"librbfkr.so not found at {p}; the CUDA library is required")
     lib = C.CDLL(p)
@@ -356,6 +360,13 @@ class Context:
         t = (C.c_double * 4)(*[float(x) for x in tols])
         self._check(self.lib.rbf_stopnet_init(self.h, C.byref(net), _ptr(storage), *[fp(a) for a in keep], r, t))
         return net
+
+    def rbf_check(self):
+        """Synchronise and report a failed device index check (bounds-checked build)."""
+        self._check(self.lib.rbf_check(self.h))
+
+    def rbf_check_selftest(self):
+        self._check(self.lib.rbf_check_selftest(self.h))
 
     def rbf_probe_fp64(self, mode, iters, scratch):
         ms, flops = C.c_double(), C.c_double()

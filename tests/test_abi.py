@@ -47,3 +47,13 @@ def test_oracle_does_not_import_the_package():
     for f in glob.glob(os.path.join(ROOT, "oracle", "*.py")):
         mods = re.findall(r"^\s*(?:from|import)\s+([\w.]+)", open(f).read(), flags=re.M)
         assert not any(m.startswith("paper_2511_09798_gb300") for m in mods), f
+
+
+def test_checked_library_builds_and_exports_the_same_symbols():
+    from paper_2511_09798_gb300 import build
+    lib_path = build.build(checked=True)
+    import ctypes
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert lib.rbf_checked_build() == 1
