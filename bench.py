@@ -342,6 +342,7 @@ def run_ours(args, rank, world, local_rank):
     # the forms of the method on uneven instances whose field HKT resolves:
     # time to solution and error against the exact solution (after the timed region)
     forms = forms_comparison(local_rank) if wl["name"] == "cube8000" and not args.no_forms else None
+    mf_roof = mf_product_roofline(local_rank) if wl["name"] == "cube8000" and not args.no_forms else None
     # phase shares (separate context with synchronising per-phase timers)
     ctx_ph = R.Context(local_rank, stream=stream, timing=1)
     phases = {}
@@ -427,6 +428,7 @@ def run_ours(args, rank, world, local_rank):
         "lambda_over_s1_log10": [round(x, 3) for x in t_chosen],
         "gaussian_variant": gauss,
         "forms_comparison": forms,
+        "matrix_free_roofline": mf_roof,
         "gkb_steps_done": done, "solves": solves,
         "roofline": roof,
         "e2e": {"value": round(done_e2e / (ms_e2e / 1e3), 2), "unit": "GKB steps/s",
@@ -959,6 +961,48 @@ def run_paper_sweep(args, rank, world, local_rank):
             "config": {"workload": "paper-sweep", "c": c, "k": k, "sigma": sigma,
                        "gkb_steps": {"cube": 140, "sphere": 180}, "test_points": 2000},
             "rows": rows}
+
+
+# --------------------------------------------------------------------------- matrix-free product roofline
+def mf_product_roofline(local_rank, pairs=10):
+    """The matrix-free FP32 product (entries regenerated from the node
+    coordinates) on the 20 000-node sphere (c = 0.15, k = 10): CUDA-event
+    time of `pairs` A x / A^T x pairs through rbf_matvec after two warm-up
+    pairs, as regenerated entries per second and a fraction of the FP32 pipe
+    (11 FP32-pipe operations per PDE entry, 8 per Dirichlet entry, the MUFU
+    rsqrt beside them)."""
+    import numpy as np
+    import torch
+
+    import workloads as w
+    from paper_2511_09798_gb300 import rbfkr as R
+    ns = w.preset("sphere20000")
+    n = ns.n
+    stream = torch.cuda.current_stream()
+    ctx = R.Context(local_rank, stream=stream)
+    nodes = torch.as_tensor(ns.soa(), device=f"cuda:{local_rank}")
+    op = ctx.rbf_operator_init(nodes, n, ns.n_interior, 0.15, 10.0, R.RBF_MATRIX_FREE, R.RBF_MIXED)
+    x = torch.as_tensor(np.random.default_rng(0).normal(size=n), device=f"cuda:{local_rank}")
+    y = torch.empty_like(x)
+    for _ in range(2):
+        ctx.rbf_matvec(op, 0, x, y)
+        ctx.rbf_matvec(op, 1, y, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(pairs):
+        ctx.rbf_matvec(op, 0, x, y)
+        ctx.rbf_matvec(op, 1, y, x)
+        x.div_(torch.linalg.vector_norm(x))  # keep the iterate bounded
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.close()
+    ms = e0.elapsed_time(e1) / (2 * pairs)
+    roof = mf_roofline(n, ns.n_interior, ms)
+    roof.update({"kernel": "k_mf_partial (FP32 matrix-free product, sphere20000)", "avg_launch_ms": round(ms, 5),
+                 "timing": f"{pairs} A x / A^T x pairs through rbf_matvec (the product, the partial-sum "
+                           f"reduction and one vector normalisation per pair), CUDA events"})
+    return roof
 
 
 # --------------------------------------------------------------------------- forms at equal error
