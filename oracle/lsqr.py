@@ -24,6 +24,8 @@ from .regularize import LCURVE_MIN_SPEED2, lcurve_curvature
 
 
 def bidiag(alpha, beta, k):
+    """Lower bidiagonal C_k ((k+1) x k): alpha_1..alpha_k on the diagonal,
+    beta_2..beta_{k+1} below it (Algorithm 1)."""
     C = np.zeros((k + 1, k))
     for m in range(k):
         C[m, m] = alpha[m]

@@ -17,6 +17,7 @@ import numpy as np
 
 from . import evaluate as OE
 from . import regularize as OR
+from .lsqr import bidiag
 
 NEG = -300.0  # stands for log10(0) and for unavailable entries
 
@@ -52,16 +53,6 @@ def stop_features(alpha, beta, j):
             last = np.log10(r / beta[0]) if r > 0.0 else NEG
         f[9 + i] = last
     return f
-
-
-def bidiag(alpha, beta, i):
-    """Lower bidiagonal C_i ((i+1) x i): alpha_1..alpha_i on the diagonal,
-    beta_2..beta_{i+1} below it (Algorithm 1)."""
-    C = np.zeros((i + 1, i))
-    for m in range(i):
-        C[m, m] = alpha[m]
-        C[m + 1, m] = beta[m + 1]
-    return C
 
 
 def error_table(g, X, c, P, uref, ells, tgrid):

@@ -203,3 +203,49 @@ def test_batch96_full_size(ctx, R):
         assert lam[b] == pytest.approx(grid[i_gpu], rel=1e-12)
         assert i_gpu == idx_or or curve[i_gpu] <= curve[idx_or] * (1 + 1e-9)
         check_hkt_against_projected_oracle(g, lam[b], i_gpu, coef[off:off + n].cpu().numpy(), rule=None)
+
+
+def test_cube8000_six_solves_on_lanes(ctx, R):
+    """The default benchmark's launch configuration: the six cube8000 FP64
+    solves (c in {0.1, 0.2, 0.5} x k in {2, 5}, 100 steps, HKT with GCV) assembled
+    and run on six concurrent lanes (rbf_gkb_many, rbf_hkt_many).  Every state and
+    every coefficient vector equals the single-run path bitwise, and one solve
+    is checked against the FP64 oracle directly (u at the oracle's lambda)."""
+    from oracle import evaluate as OE
+    ns = w.preset("cube8000")
+    n, L = ns.n, 100
+    cases = [(c, k) for c in (0.1, 0.2, 0.5) for k in (2.0, 5.0)]
+    nodes = dev(ns.soa())
+    lda = R.padded_lda(n, R.RBF_FP64)
+    mats = [torch.empty((n, lda), dtype=torch.float64, device="cuda") for _ in cases]
+    ops = [ctx.rbf_operator_init(nodes, n, ns.n_interior, c, k, R.RBF_ASSEMBLED, R.RBF_FP64, 0, A, lda)
+           for (c, k), A in zip(cases, mats)]
+    fs = {k: dev(w.plane_wave_rhs(ns, k)) for k in (2.0, 5.0)}
+    bufs = [R.make_state(torch, n, L) for _ in cases]
+    states = [b[0] for b in bufs]
+    ctx.rbf_gkb_many(ops, [fs[k] for _, k in cases], L, states, assemble=True)
+    coefs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in cases]
+    infos = ctx.rbf_hkt_many(states, R.RBF_GCV, 0.0, coefs)
+    for i, (c, k) in enumerate(cases):
+        st1, W1, Z1, a1, b1 = R.make_state(torch, n, L)
+        ctx.rbf_gkb(ops[i], fs[k], L, st1)
+        assert st1.steps_done == states[i].steps_done
+        _, W2, Z2, a2, b2 = bufs[i]
+        assert torch.equal(a1, a2) and torch.equal(b1, b2) and torch.equal(W1, W2) and torch.equal(Z1, Z2), i
+        c1 = torch.empty(n, dtype=torch.float64, device="cuda")
+        inf1 = ctx.rbf_hkt(st1, R.RBF_GCV, 0.0, c1)
+        assert torch.equal(c1, coefs[i]) and inf1.lambda_ == infos[i].lambda_, i
+    # one of the six against the oracle: u at the oracle's GCV lambda
+    i = 3
+    c, k = cases[i]
+    A = OM.assemble(ns.X, ns.n_interior, c, k)
+    g = OG.gkb(A, None, w.plane_wave_rhs(ns, k), L)
+    assert g.steps_done == states[i].steps_done
+    h = OR.hkt(g, "gcv")
+    coef = torch.empty(n, dtype=torch.float64, device="cuda")
+    ctx.rbf_hkt(states[i], R.RBF_FIXED, h["lam"], coef)
+    P = w.test_points(ns)
+    u = torch.empty(P.shape[0], dtype=torch.float64, device="cuda")
+    ctx.rbf_evaluate(ops[i], coef, dev(P.T), P.shape[0], u)
+    u_or = OE.reconstruct(h["coef"], ns.X, P, c)
+    assert np.max(np.abs(u.cpu().numpy() - u_or)) / np.max(np.abs(u_or)) < 1e-10
