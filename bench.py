@@ -634,25 +634,29 @@ def run_batch(args, rank, world, local_rank):
         half_ms = ct["reorth_ms"] / nh
         prod_ms = sum(ct["product_ms"])
         done_b = [bt.steps_done[b] for b in range(len(inst))]
-        # algorithmic bytes of one batched half-step, averaged over the run: one
-        # read of every active instance's basis (sum over the run of 8 n_b
-        # (j - 1) + 8 n_b j = 8 n_b l_b^2) plus the vectors each half-step must
-        # read and write (product partials, q, the new vector: ~5 x 8 n_b)
+        # algorithmic work of one batched half-step, averaged over the run:
+        # classical Gram-Schmidt applied twice against each active instance's
+        # basis of M vectors is 2 passes x (dots + update) = 4 n_b M FP64 FMAs;
+        # over a run M = j - 1 (r-side) and j (p-side), so the FMAs sum to
+        # 4 n_b l_b^2.  Bytes: one read of every active basis (8 n_b l_b^2 over
+        # the run) plus the vectors each half-step reads and writes (~5 x 8 n_b).
+        fma = sum(4 * s_.n * l_b * l_b for s_, l_b in zip(inst, done_b)) / (2 * L)
         basis = sum(8 * s_.n * l_b * l_b for s_, l_b in zip(inst, done_b))
         vec = sum(2 * l_b * 5 * 8 * s_.n for s_, l_b in zip(inst, done_b))
         alg = (basis + vec) / (2 * L)
         peak_hbm = measured_peaks().get("hbm_gbs", 6801.7)
         gbs = alg / (half_ms / 1e3) / 1e9
+        tflops = 2 * fma / (half_ms / 1e3) / 1e12
         kern = {"half_step_roofline": {
-                    "kernel": "k_half_batch", "bound": "hbm", "achieved": round(gbs, 1), "peak": peak_hbm,
-                    "unit": "GB/s", "frac": round(gbs / peak_hbm, 4), "traffic": None,
+                    "kernel": "k_half_batch", "bound": "alu", "achieved": round(tflops, 4),
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                    "traffic": None, "pipe": "fp64 (CGS2: 4 n M FMA per half-step)",
+                    "peak_source": FP64_PEAK_SOURCE,
                     "avg_launch_ms": round(half_ms, 5), "launches_timed": int(ct["reorth_launches"]),
-                    "algorithmic_per_launch": f"{alg:.4g} bytes (one read of each active basis + vectors, "
-                                              f"averaged over the {2 * L} half-steps)",
-                    "design_traffic_per_launch": f"{(4 * basis + vec) / (2 * L):.4g} bytes (the kernel reads "
-                                                 f"each basis 4 times: 2 dot passes, 2 update passes)",
-                    "design_traffic_gbs": round((4 * basis + vec) / (2 * L) / (half_ms / 1e3) / 1e9, 1),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+                    "algorithmic_per_launch": f"{fma:.4g} FP64 FMA, {alg:.4g} bytes (one read of each active "
+                                              f"basis + vectors), averaged over the {2 * L} half-steps",
+                    "hbm_achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak_hbm, 4),
+                    "design_traffic_gbs": round((4 * basis + vec) / (2 * L) / (half_ms / 1e3) / 1e9, 1)},
                 "batch_ms_graph_with_solve_and_u": round(ms / args.steps, 2),
                 "batch_gkb_ms_graph": round(ms_graph_gkb, 2),
                 "batch_gkb_ms_direct_timed": round(ms_direct, 2),

@@ -128,3 +128,30 @@ def test_many_rejects_bad_arguments(R):
         ctx.rbf_gkb_many([op], [f], 5, [st], lanes=9)
     assert e.value.status == R.RBF_ERR_INVALID
     ctx.close()
+
+
+def test_many_more_runs_than_lanes_and_stream_order(R):
+    """Ten runs with the default lane count (capped at 8, and by the half-step
+    kernel's co-residency), inputs written on the context stream just before
+    the call (the lanes start after that work), results equal to single runs."""
+    rng = np.random.Generator(np.random.PCG64(81))
+    sets = [w.cube_faces_random(int(n), 0.3, rng) for n in rng.integers(300, 1400, 10)]
+    steps = 15
+    stream = torch.cuda.Stream()
+    ctx = R.Context(0, stream=stream)
+    ops, keep = _ops(ctx, R, sets, [(R.RBF_ASSEMBLED, R.RBF_FP64)] * 10, [0.3] * 10, [2.0] * 10)
+    torch.cuda.synchronize()
+    host = [torch.as_tensor(w.plane_wave_rhs(s, 2.0)).pin_memory() for s in sets]
+    fs = [torch.zeros(s.n, dtype=torch.float64, device="cuda") for s in sets]
+    states = [R.make_state(torch, s.n, steps)[0] for s in sets]
+    with torch.cuda.stream(stream):
+        for f, h in zip(fs, host):
+            f.copy_(h, non_blocking=True)  # enqueued on the context stream
+        ctx.rbf_gkb_many(ops, fs, steps, states)
+    for i, s in enumerate(sets):
+        st1, W1, Z1, a1, b1 = R.make_state(torch, s.n, steps)
+        ctx.rbf_gkb(ops[i], fs[i], steps, st1)
+        torch.cuda.synchronize()
+        assert st1.steps_done == states[i].steps_done == steps
+        assert torch.equal(a1, states[i]._keep[2]) and torch.equal(W1, states[i]._keep[0]), i
+    ctx.close()
