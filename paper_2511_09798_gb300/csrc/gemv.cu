@@ -26,19 +26,22 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p);
 // ---------------------------------------------------------------------------
 // FP64 A x by a flat split of the matrix: warp w (of W active warps) owns the
 // row-major elements [b_w, b_{w+1}) with b_w = floor(n^2 w / W), its column
-// rounded down to even (16-byte aligned double2 loads), so every warp streams
-// the same number of entries to within two.  Each row piece of a warp is
+// rounded down to a multiple of 128 (16-byte aligned double2 loads, full
+// 128-column blocks), so every warp streams the same number of entries to
+// within 128.  Each row piece of a warp is
 // reduced across the warp and written to part[slot][row], slot = w minus the
 // first warp that touches the row; the warp holding the end of a row writes
 // zeros into the row's remaining slots, so part[0 .. chunks-1][row] always sum
 // to (A x)_row.  n^2 W stays far below 2^63 for any matrix that fits in
 // device memory.
 // ---------------------------------------------------------------------------
+constexpr int64_t FLAT_ALIGN = 128;  // piece starts within a row: multiples of 128 columns
+
 __device__ __forceinline__ int64_t flat_bound(int64_t n, int64_t W, int64_t w) {
     if (w >= W) return n * n;
     const int64_t b = n * n * w / W;
     const int64_t r = b / n;
-    return r * n + ((b - r * n) & ~(int64_t)1);
+    return r * n + ((b - r * n) & ~(FLAT_ALIGN - 1));
 }
 
 __global__ void __launch_bounds__(GN_THREADS) k_gemv_flat_f64(
@@ -60,6 +63,8 @@ __global__ void __launch_bounds__(GN_THREADS) k_gemv_flat_f64(
         const double2* __restrict__ row = reinterpret_cast<const double2*>(A + r * lda + cs);
         const double2* __restrict__ xv = reinterpret_cast<const double2*>(x + cs);
         const int64_t nvec = (ce - cs) >> 1;
+        // piece lengths are multiples of 128 columns except at a row's end, so
+        // every lane is busy in all but the row's last loads
         double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         int64_t v = lane;
         for (; v + 96 < nvec; v += 128) {
@@ -72,12 +77,14 @@ __global__ void __launch_bounds__(GN_THREADS) k_gemv_flat_f64(
             a2 = fma(m2.x, x2.x, a2); a2 = fma(m2.y, x2.y, a2);
             a3 = fma(m3.x, x3.x, a3); a3 = fma(m3.y, x3.y, a3);
         }
+        a0 += a2;
+        a1 += a3;
         for (; v < nvec; v += 32) {
             double2 m0 = ld_stream(row + v), x0 = __ldg(xv + v);
             a0 = fma(m0.x, x0.x, a0); a0 = fma(m0.y, x0.y, a0);
         }
         if (((ce - cs) & 1) && lane == 0) a1 = fma(A[r * lda + ce - 1], __ldg(x + ce - 1), a1);
-        const double acc = warp_sum((a0 + a1) + (a2 + a3));
+        const double acc = warp_sum(a0 + a1);
         if (lane == 0 && RBF_IN_RANGE(slot, chunks)) {
             part[(int64_t)slot * n + r] = acc;
             if (ce == n)
@@ -158,9 +165,12 @@ __global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f64(
         return;
     }
     const double* __restrict__ base = A + i0 * lda + c;
-    double ax[GT_UNROLL], ay[GT_UNROLL];
+    // 8 rows of loads in flight, 4 accumulator pairs (rows u and u + 4 share
+    // one): the combine at the end costs 6 adds per column pair
+    constexpr int GT_ACC = GT_UNROLL / 2;
+    double ax[GT_ACC], ay[GT_ACC];
 #pragma unroll
-    for (int u = 0; u < GT_UNROLL; ++u) ax[u] = ay[u] = 0.0;
+    for (int u = 0; u < GT_ACC; ++u) ax[u] = ay[u] = 0.0;
     const int64_t rows = i1 - i0;
     int64_t r = 0;
     for (; r + GT_UNROLL - 1 < rows; r += GT_UNROLL) {
@@ -169,8 +179,8 @@ __global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f64(
         for (int u = 0; u < GT_UNROLL; ++u) m[u] = ld_stream(reinterpret_cast<const double2*>(base + (r + u) * lda));
 #pragma unroll
         for (int u = 0; u < GT_UNROLL; ++u) {
-            ax[u] = fma(m[u].x, xs[r + u], ax[u]);
-            ay[u] = fma(m[u].y, xs[r + u], ay[u]);
+            ax[u % GT_ACC] = fma(m[u].x, xs[r + u], ax[u % GT_ACC]);
+            ay[u % GT_ACC] = fma(m[u].y, xs[r + u], ay[u % GT_ACC]);
         }
     }
     for (; r < rows; ++r) {
@@ -178,12 +188,8 @@ __global__ void __launch_bounds__(GT_THREADS) k_gemv_t_f64(
         ax[0] = fma(m0.x, xs[r], ax[0]);
         ay[0] = fma(m0.y, xs[r], ay[0]);
     }
-    double sx = 0.0, sy = 0.0;
-#pragma unroll
-    for (int u = 0; u < GT_UNROLL; ++u) {
-        sx += ax[u];
-        sy += ay[u];
-    }
+    const double sx = (ax[0] + ax[1]) + (ax[2] + ax[3]);
+    const double sy = (ay[0] + ay[1]) + (ay[2] + ay[3]);
     part[(int64_t)q * n + c] = sx;
     if (c + 1 < n) part[(int64_t)q * n + c + 1] = sy;
 }
@@ -304,10 +310,13 @@ static void gemv_flat_plan(const rbf_ctx* ctx, int64_t n, int* grid, int64_t* W_
     int64_t W = (int64_t)ctx->sm_count * gemv_n_occupancy(ctx, true) * (GN_THREADS / 32);
     if (W > e / 256) W = e / 256;
     if (W < 1) W = 1;
+    // a warp owns at least per - FLAT_ALIGN entries (each bound is rounded down
+    // by less than FLAT_ALIGN), so a row meets at most this many warp ranges
     auto pieces = [&](int64_t w) -> int64_t {
         if (w <= 1) return 1;
         const int64_t per = e / w;
-        return (n + per - 3) / (per - 2) + 1;
+        if (per <= FLAT_ALIGN) return n;  // never taken: W <= e / 256
+        return (n + per - FLAT_ALIGN - 1) / (per - FLAT_ALIGN) + 1;
     };
     while (W > 1 && pieces(W) > 8) --W;
     *W_out = W;
