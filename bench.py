@@ -57,8 +57,8 @@ FP32_LANE_TOPS = 152 * 128 * 2.07e9 / 1e12  # FP32 pipe: one operation per lane 
 # ncu capture of that kernel at the workload's size (dram__bytes_read.sum +
 # dram__bytes_write.sum); None where the kernel changed after its capture.
 MEASURED_TRAFFIC = {
-    ("cube8000", 0): 512.658e6 + 2.903e6,                      # k_gemv_flat_f64
-    ("cube8000", 1): 512.185e6 + 3.901e6,                      # k_gemv_t_f64
+    ("cube8000", 0): 512.113e6 + 0.166e6,                      # k_gemv_flat_f64
+    ("cube8000", 1): 512.116e6 + 4.010e6,                      # k_gemv_t_f64
     ("sphere20000-mixed-assembled", 0): 1600.665e6 + 4.324e6,  # k_gemv_nseg_f32
     ("sphere20000-mixed-assembled", 1): 1600.146e6 + 3.266e6,  # k_gemv_t_f32
 }
