@@ -583,9 +583,10 @@ rbf_status rbf_batch_learned_hkt(rbf_ctx* ctx, rbf_batch* batch, const rbf_stopn
 /* 1 for the bounds-checked build, 0 otherwise. */
 int rbf_checked_build(void);
 
-/* Synchronise the device and return RBF_ERR_INTERNAL if a device index check
- * failed since the last report (always RBF_OK in the normal build, apart from
- * CUDA errors). */
+/* Wait for all work of the context (its stream, its lanes and the batched
+ * driver's stream) and return RBF_ERR_INTERNAL if a device index check failed
+ * since the last report (always RBF_OK in the normal build, apart from CUDA
+ * errors). */
 rbf_status rbf_check(rbf_ctx* ctx);
 
 /* Enqueue one index test that fails by construction and touches no memory, so

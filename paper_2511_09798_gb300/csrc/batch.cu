@@ -607,6 +607,10 @@ static BatchTuneState& tune_state(rbf_ctx* ctx) {
     return *(BatchTuneState*)ctx->batch_state;
 }
 
+cudaStream_t rbf_batch_stream(rbf_ctx* ctx) {
+    return ctx->batch_state ? ((BatchTuneState*)ctx->batch_state)->stream : nullptr;
+}
+
 void rbf_batch_state_free(rbf_ctx* ctx) {
     if (!ctx->batch_state) return;
     BatchTuneState* ts = (BatchTuneState*)ctx->batch_state;

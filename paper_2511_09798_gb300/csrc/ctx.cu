@@ -69,11 +69,15 @@ rbf_status rbf_lane(rbf_ctx* ctx, int i, rbf_ctx** out) {
         rbf_options o = ctx->opt;
         o.timing = 0;  // a lane's product timings go to its owner; no per-phase timers
         cudaStream_t s = nullptr;
+        int prev = 0;  // the caller's current device is restored below
+        RBF_CUDA(ctx, cudaGetDevice(&prev));
         RBF_CUDA(ctx, cudaSetDevice(ctx->device));
-        RBF_CUDA(ctx, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         rbf_ctx* l = nullptr;
-        if (rbf_create(&l, ctx->device, s, &o) != RBF_OK) {
-            cudaStreamDestroy(s);
+        const bool made = e == cudaSuccess && rbf_create(&l, ctx->device, s, &o) == RBF_OK;
+        cudaSetDevice(prev);
+        if (!made) {
+            if (s) cudaStreamDestroy(s);
             return rbf_fail(ctx, RBF_ERR_CUDA, "creating lane %d failed", i);
         }
         l->own_stream = true;
@@ -141,6 +145,15 @@ double rbf_timer_stop(rbf_ctx* ctx) {
 
 RBF_CHECK_READER(ctx)
 
+rbf_status rbf_sync_all(rbf_ctx* ctx) {
+    RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < rbf_ctx::MAX_LANES; ++i)
+        if (ctx->lane[i]) RBF_CUDA(ctx, cudaStreamSynchronize(ctx->lane[i]->stream));
+    cudaStream_t bs = rbf_batch_stream(ctx);
+    if (bs) RBF_CUDA(ctx, cudaStreamSynchronize(bs));
+    return RBF_OK;
+}
+
 rbf_status rbf_check_all(rbf_ctx* ctx) {
     struct Unit {
         const char* name;
@@ -179,8 +192,7 @@ int rbf_checked_build(void) {
 rbf_status rbf_check(rbf_ctx* ctx) {
     RbfRange range_("rbf_check");
     if (!ctx) return RBF_ERR_INVALID;
-    RBF_CUDA(ctx, cudaSetDevice(ctx->device));
-    RBF_CUDA(ctx, cudaDeviceSynchronize());  // every stream of the context, its lanes and the batch driver
+    RBF_TRY(rbf_sync_all(ctx));
     return rbf_check_all(ctx);
 }
 
@@ -244,10 +256,7 @@ rbf_status rbf_get_counters(rbf_ctx* ctx, rbf_counters* out, int reset) {
     out->reorth_launches = ctx->pcount[2];
     out->reorth_ms = 0.0;
     if (ctx->pev && ctx->pcount[2]) {
-        RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        for (int i = 0; i < rbf_ctx::MAX_LANES; ++i)
-            if (ctx->lane[i]) RBF_CUDA(ctx, cudaStreamSynchronize(ctx->lane[i]->stream));
-        if (ctx->batch_state) RBF_CUDA(ctx, cudaDeviceSynchronize());  // the batched driver's own stream
+        RBF_TRY(rbf_sync_all(ctx));
         for (int i = 0; i < ctx->pcount[2]; ++i) {
             float ms = 0.f;
             const size_t b = ((size_t)2 * rbf_ctx::PMAX + i) * 2;
@@ -256,10 +265,7 @@ rbf_status rbf_get_counters(rbf_ctx* ctx, rbf_counters* out, int reset) {
         }
     }
     if (ctx->pev && (ctx->pcount[0] || ctx->pcount[1])) {
-        RBF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        for (int i = 0; i < rbf_ctx::MAX_LANES; ++i)
-            if (ctx->lane[i]) RBF_CUDA(ctx, cudaStreamSynchronize(ctx->lane[i]->stream));
-        if (ctx->batch_state) RBF_CUDA(ctx, cudaDeviceSynchronize());
+        RBF_TRY(rbf_sync_all(ctx));
         std::vector<std::pair<double, double>> iv;
         iv.reserve((size_t)ctx->pcount[0] + ctx->pcount[1]);
         for (int t = 0; t < 2; ++t)

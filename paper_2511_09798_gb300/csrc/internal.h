@@ -77,6 +77,10 @@ struct rbf_ctx {
     int h_many_cap = 0;
 };
 void rbf_batch_state_free(rbf_ctx* ctx);
+cudaStream_t rbf_batch_stream(rbf_ctx* ctx);  // the batched driver's stream, or null
+// Wait for everything the context has enqueued: its stream, its lanes' streams
+// and the batched driver's stream.
+rbf_status rbf_sync_all(rbf_ctx* ctx);
 // Lane i of ctx (created on first use).  Errors: RBF_ERR_CUDA.
 rbf_status rbf_lane(rbf_ctx* ctx, int i, rbf_ctx** out);
 // Pinned host slots for `count` device-state copies.
