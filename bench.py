@@ -1017,8 +1017,9 @@ def forms_comparison(local_rank, count=24, L=150, m=500, reps=1):
     """Time to solution and error against the exact solution of the same
     uneven instances by each form of the method: plain FP64 HKT (assembled,
     one instance after another, and all instances on concurrent lanes), mixed
-    precision (FP32 matrix-free products, FP64 elsewhere), the batched mixed
-    form, and the batched mixed form with the learned stop (GCV fallback).
+    precision (FP32 matrix-free products, FP64 elsewhere; one after another
+    and on lanes), the batched mixed form, and the batched mixed form with the
+    learned stop (GCV fallback).
 
     Instances: the held-out draws of the learned stop's generator (cube or
     sphere, N ~ U{2000..16000}, c log-uniform in [0.05, 1], k ~ U[1, 20]) with
@@ -1093,7 +1094,14 @@ def forms_comparison(local_rank, count=24, L=150, m=500, reps=1):
             ctx.rbf_hkt(sts[b], R.RBF_GCV, 0.0, coefs[b])
             ctx.rbf_evaluate(opsm[b], coefs[b], P_d[b], m, u_d[b])
 
+    def mixed_lanes():
+        ctx.rbf_gkb_many(opsm, f_d, L, sts)
+        ctx.rbf_hkt_many(sts, R.RBF_GCV, 0.0, coefs)
+        for b in range(count):
+            ctx.rbf_evaluate(opsm[b], coefs[b], P_d[b], m, u_d[b])
+
     out["mixed_single"] = timed(mixed_serial)
+    out["mixed_lanes"] = timed(mixed_lanes)
     bt, keep = R.make_batch(torch, inst, [s_.params["c"] for s_ in inst], [s_.params["k"] for s_ in inst], fs, L, dev)
     T = int(keep["offsets"][-1])
     coef_b = torch.empty(T, dtype=torch.float64, device=dev)
