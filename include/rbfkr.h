@@ -260,8 +260,10 @@ rbf_status rbf_gkb_restore(rbf_ctx* ctx, rbf_gkb_state* st, const double* h_W, c
  * step per lane in turn, so that one run's latency-bound reorthogonalization
  * kernels overlap another run's matrix-vector products.  Each lane owns its
  * own workspace (opt.workspace_cap applies per lane) and device state.  With
- * `assemble` non-zero each assembled operator is first filled by its lane
- * (rbf_assemble), so runs must then not share a matrix buffer.  The lanes
+ * `assemble` non-zero each assembled operator is first filled (rbf_assemble;
+ * FP64 operators that differ only in k are assembled two at a time, sharing
+ * the distances, with the same entries), so runs must then not share a matrix
+ * buffer.  The lanes
  * start after the work already enqueued on the context stream, and the
  * context stream waits for all of them before later work.  Synchronises once;
  * fills every state's steps_done, breakdown and c_hat.  Errors as rbf_gkb,

@@ -61,10 +61,22 @@ __global__ void __launch_bounds__(AS_TN) k_assemble_f32(const double* __restrict
 constexpr int SY_T = 32;     // tile edge
 constexpr int SY_ROWS = 8;   // thread rows per CTA
 
+// NM operators that share the nodes and c (and so s and 1/sqrt(s)) but differ
+// in k are assembled together: Phi, 1/s and the distances once, the k-dependent
+// polynomial of L Phi per matrix (same operations, in the same order, as for
+// one matrix).
+template <int NM>
+struct AsmOut {
+    double* A[NM];
+    int64_t lda[NM];
+    double k2[NM];
+};
+
+template <int NM>
 __global__ void __launch_bounds__(SY_T * SY_ROWS) k_assemble_sym_f64(const double* __restrict__ X, int64_t n,
-                                                                      int64_t ni, double c, double k, double scale,
-                                                                      double* __restrict__ A, int64_t lda) {
-    __shared__ double tr[SY_T][SY_T + 1];
+                                                                      int64_t ni, double c, double scale,
+                                                                      AsmOut<NM> o) {
+    __shared__ double tr[NM][SY_T][SY_T + 1];
     __shared__ double pi[3][SY_T], pj[3][SY_T];
     const int bi = blockIdx.y, bj = blockIdx.x;
     if (bi > bj) return;
@@ -78,7 +90,7 @@ __global__ void __launch_bounds__(SY_T * SY_ROWS) k_assemble_sym_f64(const doubl
         }
     }
     __syncthreads();
-    const double c2 = c * c, k2 = k * k;
+    const double c2 = c * c;
     const int64_t j = J0 + tx;
     const bool jint = j < ni;
     const bool scaled = scale != 1.0;
@@ -86,21 +98,31 @@ __global__ void __launch_bounds__(SY_T * SY_ROWS) k_assemble_sym_f64(const doubl
     for (int rr = 0; rr < SY_T / SY_ROWS; ++rr) {
         const int li = ty + SY_ROWS * rr;
         const int64_t i = I0 + li;
-        double eji = 0.0;
+        double eji[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) eji[m] = 0.0;
         if (i < n && j < n) {
             const double dx = pi[0][li] - pj[0][tx], dy = pi[1][li] - pj[1][tx], dz = pi[2][li] - pj[2][tx];
             const double s = fma(dx, dx, fma(dy, dy, fma(dz, dz, c2)));
             const double rs = rsqrt_f64(s);
             const bool iint = i < ni;
-            double eij = iint ? lphi_from(s, rs, c2, k2) : s * rs;
-            eji = jint == iint ? eij : (jint ? lphi_from(s, rs, c2, k2) : s * rs);
-            if (scaled) {
-                eij *= scale;
-                eji *= scale;
+            const double phi = s * rs;
+            const bool need_l = iint || jint;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const double lp = need_l ? lphi_from(s, rs, c2, o.k2[m]) : 0.0;
+                double eij = iint ? lp : phi;
+                double e2 = jint == iint ? eij : (jint ? lp : phi);
+                if (scaled) {
+                    eij *= scale;
+                    e2 *= scale;
+                }
+                if (RBF_IN_RANGE(j, o.lda[m])) o.A[m][i * o.lda[m] + j] = eij;
+                eji[m] = e2;
             }
-            if (RBF_IN_RANGE(j, lda)) A[i * lda + j] = eij;
         }
-        tr[li][tx] = eji;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) tr[m][li][tx] = eji[m];
     }
     if (bi == bj) return;
     __syncthreads();
@@ -108,7 +130,10 @@ __global__ void __launch_bounds__(SY_T * SY_ROWS) k_assemble_sym_f64(const doubl
     for (int rr = 0; rr < SY_T / SY_ROWS; ++rr) {
         const int lj = ty + SY_ROWS * rr;
         const int64_t jr = J0 + lj, ic = I0 + tx;
-        if (jr < n && ic < n && RBF_IN_RANGE(ic, lda)) A[jr * lda + ic] = tr[tx][lj];
+        if (jr < n && ic < n)
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+                if (RBF_IN_RANGE(ic, o.lda[m])) o.A[m][jr * o.lda[m] + ic] = tr[m][tx][lj];
     }
 }
 
@@ -165,14 +190,34 @@ rbf_status launch_assemble(rbf_ctx* ctx, const rbf_operator* op) {
     if (op->precision == RBF_FP64) {
         const int64_t nt = (n + SY_T - 1) / SY_T;
         if (nt > 65535) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large for assembly grid");
-        k_assemble_sym_f64<<<dim3((unsigned)nt, (unsigned)nt), SY_T * SY_ROWS, 0, ctx->stream>>>(
-            op->d_nodes, n, op->n_interior, op->c, op->k, scale, (double*)op->d_A, op->lda);
+        AsmOut<1> o{{(double*)op->d_A}, {op->lda}, {op->k * op->k}};
+        k_assemble_sym_f64<1><<<dim3((unsigned)nt, (unsigned)nt), SY_T * SY_ROWS, 0, ctx->stream>>>(
+            op->d_nodes, n, op->n_interior, op->c, scale, o);
         RBF_LAUNCHED(ctx, "k_assemble_sym_f64");
         return RBF_OK;
     }
     k_assemble_f32<<<grid, AS_TN, 0, ctx->stream>>>(op->d_nodes, n, op->n_interior, op->c, op->k, scale,
                                                     (float*)op->d_A, op->lda);
     RBF_LAUNCHED(ctx, "k_assemble_f32");
+    return RBF_OK;
+}
+
+bool assemble_pairable(const rbf_operator* a, const rbf_operator* b) {
+    return a->storage == RBF_ASSEMBLED && b->storage == RBF_ASSEMBLED && a->precision == RBF_FP64 &&
+           b->precision == RBF_FP64 && a->d_nodes == b->d_nodes && a->n == b->n && a->n_interior == b->n_interior &&
+           a->c == b->c && a->form == b->form && a->d_A != b->d_A;
+}
+
+rbf_status launch_assemble_pair(rbf_ctx* ctx, const rbf_operator* a, const rbf_operator* b) {
+    if (!assemble_pairable(a, b)) return rbf_fail(ctx, RBF_ERR_INTERNAL, "operators cannot be assembled together");
+    const int64_t n = a->n;
+    const int64_t nt = (n + SY_T - 1) / SY_T;
+    if (nt > 65535) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large for assembly grid");
+    const double scale = a->form == RBF_FORM_EPS ? 1.0 / a->c : 1.0;
+    AsmOut<2> o{{(double*)a->d_A, (double*)b->d_A}, {a->lda, b->lda}, {a->k * a->k, b->k * b->k}};
+    k_assemble_sym_f64<2><<<dim3((unsigned)nt, (unsigned)nt), SY_T * SY_ROWS, 0, ctx->stream>>>(
+        a->d_nodes, n, a->n_interior, a->c, scale, o);
+    RBF_LAUNCHED(ctx, "k_assemble_sym_f64<2>");
     return RBF_OK;
 }
 

@@ -759,6 +759,17 @@ extern "C" rbf_status rbf_gkb_many(rbf_ctx* ctx, int count, const rbf_operator* 
     }
     ctx->lane_count = L;
     RBF_TRY(rbf_many_slots(ctx, count));
+    // operators that differ only in k are assembled two at a time on the
+    // context stream (the distances and 1/sqrt(s) computed once), before the
+    // lanes start; the others by their lane
+    std::vector<char> assembled(count, 0);
+    if (assemble)
+        for (int i = 0; i < count; ++i)
+            for (int j = i + 1; j < count && !assembled[i]; ++j)
+                if (!assembled[j] && assemble_pairable(&ops[i], &ops[j])) {
+                    RBF_TRY(launch_assemble_pair(ctx, &ops[i], &ops[j]));
+                    assembled[i] = assembled[j] = 1;
+                }
     RBF_TRY(rbf_lanes_fork(ctx, L));
     rbf_timer_start(ctx);
     std::vector<rbf_ctx*> lane(L);
@@ -787,7 +798,7 @@ extern "C" rbf_status rbf_gkb_many(rbf_ctx* ctx, int count, const rbf_operator* 
             busy = true;
             rbf_ctx* c = lane[l];
             if (jnext[l] == 0) {
-                if (assemble && ops[i].storage == RBF_ASSEMBLED) err = launch_assemble(c, &ops[i]);
+                if (assemble && ops[i].storage == RBF_ASSEMBLED && !assembled[i]) err = launch_assemble(c, &ops[i]);
                 if (err == RBF_OK) err = run[i].begin(c, &ops[i], d_f[i], 1, &states[i]);
                 jnext[l] = 1;
             }

@@ -158,6 +158,11 @@ double rbf_timer_stop(rbf_ctx* ctx);  // ms, synchronises when timing is on
 // ---- launchers (one per translation unit family) ------------------------------
 // assemble.cu
 rbf_status launch_assemble(rbf_ctx* ctx, const rbf_operator* op);
+// Two FP64 assembled operators on the same nodes, n_interior, c and form (k may
+// differ) into distinct matrices, in one pass; entries bitwise equal to two
+// launch_assemble calls.
+bool assemble_pairable(const rbf_operator* a, const rbf_operator* b);
+rbf_status launch_assemble_pair(rbf_ctx* ctx, const rbf_operator* a, const rbf_operator* b);
 rbf_status launch_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* coef,
                            const double* pts, int64_t m, double* u);
 // gemv.cu

@@ -97,6 +97,51 @@ def test_gkb_many_equals_single_runs(R, lanes, assemble):
     ctx.close()
 
 
+def test_many_pair_assembly_of_operators_sharing_nodes(R):
+    """FP64 operators on one node array with one c and form, differing in k, are
+    assembled two at a time by rbf_gkb_many: every matrix equals its own
+    rbf_assemble bitwise (both forms, an odd operator left over, a mixed one
+    not paired), and so do the GKB runs."""
+    ns = w.cube_faces_random(700, 0.3, np.random.Generator(np.random.PCG64(91)))
+    nodes = torch.as_tensor(ns.soa(), device="cuda")
+    specs = [(R.RBF_FP64, R.RBF_FORM_C, 2.0), (R.RBF_MIXED, R.RBF_FORM_C, 3.0), (R.RBF_FP64, R.RBF_FORM_C, 5.0),
+             (R.RBF_FP64, R.RBF_FORM_EPS, 2.0), (R.RBF_FP64, R.RBF_FORM_C, 3.5), (R.RBF_FP64, R.RBF_FORM_EPS, 4.0)]
+    steps = 12
+    ctx = R.Context(0)
+
+    def make(fill):
+        ops, mats = [], []
+        for prec, form, k in specs:
+            lda = R.padded_lda(ns.n, prec)
+            dt = torch.float64 if prec == R.RBF_FP64 else torch.float32
+            A = torch.full((ns.n, lda), float("nan"), dtype=dt, device="cuda")
+            op = ctx.rbf_operator_init(nodes, ns.n, ns.n_interior, 0.3, k, R.RBF_ASSEMBLED, prec, form, A, lda)
+            if fill:
+                ctx.rbf_assemble(op)
+            ops.append(op)
+            mats.append(A)
+        return ops, mats
+    ops1, mats1 = make(True)
+    ops2, mats2 = make(False)
+    fs = [torch.as_tensor(w.plane_wave_rhs(ns, k), device="cuda") for _, _, k in specs]
+    ref = []
+    for op, f in zip(ops1, fs):
+        st, W, Z, al, be = R.make_state(torch, ns.n, steps)
+        ctx.rbf_gkb(op, f, steps, st)
+        ref.append((W, al))
+    states, bufs = [], []
+    for _ in specs:
+        st, *b = R.make_state(torch, ns.n, steps)
+        states.append(st)
+        bufs.append(b)
+    ctx.rbf_gkb_many(ops2, fs, steps, states, lanes=2, assemble=True)
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        assert torch.equal(mats2[i][:, :ns.n], mats1[i][:, :ns.n]), i
+        assert torch.equal(bufs[i][0], ref[i][0]) and torch.equal(bufs[i][2], ref[i][1]), i
+    ctx.close()
+
+
 def test_many_busy_time_and_counts(R):
     """Product timing with lanes: the union of the launch intervals never exceeds
     their sum, and every product launch is counted."""
