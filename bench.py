@@ -285,7 +285,16 @@ def run_ours(args, rank, world, local_rank):
     ops = [ctx.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, storage, prec, R.RBF_FORM_C, Ac,
                                  lda if Ac is not None else 0) for (c, k), Ac in zip(cases, mats)]
     states = [R.make_state(torch, n, L, dev)[0] for _ in cases]
-    coefs = [torch.empty(n, dtype=torch.float64, device=dev) for _ in cases]
+    coef_all = torch.empty((len(cases), n), dtype=torch.float64, device=dev)
+    coefs = list(coef_all)
+    # consecutive cases with the same c share Phi(P, X) (it does not depend on
+    # k): their reconstructions are one rbf_evaluate_many call
+    ev_groups = []
+    for ci, (c_, _) in enumerate(cases):
+        if ev_groups and cases[ev_groups[-1][0]][0] == c_:
+            ev_groups[-1][1] += 1
+        else:
+            ev_groups.append([ci, 1])
     fs_case = [f_d[k] for _, k in cases]
     A = mats[0]
     st = states[0]
@@ -304,8 +313,8 @@ def run_ours(args, rank, world, local_rank):
         # (Algorithm 4, GCV) and the reconstructions
         ctx.rbf_gkb_many(ops, fs_case, L, states, lanes=args.lanes, assemble=storage == R.RBF_ASSEMBLED)
         last_infos[:] = ctx.rbf_hkt_many(states, R.RBF_GCV, 0.0, coefs, lanes=args.lanes)
-        for ci in range(len(cases)):
-            ctx.rbf_evaluate(ops[ci], coefs[ci], pts_d, m, u_d[ci])
+        for c0, cnt in ev_groups:
+            ctx.rbf_evaluate_many(ops[c0], coef_all[c0], n, cnt, pts_d, m, u_d[c0])
         if e2e:
             u_h.copy_(u_d, non_blocking=True)
         return sum(s_.steps_done for s_ in states)

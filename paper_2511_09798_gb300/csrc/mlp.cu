@@ -259,7 +259,10 @@ __global__ void k_stop_features_batch(const double* __restrict__ alpha, const do
 
 // u[c][t] = sum_j coef[c][j] Phi(|P_t - X_j|) for 8 coefficient vectors per
 // grid.z slice (partials over centre chunks in grid.y).
-constexpr int EM_T = 128, EM_C = 8;
+// EM_C coefficient vectors per CTA share each Phi(|P_t - X_j|): 12 FP64-pipe
+// operations for Phi plus one FMA per vector.
+constexpr int EM_T = 128;
+template <int EM_C>
 __global__ void __launch_bounds__(EM_T) k_evaluate_many(const double* __restrict__ X, int64_t n,
                                                        const double* __restrict__ coefs, int64_t ldc, int ncoef,
                                                        const double* __restrict__ Pts, int64_t m, double c,
@@ -425,7 +428,9 @@ extern "C" rbf_status rbf_evaluate_many(rbf_ctx* ctx, const rbf_operator* op, co
         return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_evaluate_many: bad argument");
     const int64_t n = op->n;
     const int64_t tiles = (m + EM_T - 1) / EM_T;
-    const int zs = (ncoef + EM_C - 1) / EM_C;
+    // vectors per CTA: the smallest of 1, 2, 4, 8 that holds them all (8 beyond)
+    const int em_c = ncoef <= 1 ? 1 : ncoef <= 2 ? 2 : ncoef <= 4 ? 4 : 8;
+    const int zs = (ncoef + em_c - 1) / em_c;
     int64_t chunks = ((int64_t)ctx->sm_count * 8 + tiles * zs - 1) / (tiles * zs);
     if (chunks < 1) chunks = 1;
     if ((n + chunks - 1) / chunks < 256) chunks = (n + 255) / 256;
@@ -436,8 +441,19 @@ extern "C" rbf_status rbf_evaluate_many(rbf_ctx* ctx, const rbf_operator* op, co
     RBF_TRY(rbf_ws_reserve(ctx, ws_align((size_t)chunks * total * 8)));
     double* part = (double*)ctx->ws;
     const double scale = op->form == RBF_FORM_EPS ? 1.0 / op->c : 1.0;
-    k_evaluate_many<<<dim3((unsigned)tiles, (unsigned)chunks, (unsigned)zs), EM_T, 0, ctx->stream>>>(
-        op->d_nodes, n, d_coefs, ldc, ncoef, d_points, m, op->c, scale, chunk, part);
+    const dim3 grid((unsigned)tiles, (unsigned)chunks, (unsigned)zs);
+    if (em_c == 1)
+        k_evaluate_many<1><<<grid, EM_T, 0, ctx->stream>>>(op->d_nodes, n, d_coefs, ldc, ncoef, d_points, m, op->c,
+                                                           scale, chunk, part);
+    else if (em_c == 2)
+        k_evaluate_many<2><<<grid, EM_T, 0, ctx->stream>>>(op->d_nodes, n, d_coefs, ldc, ncoef, d_points, m, op->c,
+                                                           scale, chunk, part);
+    else if (em_c == 4)
+        k_evaluate_many<4><<<grid, EM_T, 0, ctx->stream>>>(op->d_nodes, n, d_coefs, ldc, ncoef, d_points, m, op->c,
+                                                           scale, chunk, part);
+    else
+        k_evaluate_many<8><<<grid, EM_T, 0, ctx->stream>>>(op->d_nodes, n, d_coefs, ldc, ncoef, d_points, m, op->c,
+                                                           scale, chunk, part);
     RBF_LAUNCHED(ctx, "k_evaluate_many");
     k_reduce_many<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(part, (int)chunks, total, d_u);
     RBF_LAUNCHED(ctx, "k_reduce_many");

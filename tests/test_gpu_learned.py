@@ -193,6 +193,31 @@ def test_evaluate_many_and_error_table_match_oracle(ctx, R):
     assert np.all(np.abs(E - ref) <= tol * np.maximum(ref, 1e-3)), np.max(np.abs(E - ref) / ref)
 
 
+@pytest.mark.parametrize("ncoef", [1, 2, 3, 5, 11])
+def test_evaluate_many_vector_counts(ctx, R, ncoef):
+    """1, 2, 4 or 8 vectors per CTA (3, 5 and 11 leave a group part empty):
+    every row equals the oracle's reconstruction and the single-vector call."""
+    ns, f, c, k = _fp64_problem(n=389, seed=17)
+    nodes = _dev(ns.soa())
+    op = ctx.rbf_operator_init(nodes, ns.n, ns.n_interior, c, k, R.RBF_MATRIX_FREE, R.RBF_FP64, R.RBF_FORM_EPS)
+    rng = np.random.default_rng(ncoef)
+    ldc = ns.n + 3
+    Cf = rng.normal(size=(ncoef, ldc))
+    P = w.test_points(ns, 211)
+    m = P.shape[0]
+    U = torch.empty((ncoef, m), dtype=torch.float64, device="cuda")
+    ctx.rbf_evaluate_many(op, _dev(Cf), ldc, ncoef, _dev(P.T), m, U)
+    Phi = OM.phi(OM.distances(P, ns.X), c) / c  # eps form scales by 1/c
+    ref = Cf[:, :ns.n] @ Phi.T
+    Ug = U.cpu().numpy()
+    scale = np.abs(Cf[:, :ns.n]) @ np.abs(Phi.T)
+    assert np.all(np.abs(Ug - ref) <= 1e-13 * scale), np.max(np.abs(Ug - ref) / scale)
+    u1 = torch.empty(m, dtype=torch.float64, device="cuda")
+    for i in sorted({0, ncoef - 1}):
+        ctx.rbf_evaluate(op, _dev(np.ascontiguousarray(Cf[i, :ns.n])), _dev(P.T), m, u1)
+        assert np.all(np.abs(Ug[i] - u1.cpu().numpy()) <= 1e-13 * scale[i])
+
+
 def _constant_net(R, l_target, t_target, **kw):
     """A network whose output is exactly its last bias: W3 = 0 (the rest
     random), so the prediction is known: l = l_target, t = t_target."""
