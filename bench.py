@@ -73,9 +73,23 @@ def mf_ops_per_entry(n, n_interior):
     return (n_interior * 11 + (n - n_interior) * 8) / n
 
 
-def mf_roofline(n, n_interior, avg_ms):
+def mf_pair_ops(n, n_interior):
+    """FP32 pipe operations of one single-instance matrix-free product, which
+    evaluates each unordered node pair once (s = |X_i - X_j|^2 + c^2 and its
+    rsqrt are shared by A_ij and A_ji): 3 differences and 3 FMA for s, the
+    entry factors the two row types need (PDE: rs^2, two FMA, one multiply;
+    Dirichlet: rs s; a mixed pair both) and two accumulate FMA; the diagonal
+    entries one accumulate each.  The rsqrt goes to the MUFU unit."""
+    ni, nb = n_interior, n - n_interior
+    return (12 * ni * (ni - 1) / 2 + 9 * nb * (nb - 1) / 2 + 13 * ni * nb + 11 * ni + 8 * nb)
+
+
+def mf_roofline(n, n_interior, avg_ms, pairs=True):
+    """Roofline of the FP32 matrix-free product: `pairs` for the single-instance
+    tile-pair kernel (mf_pair_ops), else one evaluation per entry (the batched
+    kernel, mf_ops_per_entry)."""
     ent = n * n / (avg_ms / 1e3)
-    ops = mf_ops_per_entry(n, n_interior)
+    ops = mf_pair_ops(n, n_interior) / (n * n) if pairs else mf_ops_per_entry(n, n_interior)
     tops = ent * ops / 1e12
     return {"bound": "alu", "achieved": round(tops, 3), "peak": round(FP32_LANE_TOPS, 3),
             "unit": "T FP32-pipe ops/s", "frac": round(tops / FP32_LANE_TOPS, 4), "traffic": None,
@@ -409,7 +423,9 @@ def run_ours(args, rank, world, local_rank):
     else:
         roof = mf_roofline(n, ns.n_interior, avg_ms)
     roof["traffic"] = MEASURED_TRAFFIC.get((wl["name"], dom))
-    roof.update({"kernel": "gemv_n (p = A z) and gemv_t (r = A^T w)", "avg_launch_ms": round(avg_ms, 5),
+    kname = ("gemv_n (p = A z) and gemv_t (r = A^T w)" if storage == R.RBF_ASSEMBLED
+             else ("k_mf_partial_f64" if prec == R.RBF_FP64 else "k_mf_sym") + " (p = A z, r = A^T w, matrix-free)")
+    roof.update({"kernel": kname, "avg_launch_ms": round(avg_ms, 5),
                  "avg_launch_ms_how": "union of the product launch intervals / launches (CUDA events on the "
                                       "launching streams, timed region)",
                  "avg_launch_ms_events": round(both_avg_ms, 5), "launches_timed": int(p_cnt[0] + p_cnt[1]),
@@ -982,8 +998,8 @@ def mf_product_roofline(local_rank, pairs=10):
     coordinates) on the 20 000-node sphere (c = 0.15, k = 10): CUDA-event
     time of `pairs` A x / A^T x pairs through rbf_matvec after two warm-up
     pairs, as regenerated entries per second and a fraction of the FP32 pipe
-    (11 FP32-pipe operations per PDE entry, 8 per Dirichlet entry, the MUFU
-    rsqrt beside them)."""
+    (the operations of mf_pair_ops: each node pair evaluated once for A_ij and
+    A_ji, the MUFU rsqrt beside them)."""
     import numpy as np
     import torch
 
@@ -1015,7 +1031,7 @@ def mf_product_roofline(local_rank, pairs=10):
     ctx.close()
     ms = e0.elapsed_time(e1) / (2 * pairs)
     roof = mf_roofline(n, ns.n_interior, ms)
-    roof.update({"kernel": "k_mf_partial (FP32 matrix-free product, sphere20000)", "avg_launch_ms": round(ms, 5),
+    roof.update({"kernel": "k_mf_sym (FP32 matrix-free product, sphere20000)", "avg_launch_ms": round(ms, 5),
                  "timing": f"{pairs} A x / A^T x pairs through rbf_matvec (the product, the partial-sum "
                            f"reduction and one vector normalisation per pair), CUDA events"})
     return roof

@@ -418,12 +418,17 @@ extern "C" rbf_status rbf_matvec(rbf_ctx* ctx, const rbf_operator* op, int trans
     if (!op || !d_x || !d_y) return rbf_fail(ctx, RBF_ERR_INVALID, "rbf_matvec: NULL argument");
     const int64_t n = op->n;
     if (op->storage == RBF_MATRIX_FREE) {
-        RBF_TRY(rbf_ws_reserve(ctx, mf_ws_bytes(ctx, n) + ws_align((size_t)n * sizeof(float))));
+        RBF_TRY(rbf_ws_reserve(ctx, mf_ws_bytes(ctx, n) + ws_align((size_t)n * sizeof(float)) +
+                                        ws_align((size_t)3 * n * sizeof(float))));
         WsCarve wc(ctx->ws);
         float* x32 = wc.take<float>((size_t)n);
-        double* part = wc.take<double>((size_t)mf_chunks(ctx, op) * n);
-        if (op->precision == RBF_MIXED) RBF_TRY(launch_to_f32(ctx, n, d_x, x32));
-        RBF_TRY(launch_mf_partial(ctx, op, trans, d_x, x32, part, nullptr));
+        float* X32 = wc.take<float>((size_t)3 * n);
+        double* part = wc.take<double>((size_t)mf_part_rows(ctx, op) * n);
+        if (op->precision == RBF_MIXED) {
+            RBF_TRY(launch_to_f32(ctx, n, d_x, x32));
+            RBF_TRY(launch_to_f32(ctx, 3 * n, op->d_nodes, X32));
+        }
+        RBF_TRY(launch_mf_partial(ctx, op, trans, d_x, x32, X32, part, nullptr));
         return launch_reduce_partials(ctx, n, mf_chunks(ctx, op), part, d_y);
     }
     RBF_TRY(rbf_ws_reserve(ctx, gemv_ws_bytes(ctx, n)));

@@ -461,9 +461,11 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
     (void)precision;
     rbf_operator fake{};
     fake.n = n;
-    fake.precision = RBF_MIXED;
     fake.storage = RBF_MATRIX_FREE;
-    int ch = mf_chunks(ctx, &fake);
+    fake.precision = RBF_MIXED;
+    int ch = mf_part_rows(ctx, &fake);
+    fake.precision = RBF_FP64;
+    ch = std::max(ch, mf_part_rows(ctx, &fake));
     fake.storage = RBF_ASSEMBLED;
     for (int prec : {RBF_MIXED, RBF_FP64}) {  // the assembled products' partial-sum rows
         fake.precision = prec;
@@ -474,6 +476,7 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
     b += ws_align((size_t)ch * n * 8);                // partials
     b += 2 * ws_align((size_t)n * 8);                 // vr, vp
     b += 2 * ws_align((size_t)n * 4);                 // vr32, vp32
+    b += ws_align((size_t)3 * n * 4);                 // FP32 node coordinates (matrix-free FP32)
     b += ws_align((size_t)(steps + 2) * G * 8);       // hpart
     b += ws_align((size_t)2 * (steps + 2) * G * 8);   // gpart (two buffers, at most G groups)
     b += ws_align((size_t)(G + 2) * BAR_STRIDE * 4);  // barrier counters
@@ -483,10 +486,10 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
 
 // Launch the product "part = M q_raw" for one half-step.
 static rbf_status gkb_product(rbf_ctx* ctx, const rbf_operator* op, int trans, const double* q_raw,
-                              const float* q32, double* part, const int* done) {
+                              const float* q32, const float* X32, double* part, const int* done) {
     const int slot = rbf_prod_begin(ctx, trans);
     rbf_status st;
-    if (op->storage == RBF_MATRIX_FREE) st = launch_mf_partial(ctx, op, trans, q_raw, q32, part, done);
+    if (op->storage == RBF_MATRIX_FREE) st = launch_mf_partial(ctx, op, trans, q_raw, q32, X32, part, done);
     else if (trans) st = launch_gemv_t_partial(ctx, op, q_raw, q32, part, done);
     else st = launch_gemv_n(ctx, op, q_raw, q32, part, done);
     rbf_prod_end(ctx, trans, slot);
@@ -505,7 +508,7 @@ struct GkbRun {
     int64_t n = 0;
     int G = 0, chT = 0, chN = 0, rmax = 0, bar_group = 0, bar_k = 0, j_begin = 1;
     double *part = nullptr, *vr = nullptr, *vp = nullptr, *hpart = nullptr, *gpart = nullptr, *npart = nullptr;
-    float *vr32 = nullptr, *vp32 = nullptr;
+    float *vr32 = nullptr, *vp32 = nullptr, *X32 = nullptr;  // X32: FP32 node coordinates (matrix-free FP32)
     unsigned* bar = nullptr;
     const double* q_raw = nullptr;
     unsigned epochs = 0;  // barriers on `bar` since it was zeroed
@@ -524,11 +527,16 @@ struct GkbRun {
         WsCarve wc(ctx->ws);
         chT = product_chunks(ctx, op, 1);
         chN = product_chunks(ctx, op, 0);
-        part = wc.take<double>((size_t)(chT > chN ? chT : chN) * n);
+        const int prow = op->storage == RBF_MATRIX_FREE ? mf_part_rows(ctx, op) : 0;
+        part = wc.take<double>((size_t)std::max(prow, std::max(chT, chN)) * n);
         vr = wc.take<double>((size_t)n);
         vp = wc.take<double>((size_t)n);
         vr32 = wc.take<float>((size_t)n);
         vp32 = wc.take<float>((size_t)n);
+        if (op->storage == RBF_MATRIX_FREE && op->precision != RBF_FP64) {
+            X32 = wc.take<float>((size_t)3 * n);
+            RBF_TRY(launch_to_f32(ctx, 3 * n, op->d_nodes, X32));
+        }
         hpart = wc.take<double>((size_t)(st->capacity + 2) * G);
         bar_group = 1;
         while (bar_group * bar_group < G) ++bar_group;
@@ -630,11 +638,11 @@ struct GkbRun {
         double* Z = st->d_Z;
         const int64_t ldw = st->ldw, ldz = st->ldz;
         // ---------------- r-side: r = A^T w_j - beta_j z_{j-1} ----------------
-        RBF_TRY(gkb_product(ctx, op, 1, q_raw, vp32, part, done));
+        RBF_TRY(gkb_product(ctx, op, 1, q_raw, vp32, X32, part, done));
         RBF_TRY(half(0, j, (j == j_begin && j_begin > 1) ? 1 : 0, j >= 2 ? Z + (int64_t)(j - 2) * ldz : nullptr,
                      q_raw, W + (int64_t)(j - 1) * ldw, vr, mixed ? vr32 : nullptr, Z, ldz, j - 1, chT));
         // ---------------- p-side: p = A z_j - alpha_j w_j ----------------
-        RBF_TRY(gkb_product(ctx, op, 0, vr, vr32, part, done));
+        RBF_TRY(gkb_product(ctx, op, 0, vr, vr32, X32, part, done));
         RBF_TRY(half(1, j, 0, W + (int64_t)(j - 1) * ldw, vr, Z + (int64_t)(j - 1) * ldz, vp,
                      mixed ? vp32 : nullptr, W, ldw, j, chN));
         q_raw = vp;

@@ -178,10 +178,15 @@ rbf_status launch_gemv_t_partial(rbf_ctx* ctx, const rbf_operator* op, const dou
                                  const float* x32, double* part, const int* done);
 rbf_status launch_reduce_partials(rbf_ctx* ctx, int64_t n, int chunks, const double* part, double* y);
 // mf.cu (matrix-free products, FP32 or FP64; partial sums over `mf_chunks` centre chunks)
+// Partial rows the consumer sums (mf_chunks) and rows the product writes
+// (mf_part_rows >= mf_chunks; the FP32 tile-pair product folds its slots).
 int mf_chunks(const rbf_ctx* ctx, const rbf_operator* op);
+int mf_part_rows(const rbf_ctx* ctx, const rbf_operator* op);
 size_t mf_ws_bytes(const rbf_ctx* ctx, int64_t n);
+// x: FP64 input (FP64 operators); x32 and X32 (the node coordinates, SoA
+// [3][n], rounded to FP32): inputs of FP32 operators.
 rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, const double* x,
-                             const float* x32, double* part, const int* done);  // x (FP64 op) or x32
+                             const float* x32, const float* X32, double* part, const int* done);  // x (FP64 op) or x32
 // gkb.cu
 rbf_status gkb_run(rbf_ctx* ctx, const rbf_operator* op, const double* f, int j_begin, int j_end,
                    rbf_gkb_state* st);

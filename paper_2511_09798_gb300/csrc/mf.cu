@@ -1,115 +1,244 @@
-// Matrix-free FP32 products with the collocation matrix (mixed precision).
+// Matrix-free products with the collocation matrix.
 //
-// Entry (i, j) is regenerated from the node coordinates on every product (the
-// entry formula and the packed f32x2 inner loop are in mf_core.cuh).  Each
-// thread keeps MF_R outputs (coordinates, row coefficients and FP64
-// accumulators) in registers and streams the summation nodes through shared
-// memory; products of one shared tile are summed in FP32 and the tile sum is
-// added into the FP64 accumulator.  The summation range is split into chunks
-// (grid.y) whose partial sums are reduced deterministically by the consumer.
-//   trans = 0: y = A x,   outputs are rows i,    summation over centres j
-//   trans = 1: y = A^T x, outputs are centres j, summation over rows i
+// FP32 entries (mixed precision): tile pairs.  Rows and columns of A are the
+// same node list, s_ij = |X_i - X_j|^2 + c^2 = s_ji, and an entry depends on
+// its row's type only (L Phi for PDE rows, Phi for Dirichlet rows), so the
+// PDE x PDE and Dirichlet x Dirichlet blocks are symmetric.  The nodes are cut
+// into nb blocks of B; CTA (I, J), I < J, evaluates s and s^{-1/2} once per
+// node pair (i in I, j in J) and feeds both A_ij and A_ji (one value when the
+// two rows have the same type): y_i += A_ij x_j and y_j += A_ji x_i for y = A x,
+// the mirror for y = A^T x.  Diagonal tiles (I == I) take every ordered pair
+// once.  Partial sums: the contributions of tile (I, J) to the outputs of block
+// I go to slot J, those to the outputs of block J to slot I, so every output
+// receives exactly one value in each of the nb slots and the consumer sums
+// the slots in a fixed order (deterministic, no atomics).
+//
+// Inside a CTA the tile's rows sit in registers (R per lane, f32x2 pairs) and
+// its four warps split the columns; a warp stages 32 columns in shared memory
+// and runs over them together (one broadcast read per column).  The column
+// sums (A_ji x_i over the warp's rows) leave each step as one FP32 value per
+// lane and are added over the lanes through a padded shared array after 32
+// columns.  FP32 runs: a row sum covers the B <= 256 columns of the tile, a
+// column sum its B rows; each then goes to FP64 (the node coordinates come
+// rounded to FP32 from the caller, converted once per GKB run).
+//
+// FP64 operators: one output per thread, summation nodes streamed through
+// shared memory in chunks (grid.y), partials per chunk.
+//   trans = 0: y = A x,   trans = 1: y = A^T x
+#include <cmath>
+
 #include "common.cuh"
 #include "internal.h"
 #include "mf_core.cuh"
 
 namespace {
 
-constexpr int MF_T = 128;   // threads per CTA
-constexpr int MF_R = 4;     // outputs per thread (two f32x2 pairs)
-constexpr int MF_S = 256;   // summation nodes per shared tile
-constexpr int MF_OUT = MF_T * MF_R;
-constexpr int MF_MIN_CTAS = 8;  // resident CTAs per SM the register budget is held to
+// ---- FP32 tile-pair kernel ----
+constexpr int MS_W = 4;                          // warps per CTA, splitting the tile's columns
+enum { MS_INT = 0, MS_BND = 1, MS_MIX = 2 };     // row / column type of a range of nodes
 
-template <int TRANS>
-__global__ void __launch_bounds__(MF_T, MF_MIN_CTAS) k_mf_partial(const double* __restrict__ X, int64_t n,
-                                                     int64_t ni, float c2, float k2, double scale,
-                                                     const float* __restrict__ x32, int64_t chunk,
-                                                     double* __restrict__ part,
-                                                     const int* __restrict__ done) {
+__device__ __forceinline__ int ms_type(int64_t lo, int64_t hi, int64_t ni) {
+    return hi <= ni ? MS_INT : (lo >= ni ? MS_BND : MS_MIX);
+}
+
+// Tile t of the nb (nb + 1) / 2 tiles (I, J), I <= J.  The FP32 square root
+// estimates the row; the integer loops correct it (the FP64 pipe is slow).
+__device__ __forceinline__ void ms_tile(int64_t t, int64_t nb, int64_t& I, int64_t& J) {
+    const int64_t u = nb * (nb + 1) / 2 - 1 - t;
+    int64_t r = (int64_t)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+    if (r < 0) r = 0;
+    while ((r + 1) * (r + 2) / 2 <= u) ++r;
+    while (r > 0 && r * (r + 1) / 2 > u) --r;
+    I = nb - 1 - r;
+    J = nb - 1 - (u - r * (r + 1) / 2);
+}
+
+// 32 staged columns against the lane's NP row pairs.  Entries of the row's
+// type: eR; of the column's type: eC.  The own side (outputs = the lane's rows)
+// takes T=0: A_ij = eR, T=1: A_ji = eC, times x_j; with SYM the other side
+// (outputs = the columns) takes the other one times x_i, summed over the
+// lane's rows into colpart[q][lane].
+template <int TRANS, bool SYM, int RT, int CT, int NP>
+__device__ __forceinline__ void ms_cols(const MfNode* __restrict__ cols, float (*colpart)[33], int lane,
+                                        const f2_t* OX, const f2_t* OY, const f2_t* OZ, const f2_t* XI,
+                                        unsigned imask, f2_t C2, f2_t K2, f2_t TWO, int64_t cb, int64_t ni,
+                                        f2_t* T) {
+    constexpr bool useR = SYM || TRANS == 0;
+    constexpr bool useC = SYM || TRANS == 1;
+    constexpr bool needL = (useR && RT != MS_BND) || (useC && CT != MS_BND);
+    constexpr bool needP = (useR && RT != MS_INT) || (useC && CT != MS_INT);
+#pragma unroll 2
+    for (int q = 0; q < 32; ++q) {
+        const MfNode nd = cols[q];
+        const bool cint = CT == MS_INT || (CT == MS_MIX && cb + q < ni);
+        f2_t CA = 0ull;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const f2_t dx = f2_sub(OX[p], nd.xx);
+            const f2_t dy = f2_sub(OY[p], nd.yy);
+            const f2_t dz = f2_sub(OZ[p], nd.zz);
+            f2_t s = f2_fma(dz, dz, C2);
+            s = f2_fma(dy, dy, s);
+            s = f2_fma(dx, dx, s);
+            float s0, s1;
+            f2_unpack(s, s0, s1);
+            const f2_t rs = f2_pack(mf_rsqrt(s0), mf_rsqrt(s1));
+            f2_t eL = 0ull, eP = 0ull, eR;
+            if constexpr (needL) eL = f2_mul(rs, f2_fma(C2, f2_mul(rs, rs), f2_fma(K2, s, TWO)));
+            if constexpr (needP) eP = f2_mul(rs, s);
+            if constexpr (RT == MS_MIX) {  // bit 2p + h of imask: row 2p + h is a PDE row
+                float l0, l1, p0, p1;
+                f2_unpack(eL, l0, l1);
+                f2_unpack(eP, p0, p1);
+                eR = f2_pack((imask >> (2 * p)) & 1u ? l0 : p0, (imask >> (2 * p + 1)) & 1u ? l1 : p1);
+            } else {
+                eR = RT == MS_INT ? eL : eP;
+            }
+            const f2_t eC = cint ? eL : eP;
+            T[p] = f2_fma(TRANS == 0 ? eR : eC, nd.ww, T[p]);
+            if constexpr (SYM) CA = p == 0 ? f2_mul(TRANS == 0 ? eC : eR, XI[p]) : f2_fma(TRANS == 0 ? eC : eR, XI[p], CA);
+        }
+        if constexpr (SYM) {
+            float lo, hi;
+            f2_unpack(CA, lo, hi);
+            colpart[q][lane] = lo + hi;
+        }
+    }
+}
+
+template <int TRANS, bool SYM, int NP>
+__device__ __forceinline__ void ms_dispatch(int rt, int ct, const MfNode* cols, float (*colpart)[33], int lane,
+                                            const f2_t* OX, const f2_t* OY, const f2_t* OZ, const f2_t* XI,
+                                            unsigned imask, f2_t C2, f2_t K2, f2_t TWO, int64_t cb, int64_t ni,
+                                            f2_t* T) {
+    // without SYM only one of the two types matters
+    if (!SYM && TRANS == 0) ct = MS_INT;
+    if (!SYM && TRANS == 1) rt = MS_INT;
+#define MS_CASE(R_, C_)                                                                                        \
+    case R_ * 3 + C_:                                                                                          \
+        ms_cols<TRANS, SYM, R_, C_, NP>(cols, colpart, lane, OX, OY, OZ, XI, imask, C2, K2, TWO, cb, ni, T);    \
+        break;
+    switch (rt * 3 + ct) {
+        MS_CASE(MS_INT, MS_INT)
+        MS_CASE(MS_INT, MS_BND)
+        MS_CASE(MS_INT, MS_MIX)
+        MS_CASE(MS_BND, MS_INT)
+        MS_CASE(MS_BND, MS_BND)
+        MS_CASE(MS_BND, MS_MIX)
+        MS_CASE(MS_MIX, MS_INT)
+        MS_CASE(MS_MIX, MS_BND)
+        MS_CASE(MS_MIX, MS_MIX)
+        default: break;
+    }
+#undef MS_CASE
+}
+
+// One tile (I, J) per CTA; rows I*B + lane + 32 r (r < R), B = 32 R.
+template <int TRANS, int R>
+__global__ void __launch_bounds__(MS_W * 32) k_mf_sym(const float* __restrict__ X, int64_t n, int64_t ni, float c2,
+                                                    float k2, double scale, const float* __restrict__ x32,
+                                                    int64_t nb, double* __restrict__ part,
+                                                    const int* __restrict__ done) {
     if (gkb_done(done)) return;
-    constexpr int NP = MF_R / 2;
-    __shared__ MfNode tile[MF_S];
-    const int64_t obase = (int64_t)blockIdx.x * MF_OUT;
-    f2_t OX[NP], OY[NP], OZ[NP], A0[NP], A1[NP], A2[NP];
-    double acc[MF_R];
+    constexpr int NP = R / 2, B = 32 * R, CW = B / MS_W;  // CW columns per warp
+    static_assert(CW % 32 == 0, "a warp takes whole groups of 32 columns");
+    __shared__ MfNode cols[MS_W][32];
+    __shared__ float colpart[MS_W][32][33];
+    __shared__ float own[MS_W][R][32];
+    int64_t I, J;
+    ms_tile(blockIdx.x, nb, I, J);
+    const bool sym = I != J;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = I * B, col0 = J * B;
+    const int rt = ms_type(row0, row0 + B, ni);
+    f2_t OX[NP], OY[NP], OZ[NP], XI[NP], T[NP];
+    unsigned imask = 0;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        float cx[2], cy[2], cz[2], e0[2], e1[2], e2[2];
+        float cx[2], cy[2], cz[2], xv[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int64_t o = obase + threadIdx.x + (2 * p + h) * MF_T;
-            const bool ok = o < n;
-            cx[h] = ok ? (float)X[o] : 0.f;
-            cy[h] = ok ? (float)X[n + o] : 0.f;
-            cz[h] = ok ? (float)X[2 * n + o] : 0.f;
-            const bool interior = TRANS == 0 && o < ni;
-            e0[h] = interior ? c2 : 0.f;
-            e1[h] = interior ? 2.f : 0.f;
-            e2[h] = interior ? k2 : 1.f;
+            const int64_t i = row0 + lane + 32 * (2 * p + h);
+            const bool ok = i < n;
+            cx[h] = ok ? X[i] : 0.f;
+            cy[h] = ok ? X[n + i] : 0.f;
+            cz[h] = ok ? X[2 * n + i] : 0.f;
+            xv[h] = ok ? x32[i] : 0.f;
+            if (i < ni) imask |= 1u << (2 * p + h);
         }
         OX[p] = f2_pack(cx[0], cx[1]);
         OY[p] = f2_pack(cy[0], cy[1]);
         OZ[p] = f2_pack(cz[0], cz[1]);
-        A0[p] = f2_pack(e0[0], e0[1]);
-        A1[p] = f2_pack(e1[0], e1[1]);
-        A2[p] = f2_pack(e2[0], e2[1]);
-        acc[2 * p] = acc[2 * p + 1] = 0.0;
+        XI[p] = f2_pack(xv[0], xv[1]);
+        T[p] = 0ull;
     }
-    const f2_t C2 = f2_pack(c2, c2);
-    const int64_t s0 = (int64_t)blockIdx.y * chunk;
-    const int64_t s1 = min(n, s0 + chunk);
-    // For trans = 1 the row type follows the summation index: split at ni.
-    for (int seg = 0; seg < (TRANS ? 2 : 1); ++seg) {
-        int64_t lo = s0, hi = s1;
-        bool bnd = obase >= ni;  // trans = 0: every output row is a Dirichlet row
-        if (TRANS) {
-            if (seg == 0) {
-                hi = min(s1, ni);
-                bnd = false;
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    A0[p] = C2;
-                    A1[p] = f2_pack(2.f, 2.f);
-                    A2[p] = f2_pack(k2, k2);
-                }
-            } else {
-                lo = max(s0, ni);
-                bnd = true;
-            }
-            if (hi <= lo) continue;
+    const f2_t C2 = f2_pack(c2, c2), K2 = f2_pack(k2, k2), TWO = f2_pack(2.f, 2.f);
+    const bool scaled = scale != 1.0;
+    for (int g = 0; g < CW / 32; ++g) {
+        const int64_t cb = col0 + warp * CW + g * 32;
+        {
+            const int64_t j = cb + lane;
+            const bool ok = j < n;
+            cols[warp][lane] = ok ? mf_node(X[j], X[n + j], X[2 * n + j], x32[j]) : mf_node(0.f, 0.f, 0.f, 0.f);
         }
-        for (int64_t tb = lo; tb < hi; tb += MF_S) {
-            __syncthreads();
-            for (int q = threadIdx.x; q < MF_S; q += MF_T) {
-                const int64_t s = tb + q;
-                tile[q] = s < hi ? mf_node((float)X[s], (float)X[n + s], (float)X[2 * n + s], x32[s])
-                                 : mf_node(0.f, 0.f, 0.f, 0.f);
-            }
-            __syncthreads();
-            const int cnt = (int)min((int64_t)MF_S, hi - tb);
-            f2_t T[NP];
+        __syncwarp();
+        const int ct = ms_type(cb, cb + 32, ni);
+        if (sym)
+            ms_dispatch<TRANS, true, NP>(rt, ct, cols[warp], colpart[warp], lane, OX, OY, OZ, XI, imask, C2, K2, TWO,
+                                         cb, ni, T);
+        else
+            ms_dispatch<TRANS, false, NP>(rt, ct, cols[warp], colpart[warp], lane, OX, OY, OZ, XI, imask, C2, K2,
+                                          TWO, cb, ni, T);
+        __syncwarp();
+        if (sym) {
+            // column cb + lane: the sum over the warp's 32 R rows (lanes m, m + 4,
+            // ... in four running sums, then combined in a fixed order)
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int p = 0; p < NP; ++p) T[p] = 0ull;
-            if (bnd)
-                mf_tile<NP, true>(tile, cnt, OX, OY, OZ, A0, A1, A2, C2, T);
-            else
-                mf_tile<NP, false>(tile, cnt, OX, OY, OZ, A0, A1, A2, C2, T);
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                float t0, t1;
-                f2_unpack(T[p], t0, t1);
-                acc[2 * p] += (double)t0;
-                acc[2 * p + 1] += (double)t1;
-            }
+            for (int m = 0; m < 32; ++m) v[m & 3] += colpart[warp][lane][m];
+            const float vs = (v[0] + v[1]) + (v[2] + v[3]);
+            const int64_t j = cb + lane;
+            if (j < n) part[I * n + j] = scaled ? (double)vs * scale : (double)vs;
+            __syncwarp();
         }
     }
+    // row sums: the warps' FP32 partials added in order (FP32: B products in all)
 #pragma unroll
-    for (int r = 0; r < MF_R; ++r) {
-        const int64_t o = obase + threadIdx.x + r * MF_T;
-        if (o < n) part[(int64_t)blockIdx.y * n + o] = acc[r] * scale;
+    for (int p = 0; p < NP; ++p) {
+        float t0, t1;
+        f2_unpack(T[p], t0, t1);
+        own[warp][2 * p][lane] = t0;
+        own[warp][2 * p + 1][lane] = t1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < B; e += MS_W * 32) {
+        const int r = e >> 5, l = e & 31;
+        const int64_t i = row0 + l + 32 * r;
+        float acc = 0.f;
+#pragma unroll
+        for (int w = 0; w < MS_W; ++w) acc += own[w][r][l];
+        if (i < n) part[J * n + i] = scaled ? (double)acc * scale : (double)acc;
     }
 }
+
+// Fold the nb slots (rows G .. G + nb - 1 of the partial buffer) into G
+// groups of k consecutive slots (rows 0 .. G - 1), each group summed in order;
+// one thread per (output, group).
+__global__ void k_ms_fold(double* __restrict__ part, int64_t n, int nb, int k, const int* __restrict__ done) {
+    if (gkb_done(done)) return;
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int g = blockIdx.y, G = gridDim.y;
+    const int s1 = min(nb, (g + 1) * k);
+    double acc = 0.0;
+    for (int s = g * k; s < s1; ++s) acc += part[(int64_t)(G + s) * n + o];
+    part[(int64_t)g * n + o] = acc;
+}
+
+constexpr int MF_T = 128;   // FP64 kernel: threads per CTA
+constexpr int MF_R = 4;     // outputs per thread
+constexpr int MF_S = 256;   // summation nodes per shared tile
+constexpr int MF_OUT = MF_T * MF_R;
 
 // FP64 matrix-free products (RBF_FP64 operators): the same entry formula and
 // tiling as the FP32 kernel, in FP64 (s^{-1/2} from an FP32 estimate refined
@@ -182,28 +311,31 @@ __global__ void __launch_bounds__(MF_T) k_mf_partial_f64(const double* __restric
     }
 }
 
-// Resident CTAs per SM of the two product kernels (the smaller), per device.
-int mf_occupancy(const rbf_ctx* ctx) {
-    static int occ[64] = {0};
+// Resident CTAs per SM of a kernel pair (the smaller), cached per device.
+template <typename K0, typename K1>
+int pair_occupancy(int* cache, const rbf_ctx* ctx, K0 k0, K1 k1, int threads, int fallback) {
     const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
-    if (!occ[dev]) {
+    if (!cache[dev]) {
         int a = 0, b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mf_partial<0>, MF_T, 0) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mf_partial<1>, MF_T, 0) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k0, threads, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, threads, 0) != cudaSuccess) {
             cudaGetLastError();
-            return MF_MIN_CTAS;
+            return fallback;
         }
-        occ[dev] = a < b ? a : b;
-        if (occ[dev] < 1) occ[dev] = 1;
+        cache[dev] = a < b ? a : b;
+        if (cache[dev] < 1) cache[dev] = 1;
     }
-    return occ[dev];
+    return cache[dev];
 }
 
-// Grid: output tiles x summation chunks, with tiles x chunks at most one wave
-// of resident CTAs (a second, mostly empty wave would cost a whole CTA time).
+// FP64 kernel grid: output tiles x summation chunks, with tiles x chunks at
+// most one wave of resident CTAs (a second, mostly empty wave would cost a
+// whole CTA time).
 void mf_plan(const rbf_ctx* ctx, int64_t n, int64_t* tiles, int* chunks, int64_t* chunk_len) {
+    static int occ[64] = {0};
     *tiles = (n + MF_OUT - 1) / MF_OUT;
-    const int64_t wave = (int64_t)ctx->sm_count * mf_occupancy(ctx);
+    const int64_t wave =
+        (int64_t)ctx->sm_count * pair_occupancy(occ, ctx, k_mf_partial_f64<0>, k_mf_partial_f64<1>, MF_T, 4);
     int64_t ch = wave / *tiles;
     if (ch < 1) ch = 1;
     int64_t max_ch = (n + MF_S - 1) / MF_S;  // at least one shared tile per chunk
@@ -213,31 +345,81 @@ void mf_plan(const rbf_ctx* ctx, int64_t n, int64_t* tiles, int* chunks, int64_t
     *chunks = (int)((n + *chunk_len - 1) / *chunk_len);
 }
 
+// FP32 tile-pair grid: blocks of 256 (8 rows per lane) once their tiles fill
+// the resident CTAs at least once, else blocks of 128 (4 rows per lane, four
+// times as many tiles).
+// The consumer of the partials (the GKB half-step) stages slots x rows-per-SM
+// doubles in shared memory: above 8192 of them (64 KB) the nb slots are first
+// folded into G <= 8192 / rows-per-SM groups (at least 8).
+struct MsPlan {
+    int R;
+    int64_t nb, tiles;
+    int k, G;  // slots per group, groups (G = nb, k = 1: no fold)
+};
+MsPlan ms_plan(const rbf_ctx* ctx, int64_t n) {
+    static int occ[64] = {0};
+    MsPlan pl{};
+    const int64_t nb8 = (n + 255) / 256;
+    const int64_t t8 = nb8 * (nb8 + 1) / 2;
+    const int64_t wave = (int64_t)ctx->sm_count * pair_occupancy(occ, ctx, k_mf_sym<0, 8>, k_mf_sym<1, 8>, MS_W * 32, 4);
+    if (t8 >= wave) {
+        pl.R = 8;
+        pl.nb = nb8;
+    } else {
+        pl.R = 4;
+        pl.nb = (n + 127) / 128;
+    }
+    pl.tiles = pl.nb * (pl.nb + 1) / 2;
+    const int64_t sm = ctx->sm_count > 0 ? ctx->sm_count : 1;
+    const int64_t rows = (n + sm - 1) / sm;
+    int64_t gmax = 8192 / (rows > 0 ? rows : 1);
+    gmax = gmax < 8 ? 8 : (gmax > 64 ? 64 : gmax);
+    if (pl.nb <= gmax) {
+        pl.k = 1;
+        pl.G = (int)pl.nb;
+    } else {
+        pl.k = (int)((pl.nb + gmax - 1) / gmax);
+        pl.G = (int)((pl.nb + pl.k - 1) / pl.k);
+    }
+    return pl;
+}
+
 }  // namespace
 
 int mf_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
+    if (op->precision != RBF_FP64) return ms_plan(ctx, op->n).G;
     int64_t tiles, len;
     int ch;
     mf_plan(ctx, op->n, &tiles, &ch, &len);
     return ch;
 }
 
+int mf_part_rows(const rbf_ctx* ctx, const rbf_operator* op) {
+    if (op->precision != RBF_FP64) {
+        const MsPlan pl = ms_plan(ctx, op->n);
+        return (int)pl.nb + (pl.k > 1 ? pl.G : 0);
+    }
+    return mf_chunks(ctx, op);
+}
+
 size_t mf_ws_bytes(const rbf_ctx* ctx, int64_t n) {
     int64_t tiles, len;
     int ch;
     mf_plan(ctx, n, &tiles, &ch, &len);
-    return ws_align((size_t)ch * n * sizeof(double));
+    const MsPlan pl = ms_plan(ctx, n);
+    const int64_t rows = pl.nb + (pl.k > 1 ? pl.G : 0);
+    return ws_align((size_t)(rows > ch ? rows : ch) * n * sizeof(double));
 }
 
 rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, const double* x,
-                             const float* x32, double* part, const int* done) {
-    int64_t tiles, len;
-    int ch;
-    mf_plan(ctx, op->n, &tiles, &ch, &len);
-    if (tiles > 2147483647LL) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large");
-    dim3 grid((unsigned)tiles, (unsigned)ch);
+                             const float* x32, const float* X32, double* part, const int* done) {
     const double scale = op->form == RBF_FORM_EPS ? 1.0 / op->c : 1.0;
     if (op->precision == RBF_FP64) {
+        int64_t tiles, len;
+        int ch;
+        mf_plan(ctx, op->n, &tiles, &ch, &len);
+        if (tiles > 2147483647LL) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large");
+        dim3 grid((unsigned)tiles, (unsigned)ch);
         const double c2d = op->c * op->c, k2d = op->k * op->k;
         if (trans)
             k_mf_partial_f64<1><<<grid, MF_T, 0, ctx->stream>>>(op->d_nodes, op->n, op->n_interior, c2d, k2d, scale,
@@ -248,13 +430,25 @@ rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, co
         RBF_LAUNCHED(ctx, "k_mf_partial_f64");
         return RBF_OK;
     }
+    const MsPlan pl = ms_plan(ctx, op->n);
+    if (pl.tiles > 2147483647LL) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large");
+    if (!X32 || !x32) return rbf_fail(ctx, RBF_ERR_INTERNAL, "FP32 product without its FP32 inputs");
     const float c2 = (float)(op->c * op->c), k2 = (float)(op->k * op->k);
-    if (trans)
-        k_mf_partial<1><<<grid, MF_T, 0, ctx->stream>>>(op->d_nodes, op->n, op->n_interior, c2, k2,
-                                                        scale, x32, len, part, done);
-    else
-        k_mf_partial<0><<<grid, MF_T, 0, ctx->stream>>>(op->d_nodes, op->n, op->n_interior, c2, k2,
-                                                        scale, x32, len, part, done);
-    RBF_LAUNCHED(ctx, "k_mf_partial");
+    const unsigned grid = (unsigned)pl.tiles;
+    const int64_t n = op->n, ni = op->n_interior;
+    double* slots = part + (pl.k > 1 ? (int64_t)pl.G * n : 0);  // folded: slots after the G group rows
+    if (pl.R == 8) {
+        if (trans) k_mf_sym<1, 8><<<grid, MS_W * 32, 0, ctx->stream>>>(X32, n, ni, c2, k2, scale, x32, pl.nb, slots, done);
+        else k_mf_sym<0, 8><<<grid, MS_W * 32, 0, ctx->stream>>>(X32, n, ni, c2, k2, scale, x32, pl.nb, slots, done);
+    } else {
+        if (trans) k_mf_sym<1, 4><<<grid, MS_W * 32, 0, ctx->stream>>>(X32, n, ni, c2, k2, scale, x32, pl.nb, slots, done);
+        else k_mf_sym<0, 4><<<grid, MS_W * 32, 0, ctx->stream>>>(X32, n, ni, c2, k2, scale, x32, pl.nb, slots, done);
+    }
+    RBF_LAUNCHED(ctx, "k_mf_sym");
+    if (pl.k > 1) {
+        k_ms_fold<<<dim3((unsigned)((n + 255) / 256), (unsigned)pl.G), 256, 0, ctx->stream>>>(part, n, (int)pl.nb, pl.k,
+                                                                                             done);
+        RBF_LAUNCHED(ctx, "k_ms_fold");
+    }
     return RBF_OK;
 }

@@ -127,6 +127,47 @@ def test_matvec_mixed(ctx, R, storage, n):
     assert e0 < 1e-5 and e1 < 1e-5
 
 
+# The FP32 matrix-free products run over tile pairs (blocks of 128 nodes, of
+# 256 from about 8700 nodes on): n_interior at 0, n, inside a 32-column group,
+# on a group edge and on a block edge; n = 1, below one group, ragged last
+# blocks; 9001 takes the 256 blocks.
+@pytest.mark.parametrize("n,ni", [(1, 0), (1, 1), (5, 3), (31, 31), (33, 0), (128, 100), (129, 128), (300, 160),
+                                  (300, 161), (1000, 1000), (2500, 1777), (9001, 6000)])
+def test_matvec_mixed_matrix_free_tile_pairs(ctx, R, n, ni):
+    ns = random_nodes(n, ni, n + 7)
+    c, k = 0.2, 5.0
+    op = ctx.rbf_operator_init(dev(ns.soa()), n, ni, c, k, R.RBF_MATRIX_FREE, R.RBF_MIXED)
+    A = OM.assemble(ns.X, ni, c, k)
+    x, y0, y1 = _products(ctx, R, op, n, 3)
+    e0 = np.max(np.abs(y0 - A @ x) / (np.abs(A) @ np.abs(x)))
+    e1 = np.max(np.abs(y1 - A.T @ x) / (np.abs(A).T @ np.abs(x)))
+    print(f"matrix-free FP32 n={n} ni={ni}: {e0:.2e} (A x), {e1:.2e} (A^T x) of |A||x|")
+    assert e0 < 1e-5 and e1 < 1e-5
+    _, z0, z1 = _products(ctx, R, op, n, 3)  # same input: bitwise the same result
+    assert np.array_equal(z0, y0) and np.array_equal(z1, y1)
+
+
+def test_matvec_mixed_matrix_free_folded_slots(ctx, R):
+    """18 000 nodes: 71 blocks of 256, more partial slots than the half-step
+    stages, folded in groups before it.  Checked on sampled rows of A x and
+    columns of A^T x (block edges, n_interior, both ends)."""
+    n, ni, c, k = 18000, 14000, 0.1, 8.0
+    ns = random_nodes(n, ni, 18)
+    op = ctx.rbf_operator_init(dev(ns.soa()), n, ni, c, k, R.RBF_MATRIX_FREE, R.RBF_MIXED)
+    x, y0, y1 = _products(ctx, R, op, n, 4)
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([[0, 1, 255, 256, 257, ni - 1, ni, ni + 1, n - 2, n - 1],
+                                    rng.integers(0, n, 150)]))
+    interior = np.arange(n) < ni
+    D = OM.distances(ns.X[idx], ns.X)  # rows idx of A
+    Ar = np.where(interior[idx, None], OM.lphi(D, c, k), OM.phi(D, c))
+    e0 = np.max(np.abs(y0[idx] - Ar @ x) / (np.abs(Ar) @ np.abs(x)))
+    Ac = np.where(interior[:, None], OM.lphi(D.T, c, k), OM.phi(D.T, c))  # columns idx of A
+    e1 = np.max(np.abs(y1[idx] - Ac.T @ x) / (np.abs(Ac).T @ np.abs(x)))
+    print(f"matrix-free FP32 n={n}: {e0:.2e} (A x), {e1:.2e} (A^T x) of |A||x| on {idx.size} samples")
+    assert e0 < 1e-5 and e1 < 1e-5
+
+
 @pytest.mark.parametrize("n", [6, 1029, 5000])
 def test_matvec_fp64_matrix_free(ctx, R, n):
     """FP64 operators regenerate the entries in FP64 (matrix-free): products
