@@ -64,15 +64,6 @@ MEASURED_TRAFFIC = {
 }
 
 
-def mf_ops_per_entry(n, n_interior):
-    """FP32 pipe operations per regenerated entry of the matrix-free product:
-    3 differences, 3 FMA for s, then 5 for a PDE entry (rs^2, two FMA, one
-    multiply, the accumulate FMA) or 2 for a Dirichlet entry (rs s, the
-    accumulate FMA); the rsqrt goes to the MUFU unit.  Averaged over the row
-    mix (A^T sums over the rows, A x over the columns of each row)."""
-    return (n_interior * 11 + (n - n_interior) * 8) / n
-
-
 def mf_pair_ops(n, n_interior):
     """FP32 pipe operations of one single-instance matrix-free product, which
     evaluates each unordered node pair once (s = |X_i - X_j|^2 + c^2 and its
@@ -84,12 +75,10 @@ def mf_pair_ops(n, n_interior):
     return (12 * ni * (ni - 1) / 2 + 9 * nb * (nb - 1) / 2 + 13 * ni * nb + 11 * ni + 8 * nb)
 
 
-def mf_roofline(n, n_interior, avg_ms, pairs=True):
-    """Roofline of the FP32 matrix-free product: `pairs` for the single-instance
-    tile-pair kernel (mf_pair_ops), else one evaluation per entry (the batched
-    kernel, mf_ops_per_entry)."""
+def mf_roofline(n, n_interior, avg_ms):
+    """Roofline of the FP32 matrix-free product (tile pairs, mf_pair_ops)."""
     ent = n * n / (avg_ms / 1e3)
-    ops = mf_pair_ops(n, n_interior) / (n * n) if pairs else mf_ops_per_entry(n, n_interior)
+    ops = mf_pair_ops(n, n_interior) / (n * n)
     tops = ent * ops / 1e12
     return {"bound": "alu", "achieved": round(tops, 3), "peak": round(FP32_LANE_TOPS, 3),
             "unit": "T FP32-pipe ops/s", "frac": round(tops / FP32_LANE_TOPS, 4), "traffic": None,
@@ -620,7 +609,7 @@ def run_batch(args, rank, world, local_rank):
     # autotuner (one A and one A^T product over the whole batch, best config)
     roof = None
     if tune.get("best_ms", 0) > 0:
-        ops = sum(2 * s_.n * (11 * s_.n_interior + 8 * (s_.n - s_.n_interior)) for s_ in inst)
+        ops = int(sum(2 * mf_pair_ops(s_.n, s_.n_interior) for s_ in inst))
         tops = ops / (tune["best_ms"] / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": round(tops, 3), "peak": round(FP32_LANE_TOPS, 3),
                 "unit": "T FP32-pipe ops/s", "frac": round(tops / FP32_LANE_TOPS, 4), "traffic": None,
@@ -628,7 +617,8 @@ def run_batch(args, rank, world, local_rank):
                 "avg_launch_ms": round(tune["best_ms"] / 2, 5),
                 "timing": "the autotuner's CUDA-event timing of the chosen configuration, this run",
                 "algorithmic_per_launch": f"{sum(s_.n * s_.n for s_ in inst)} entries, "
-                                          f"{ops // 2} FP32-pipe ops (11 per PDE entry, 8 per Dirichlet entry)",
+                                          f"{ops // 2} FP32-pipe ops (mf_pair_ops: each node pair once for "
+                                          f"A_ij and A_ji)",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (unit counts and max clock)"}
     # per-kernel times of one batch, launched directly with CUDA events around
     # every launch (a context with launch timing does not replay the graph):
@@ -993,47 +983,39 @@ def run_paper_sweep(args, rank, world, local_rank):
 
 
 # --------------------------------------------------------------------------- matrix-free product roofline
-def mf_product_roofline(local_rank, pairs=10):
+def mf_product_roofline(local_rank, steps=80):
     """The matrix-free FP32 product (entries regenerated from the node
-    coordinates) on the 20 000-node sphere (c = 0.15, k = 10): CUDA-event
-    time of `pairs` A x / A^T x pairs through rbf_matvec after two warm-up
-    pairs, as regenerated entries per second and a fraction of the FP32 pipe
-    (the operations of mf_pair_ops: each node pair evaluated once for A_ij and
-    A_ji, the MUFU rsqrt beside them)."""
-    import numpy as np
+    coordinates) on the 20 000-node sphere (c = 0.15, k = 10): the library's
+    product timing (CUDA events around every product launch on the launching
+    stream) over a GKB run of `steps` steps after a 20-step warm-up run, as
+    regenerated entries per second and a fraction of the FP32 pipe (the
+    operations of mf_pair_ops: each node pair evaluated once for A_ij and A_ji,
+    the MUFU rsqrt beside them)."""
     import torch
 
     import workloads as w
     from paper_2511_09798_gb300 import rbfkr as R
     ns = w.preset("sphere20000")
     n = ns.n
-    stream = torch.cuda.current_stream()
-    ctx = R.Context(local_rank, stream=stream)
-    nodes = torch.as_tensor(ns.soa(), device=f"cuda:{local_rank}")
+    dev = f"cuda:{local_rank}"
+    ctx = R.Context(local_rank, stream=torch.cuda.current_stream(), timing=2)
+    nodes = torch.as_tensor(ns.soa(), device=dev)
     op = ctx.rbf_operator_init(nodes, n, ns.n_interior, 0.15, 10.0, R.RBF_MATRIX_FREE, R.RBF_MIXED)
-    x = torch.as_tensor(np.random.default_rng(0).normal(size=n), device=f"cuda:{local_rank}")
-    y = torch.empty_like(x)
-
-    def pair():
-        ctx.rbf_matvec(op, 0, x, y)
-        ctx.rbf_matvec(op, 1, y, x)
-        x.div_(torch.linalg.vector_norm(x))  # keep the iterate bounded
-
-    for _ in range(3):  # warm-up, including the first use of the normalisation kernels
-        pair()
+    f = torch.as_tensor(w.plane_wave_rhs(ns, 10.0), device=dev)
+    ctx.rbf_gkb(op, f, 20, R.make_state(torch, n, 20, dev)[0])  # warm-up
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(pairs):
-        pair()
-    e1.record(stream)
+    ctx.rbf_get_counters(reset=True)
+    ctx.rbf_gkb(op, f, steps, R.make_state(torch, n, steps, dev)[0])
     torch.cuda.synchronize()
+    cnt = ctx.rbf_get_counters(reset=True)
     ctx.close()
-    ms = e0.elapsed_time(e1) / (2 * pairs)
+    launches = int(sum(cnt["product_launches"]))
+    ms = sum(cnt["product_ms"]) / max(1, launches)
     roof = mf_roofline(n, ns.n_interior, ms)
     roof.update({"kernel": "k_mf_sym (FP32 matrix-free product, sphere20000)", "avg_launch_ms": round(ms, 5),
-                 "timing": f"{pairs} A x / A^T x pairs through rbf_matvec (the product, the partial-sum "
-                           f"reduction and one vector normalisation per pair), CUDA events"})
+                 "launches_timed": launches,
+                 "timing": f"CUDA events around each product launch (k_mf_sym and its slot fold) of a "
+                           f"{steps}-step GKB run"})
     return roof
 
 

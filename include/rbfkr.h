@@ -374,7 +374,7 @@ typedef struct {
 
 /* Autotuner choice for the batched matrix-free product (see rbf_batch_gkb). */
 typedef struct {
-    int mf_outputs_per_thread;   /* outputs held in registers per thread */
+    int mf_outputs_per_thread;   /* rows held in registers per lane (tile pairs of 32 x this many nodes) */
     int mf_threads;              /* threads per CTA */
     int candidates;              /* configurations timed */
     double best_ms;              /* time of one A and one A^T product of the batch, best config */

@@ -7,7 +7,9 @@
 // instances' vectors (instance b at off_b = sum_{a<b} n_a, T = sum n_b rows).
 // Per step:
 //   k_mf_batch<1>   partial sums of A_b^T q_b for all instances: one CTA per
-//                   work item (instance, output tile, summation chunk)
+//                   work item (instance, tile pair of node blocks), each node
+//                   pair evaluated once for A_ij and A_ji (mf_core.cuh); one
+//                   partial slot per block of the instance
 //   k_half_batch    cooperative kernel over the T concatenated rows (balanced
 //                   slabs, a slab may span several instances): per-instance
 //                   norm finalisation and breakdown test, then classical
@@ -16,9 +18,9 @@
 //                   share the instance (bounded grid barriers)
 //   k_mf_batch<0>, k_half_batch   the same for the p-side
 // The whole step loop is captured into one CUDA graph and launched once.  The
-// tile shape of the batched product (outputs per thread, threads per CTA) is
-// chosen by timing candidates on the batch itself the first time a batch shape
-// is seen.
+// block size of the batched product (4 or 8 rows per lane: blocks of 128 or
+// 256 nodes) is chosen by timing both on the batch itself the first time a
+// batch shape is seen.
 #include <algorithm>
 #include <cfloat>
 #include <vector>
@@ -34,20 +36,17 @@ struct BInst {
     int64_t n, ni;
     float c2, k2;
     double scale;       // 1 (c-form) or 1/c (eps-form)
-    int64_t chunk_len;  // product: summation chunk length
-    int chunks;         // product: number of summation chunks
+    int chunks;         // product: partial slots = blocks of the tile-pair product
     int64_t poff;       // product partials offset (chunks * n doubles)
     int cfirst, ncta;   // half-step CTAs whose slabs intersect the instance
     int64_t hoff;       // dot partials offset ((L+2) * ncta doubles)
     int noff;           // norm partials offset (ncta doubles)
 };
 
-struct MfItem {
-    int b, tile, chunk;
+struct MfItem {  // tile (bi, bj), bi <= bj, of instance b
+    int b, bi, bj;
 };
 
-constexpr int MF_SB = 256;       // summation nodes per shared tile
-constexpr int MF_CHUNK = 2048;   // summation chunk length
 constexpr int HB_THREADS = 256;
 constexpr int HB_WARPS = HB_THREADS / 32;
 constexpr int SEGMAX = 16;       // instances intersecting one slab
@@ -56,103 +55,21 @@ constexpr int UPD_GROUPS_B = HB_THREADS / UPD_ROWS_B;
 
 
 // ---------------------------------------------------------------------------
-// Batched matrix-free product (same arithmetic as the single-instance kernel).
+// Batched matrix-free product: the single-instance tile-pair product
+// (mf_core.cuh) over a work list of (instance, tile) items.
 // ---------------------------------------------------------------------------
-template <int TRANS, int RO, int TH>
-__global__ void __launch_bounds__(TH) k_mf_batch(const MfItem* __restrict__ items, const BInst* __restrict__ inst,
-                                                 const double* __restrict__ nodes_all,
-                                                 const float* __restrict__ x32_all, double* __restrict__ part_all,
-                                                 const int* __restrict__ done) {
-    constexpr int NP = RO / 2;
-    __shared__ MfNode tile[MF_SB];
+template <int TRANS, int R>
+__global__ void __launch_bounds__(MS_W * 32) k_mf_batch(const MfItem* __restrict__ items, const BInst* __restrict__ inst,
+                                                      const float* __restrict__ X32_all,
+                                                      const float* __restrict__ x32_all, double* __restrict__ part_all,
+                                                      const int* __restrict__ done) {
     const MfItem it = items[blockIdx.x];
     if (done && done[it.b]) return;
     const BInst I = inst[it.b];
-    // the item's summation chunk and output tile lie inside its instance
-    if (!RBF_IN_RANGE(it.chunk, I.chunks) || !RBF_IN_RANGE((int64_t)it.tile * (TH * RO), I.n)) return;
-    const double* __restrict__ X = nodes_all + 3 * I.off;
-    const int64_t n = I.n, ni = I.ni;
-    const float* __restrict__ x32 = x32_all + I.off;
-    const float c2 = I.c2, k2 = I.k2;
-    const int64_t obase = (int64_t)it.tile * (TH * RO);
-    f2_t OX[NP], OY[NP], OZ[NP], A0[NP], A1[NP], A2[NP];
-    double acc[RO];
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        float cx[2], cy[2], cz[2], e0[2], e1[2], e2[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t o = obase + threadIdx.x + (2 * p + h) * TH;
-            const bool ok = o < n;
-            cx[h] = ok ? (float)X[o] : 0.f;
-            cy[h] = ok ? (float)X[n + o] : 0.f;
-            cz[h] = ok ? (float)X[2 * n + o] : 0.f;
-            const bool interior = TRANS == 0 && o < ni;
-            e0[h] = interior ? c2 : 0.f;
-            e1[h] = interior ? 2.f : 0.f;
-            e2[h] = interior ? k2 : 1.f;
-        }
-        OX[p] = f2_pack(cx[0], cx[1]);
-        OY[p] = f2_pack(cy[0], cy[1]);
-        OZ[p] = f2_pack(cz[0], cz[1]);
-        A0[p] = f2_pack(e0[0], e0[1]);
-        A1[p] = f2_pack(e1[0], e1[1]);
-        A2[p] = f2_pack(e2[0], e2[1]);
-        acc[2 * p] = acc[2 * p + 1] = 0.0;
-    }
-    const f2_t C2 = f2_pack(c2, c2);
-    const int64_t s0 = (int64_t)it.chunk * I.chunk_len;
-    const int64_t s1 = min(n, s0 + I.chunk_len);
-    for (int seg = 0; seg < (TRANS ? 2 : 1); ++seg) {
-        int64_t lo = s0, hi = s1;
-        bool bnd = obase >= ni;  // trans = 0: every output row is a Dirichlet row
-        if (TRANS) {
-            if (seg == 0) {
-                hi = min(s1, ni);
-                bnd = false;
-#pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    A0[p] = C2;
-                    A1[p] = f2_pack(2.f, 2.f);
-                    A2[p] = f2_pack(k2, k2);
-                }
-            } else {
-                lo = max(s0, ni);
-                bnd = true;
-            }
-            if (hi <= lo) continue;
-        }
-        for (int64_t tb = lo; tb < hi; tb += MF_SB) {
-            __syncthreads();
-            for (int q = threadIdx.x; q < MF_SB; q += TH) {
-                const int64_t s = tb + q;
-                tile[q] = s < hi ? mf_node((float)X[s], (float)X[n + s], (float)X[2 * n + s], x32[s])
-                                 : mf_node(0.f, 0.f, 0.f, 0.f);
-            }
-            __syncthreads();
-            const int cnt = (int)min((int64_t)MF_SB, hi - tb);
-            f2_t T[NP];
-#pragma unroll
-            for (int p = 0; p < NP; ++p) T[p] = 0ull;
-            if (bnd)
-                mf_tile<NP, true>(tile, cnt, OX, OY, OZ, A0, A1, A2, C2, T);
-            else
-                mf_tile<NP, false>(tile, cnt, OX, OY, OZ, A0, A1, A2, C2, T);
-#pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                float t0, t1;
-                f2_unpack(T[p], t0, t1);
-                acc[2 * p] += (double)t0;
-                acc[2 * p + 1] += (double)t1;
-            }
-        }
-    }
-    double* part = part_all + I.poff + (int64_t)it.chunk * n;
-#pragma unroll
-    for (int r = 0; r < RO; ++r) {
-        const int64_t o = obase + threadIdx.x + r * TH;
-        if (o < n) part[o] = acc[r] * I.scale;
-    }
+    // the tile lies inside its instance's block triangle
+    if (!RBF_IN_RANGE(it.bj, I.chunks) || !RBF_IN_RANGE(it.bi, it.bj + 1)) return;
+    ms_tile_product<TRANS, R>(X32_all + 3 * I.off, I.n, I.ni, I.c2, I.k2, I.scale, x32_all + I.off, it.bi, it.bj,
+                              part_all + I.poff);
 }
 
 // ---------------------------------------------------------------------------
@@ -351,14 +268,18 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
                 bout[i] = qr[i] * inv;
                 continue;
             }
-            double p0 = 0.0, p1 = 0.0;
+            // the instance's partial slots (one per block of the tile-pair
+            // product): four running sums, so that four loads are in flight
+            double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
             int q = 0;
-            for (; q + 1 < I.chunks; q += 2) {
+            for (; q + 3 < I.chunks; q += 4) {
                 p0 += part[(int64_t)q * n + i];
                 p1 += part[(int64_t)(q + 1) * n + i];
+                p2 += part[(int64_t)(q + 2) * n + i];
+                p3 += part[(int64_t)(q + 3) * n + i];
             }
-            if (q < I.chunks) p0 += part[(int64_t)q * n + i];
-            double v = (p0 + p1) * inv;
+            for (; q < I.chunks; ++q) p0 += part[(int64_t)q * n + i];
+            double v = ((p0 + p1) + (p2 + p3)) * inv;
             if (u) v = fma(-nrm, u[i], v);
             const int64_t vi = seg_base[sx] + (i - seg_i0[sx]);
             if (RBF_IN_RANGE(vi, a.rmax)) vs[vi] = v;
@@ -548,21 +469,16 @@ __global__ void k_final_batch(HalfBArgs a, int l) {
 // Autotuner candidates for the batched product.
 // ---------------------------------------------------------------------------
 struct MfCand {
-    int ro, th;
+    int ro, th;  // rows per lane (blocks of 32 ro nodes), threads per CTA
 };
-constexpr MfCand MF_CANDS[] = {{2, 128}, {4, 128}, {8, 128}, {2, 256}, {4, 256}};
+constexpr MfCand MF_CANDS[] = {{4, MS_W * 32}, {8, MS_W * 32}};
 constexpr int N_CANDS = sizeof(MF_CANDS) / sizeof(MF_CANDS[0]);
 
 template <int TRANS>
-void launch_mf_cand(int c, int items, cudaStream_t s, const MfItem* it, const BInst* in, const double* nodes,
+void launch_mf_cand(int c, int items, cudaStream_t s, const MfItem* it, const BInst* in, const float* X32,
                     const float* x32, double* part, const int* done) {
-    switch (c) {
-        case 0: k_mf_batch<TRANS, 2, 128><<<items, 128, 0, s>>>(it, in, nodes, x32, part, done); break;
-        case 1: k_mf_batch<TRANS, 4, 128><<<items, 128, 0, s>>>(it, in, nodes, x32, part, done); break;
-        case 2: k_mf_batch<TRANS, 8, 128><<<items, 128, 0, s>>>(it, in, nodes, x32, part, done); break;
-        case 3: k_mf_batch<TRANS, 2, 256><<<items, 256, 0, s>>>(it, in, nodes, x32, part, done); break;
-        default: k_mf_batch<TRANS, 4, 256><<<items, 256, 0, s>>>(it, in, nodes, x32, part, done); break;
-    }
+    if (c == 0) k_mf_batch<TRANS, 4><<<items, MS_W * 32, 0, s>>>(it, in, X32, x32, part, done);
+    else k_mf_batch<TRANS, 8><<<items, MS_W * 32, 0, s>>>(it, in, X32, x32, part, done);
 }
 
 // Host-side description of one batch shape and its device tables.
@@ -571,7 +487,7 @@ struct BatchPlan {
     int64_t T = 0;
     std::vector<BInst> inst;
     std::vector<int64_t> offs;
-    int64_t part_total = 0, hpart_total = 0;
+    int64_t part_total = 0, part_max = 0, hpart_total = 0;
     int npart_total = 0;
 };
 
@@ -620,6 +536,19 @@ void rbf_batch_state_free(rbf_ctx* ctx) {
     ctx->batch_state = nullptr;
 }
 
+// Blocks of 32 ro nodes per instance for the tile-pair product: one partial
+// slot per block, instance after instance.
+static void set_blocks(BatchPlan* P, int ro) {
+    const int64_t Bk = 32 * (int64_t)ro;
+    int64_t poff = 0;
+    for (BInst& I : P->inst) {
+        I.chunks = (int)((I.n + Bk - 1) / Bk);
+        I.poff = poff;
+        poff += (int64_t)I.chunks * I.n;
+    }
+    P->part_total = poff;
+}
+
 static rbf_status plan_batch(rbf_ctx* ctx, const rbf_batch* bt, int form, BatchPlan* P) {
     const int B = bt->count;
     P->B = B;
@@ -652,7 +581,7 @@ static rbf_status plan_batch(rbf_ctx* ctx, const rbf_batch* bt, int form, BatchP
     while (P->bar_group * P->bar_group < P->G) ++P->bar_group;
     P->bar_k = (P->G + P->bar_group - 1) / P->bar_group;
     P->inst.resize(B);
-    int64_t poff = 0, hoff = 0;
+    int64_t poff = 0, hoff = 0;  // (partials: set_blocks)
     int noff = 0;
     for (int b = 0; b < B; ++b) {
         BInst& I = P->inst[b];
@@ -662,10 +591,6 @@ static rbf_status plan_batch(rbf_ctx* ctx, const rbf_batch* bt, int form, BatchP
         I.c2 = (float)(bt->c[b] * bt->c[b]);
         I.k2 = (float)(bt->k[b] * bt->k[b]);
         I.scale = form == RBF_FORM_EPS ? 1.0 / bt->c[b] : 1.0;
-        I.chunk_len = MF_CHUNK;
-        I.chunks = (int)((I.n + MF_CHUNK - 1) / MF_CHUNK);
-        I.poff = poff;
-        poff += (int64_t)I.chunks * I.n;
         // CTAs whose balanced slab [T c / G, T (c+1) / G) intersects [off, off+n)
         const int64_t r0 = I.off, r1 = I.off + I.n;
         int c0 = (int)((r0 * G) / P->T);
@@ -681,7 +606,9 @@ static rbf_status plan_batch(rbf_ctx* ctx, const rbf_batch* bt, int form, BatchP
         I.noff = noff;
         noff += I.ncta;
     }
-    P->part_total = poff;
+    (void)poff;
+    set_blocks(P, MF_CANDS[0].ro);  // the smallest blocks: the most partial slots, for the workspace
+    P->part_max = P->part_total;
     P->hpart_total = hoff;
     P->npart_total = noff;
     // segment bound: a slab must meet at most SEGMAX instances
@@ -697,17 +624,19 @@ static rbf_status plan_batch(rbf_ctx* ctx, const rbf_batch* bt, int form, BatchP
     return RBF_OK;
 }
 
-static std::vector<MfItem> make_items(const BatchPlan& P, int out_per_cta) {
+// Every tile (bi <= bj) of every instance for blocks of 32 ro nodes, largest
+// instances first (longest-processing-time order for the block scheduler).
+static std::vector<MfItem> make_items(const BatchPlan& P, int ro) {
+    const int64_t Bk = 32 * (int64_t)ro;
+    std::vector<int> order(P.B);
+    for (int b = 0; b < P.B; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return P.inst[x].n > P.inst[y].n; });
     std::vector<MfItem> items;
-    for (int b = 0; b < P.B; ++b) {
-        const int tiles = (int)((P.inst[b].n + out_per_cta - 1) / out_per_cta);
-        for (int t = 0; t < tiles; ++t)
-            for (int ch = 0; ch < P.inst[b].chunks; ++ch) items.push_back({b, t, ch});
+    for (int b : order) {
+        const int nb = (int)((P.inst[b].n + Bk - 1) / Bk);
+        for (int i = 0; i < nb; ++i)
+            for (int j = i; j < nb; ++j) items.push_back({b, i, j});
     }
-    // largest instances first (longest-processing-time order for the block scheduler)
-    std::stable_sort(items.begin(), items.end(), [&](const MfItem& x, const MfItem& y) {
-        return P.inst[x.b].n > P.inst[y.b].n;
-    });
     return items;
 }
 
@@ -729,6 +658,7 @@ struct BatchWs {
     int64_t* offs;
     MfItem* items;
     double* part;
+    float* X32;  // node coordinates rounded to FP32, like the nodes [3][n] per instance
     double* hpart;
     double* h;
     double* npart;
@@ -748,7 +678,8 @@ size_t batch_ws_layout(const BatchPlan& P, size_t n_items_max, BatchWs* w, void*
     t.inst = wc.take<BInst>(P.B);
     t.offs = wc.take<int64_t>(P.B + 1);
     t.items = wc.take<MfItem>(n_items_max);
-    t.part = wc.take<double>(P.part_total);
+    t.part = wc.take<double>(P.part_max);
+    t.X32 = wc.take<float>((size_t)3 * P.T);
     t.hpart = wc.take<double>(P.hpart_total);
     t.h = wc.take<double>((size_t)P.B * (P.L + 2));
     t.npart = wc.take<double>(P.npart_total);
@@ -767,9 +698,12 @@ size_t batch_ws_layout(const BatchPlan& P, size_t n_items_max, BatchWs* w, void*
 size_t max_items(const BatchPlan& P) {
     size_t m = 0;
     for (int c = 0; c < N_CANDS; ++c) {
-        const int out = MF_CANDS[c].ro * MF_CANDS[c].th;
+        const int64_t Bk = 32 * (int64_t)MF_CANDS[c].ro;
         size_t cnt = 0;
-        for (int b = 0; b < P.B; ++b) cnt += (size_t)((P.inst[b].n + out - 1) / out) * P.inst[b].chunks;
+        for (int b = 0; b < P.B; ++b) {
+            const size_t nb = (size_t)((P.inst[b].n + Bk - 1) / Bk);
+            cnt += nb * (nb + 1) / 2;
+        }
         if (cnt > m) m = cnt;
     }
     return m;
@@ -848,6 +782,7 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     a.limit = w.binfo + BI_LIMIT * P.B;
     k_init_batch<<<P.G, HB_THREADS, 0, s>>>(a, bt->d_f, w.vp);
     RBF_LAUNCHED(ctx, "k_init_batch");
+    RBF_TRY(launch_to_f32(ctx, 3 * P.T, bt->d_nodes, w.X32, s));  // the products' FP32 node coordinates
 
     // ---- autotune the product tile on this batch (first time this shape is seen)
     if (ts.key_T != P.T || ts.key_B != P.B) {
@@ -857,14 +792,16 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
         double best = 1e30;
         int bestc = 1;
         for (int c = 0; c < N_CANDS; ++c) {
-            std::vector<MfItem> items = make_items(P, MF_CANDS[c].ro * MF_CANDS[c].th);
+            set_blocks(&P, MF_CANDS[c].ro);
+            std::vector<MfItem> items = make_items(P, MF_CANDS[c].ro);
+            RBF_CUDA(ctx, cudaMemcpyAsync(w.inst, P.inst.data(), sizeof(BInst) * P.B, cudaMemcpyHostToDevice, s));
             RBF_CUDA(ctx, cudaMemcpyAsync(w.items, items.data(), sizeof(MfItem) * items.size(),
                                           cudaMemcpyHostToDevice, s));
             float ms_sum = 0.f;
             for (int rep = 0; rep < 2; ++rep) {
                 RBF_CUDA(ctx, cudaEventRecord(e0, s));
-                launch_mf_cand<1>(c, (int)items.size(), s, w.items, w.inst, bt->d_nodes, w.vp32, w.part, nullptr);
-                launch_mf_cand<0>(c, (int)items.size(), s, w.items, w.inst, bt->d_nodes, w.vp32, w.part, nullptr);
+                launch_mf_cand<1>(c, (int)items.size(), s, w.items, w.inst, w.X32, w.vp32, w.part, nullptr);
+                launch_mf_cand<0>(c, (int)items.size(), s, w.items, w.inst, w.X32, w.vp32, w.part, nullptr);
                 RBF_CUDA(ctx, cudaEventRecord(e1, s));
                 RBF_CUDA(ctx, cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -886,7 +823,9 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
         ts.drop_graphs();
     }
     const int cand = ts.cand;
-    std::vector<MfItem> items = make_items(P, MF_CANDS[cand].ro * MF_CANDS[cand].th);
+    set_blocks(&P, MF_CANDS[cand].ro);
+    std::vector<MfItem> items = make_items(P, MF_CANDS[cand].ro);
+    RBF_CUDA(ctx, cudaMemcpyAsync(w.inst, P.inst.data(), sizeof(BInst) * P.B, cudaMemcpyHostToDevice, s));
     RBF_CUDA(ctx, cudaMemcpyAsync(w.items, items.data(), sizeof(MfItem) * items.size(), cudaMemcpyHostToDevice, s));
     const int nit = (int)items.size();
     const size_t hsmem = ((size_t)P.rmax + (size_t)SEGMAX * (P.L + 2)) * sizeof(double);
@@ -908,7 +847,7 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
     put(a.alpha_all); put(a.beta_all); put(a.W_all); put(a.Z_all); put(a.part_all); put(a.hpart_all);
     put(a.h_all); put(a.npart_all); put(a.binfo); put(a.limit); put(a.chat_all); put(a.stt); put(a.bar);
     put(a.bar_group); put(a.budget); put(a.rmax);
-    put(bt->d_nodes); put(bt->d_f); put(w.items); put(w.part); put(w.vr); put(w.vp); put(w.vr32); put(w.vp32);
+    put(bt->d_nodes); put(bt->d_f); put(w.items); put(w.part); put(w.X32); put(w.vr); put(w.vp); put(w.vr32); put(w.vp32);
     put(nit); put(cand); put(P.G); put(hsmem); put(steps); put(form); put(s);
     // per-launch timing (opt.timing bit 1): the loop is launched directly, each
     // launch between CUDA events on the batch stream
@@ -924,9 +863,9 @@ extern "C" rbf_status rbf_batch_gkb(rbf_ctx* ctx, rbf_batch* bt, int steps, int 
                 const float* x32 = side == 0 ? w.vp32 : w.vr32;
                 const int pslot = timed ? rbf_prod_begin(ctx, trans, s) : -1;
                 if (trans)
-                    launch_mf_cand<1>(cand, nit, s, w.items, w.inst, bt->d_nodes, x32, w.part, din);
+                    launch_mf_cand<1>(cand, nit, s, w.items, w.inst, w.X32, x32, w.part, din);
                 else
-                    launch_mf_cand<0>(cand, nit, s, w.items, w.inst, bt->d_nodes, x32, w.part, din);
+                    launch_mf_cand<0>(cand, nit, s, w.items, w.inst, w.X32, x32, w.part, din);
                 rbf_prod_end(ctx, trans, pslot, s);
                 cudaError_t e = cudaGetLastError();
                 if (e != cudaSuccess) return e;

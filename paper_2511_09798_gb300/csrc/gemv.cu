@@ -405,8 +405,8 @@ rbf_status launch_reduce_partials(rbf_ctx* ctx, int64_t n, int chunks, const dou
     return RBF_OK;
 }
 
-rbf_status launch_to_f32(rbf_ctx* ctx, int64_t n, const double* x, float* y) {
-    k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, x, y);
+rbf_status launch_to_f32(rbf_ctx* ctx, int64_t n, const double* x, float* y, cudaStream_t s) {
+    k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s ? s : ctx->stream>>>(n, x, y);
     RBF_LAUNCHED(ctx, "k_to_f32");
     return RBF_OK;
 }

@@ -169,7 +169,7 @@ rbf_status launch_evaluate(rbf_ctx* ctx, const rbf_operator* op, const double* c
 size_t gemv_ws_bytes(const rbf_ctx* ctx, int64_t n);
 int gemv_t_chunks(const rbf_ctx* ctx, const rbf_operator* op);
 int gemv_n_chunks(const rbf_ctx* ctx, const rbf_operator* op);  // partials of A x (FP64: column segments)
-rbf_status launch_to_f32(rbf_ctx* ctx, int64_t n, const double* x, float* y);
+rbf_status launch_to_f32(rbf_ctx* ctx, int64_t n, const double* x, float* y, cudaStream_t s = nullptr);
 // Partials of A x (column segments [gemv_n_chunks][n]) and of A^T x (row
 // chunks [gemv_t_chunks][n]); FP64 x for FP64 operators, x32 for FP32 ones.
 rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, const float* x32, double* part,

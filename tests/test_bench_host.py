@@ -37,13 +37,6 @@ def test_mf_pair_ops_counts_every_pair_once():
         assert bench.mf_pair_ops(n, ni) == ref
 
 
-def test_mf_ops_per_entry_mix():
-    # 11 FP32-pipe operations per PDE entry, 8 per Dirichlet entry, averaged over the rows
-    assert bench.mf_ops_per_entry(10, 10) == 11
-    assert bench.mf_ops_per_entry(10, 0) == 8
-    assert bench.mf_ops_per_entry(4, 1) == (11 + 3 * 8) / 4
-
-
 def test_shipped_stopnet_file_matches_the_npz(tmp_path):
     """The binary stop-network file read by rbf_stopnet_load holds exactly the
     arrays of the shipped .npz, in the documented layout."""
