@@ -148,11 +148,12 @@ def test_matvec_mixed_matrix_free_tile_pairs(ctx, R, n, ni):
 
 
 def test_matvec_mixed_matrix_free_folded_slots(ctx, R):
-    """18 000 nodes: 71 blocks of 256, more partial slots than the half-step
-    stages, folded in groups before it.  Checked on sampled rows of A x and
-    columns of A^T x (block edges, n_interior, both ends)."""
-    n, ni, c, k = 18000, 14000, 0.1, 8.0
-    ns = random_nodes(n, ni, 18)
+    """26 000 nodes: 102 blocks of 256, more partial slots than the half-step
+    stages (71 at 172 rows per SM), folded in pairs before it.  Checked on
+    sampled rows of A x and columns of A^T x (block edges, n_interior, both
+    ends)."""
+    n, ni, c, k = 26000, 20000, 0.1, 8.0
+    ns = random_nodes(n, ni, 26)
     op = ctx.rbf_operator_init(dev(ns.soa()), n, ni, c, k, R.RBF_MATRIX_FREE, R.RBF_MIXED)
     x, y0, y1 = _products(ctx, R, op, n, 4)
     rng = np.random.default_rng(5)
