@@ -75,6 +75,16 @@ def mf_pair_ops(n, n_interior):
     return (12 * ni * (ni - 1) / 2 + 9 * nb * (nb - 1) / 2 + 13 * ni * nb + 11 * ni + 8 * nb)
 
 
+def mf_pair_ops_f64(n, n_interior):
+    """FP64 pipe operations of one FP64 matrix-free product by tile pairs:
+    per unordered node pair 3 differences, 3 FMA for s, 5 for the refined
+    s^{-1/2} (its FP32 estimate and the conversions around it not counted),
+    the entry factors (PDE: rs^2, two FMA, one multiply; Dirichlet: rs s; a
+    mixed pair both) and two accumulate FMA; the diagonal one accumulate."""
+    ni, nb = n_interior, n - n_interior
+    return (17 * ni * (ni - 1) / 2 + 14 * nb * (nb - 1) / 2 + 18 * ni * nb + 16 * ni + 13 * nb)
+
+
 def mf_roofline(n, n_interior, avg_ms):
     """Roofline of the FP32 matrix-free product (tile pairs, mf_pair_ops)."""
     ent = n * n / (avg_ms / 1e3)
@@ -402,18 +412,20 @@ def run_ours(args, rank, world, local_rank):
             roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                     "frac": round(gbs / peaks.get("hbm_gbs", 6790.7), 4), "traffic": None,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
-    elif prec == R.RBF_FP64:  # FP64 regeneration: ~16 FP64-pipe operations per entry
+    elif prec == R.RBF_FP64:  # FP64 regeneration by tile pairs (mf_pair_ops_f64)
         ent = n * n / (avg_ms / 1e3)
         peak = 152 * 2 * 2.07e9 / 1e12
-        tops = ent * 16 / 1e12
+        ops = mf_pair_ops_f64(n, ns.n_interior)
+        tops = ops / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": round(tops, 4), "peak": round(peak, 4), "unit": "T FP64-pipe ops/s",
-                "frac": round(tops / peak, 4), "traffic": None, "entries_per_s": ent, "ops_per_entry": 16,
+                "frac": round(tops / peak, 4), "traffic": None, "entries_per_s": ent,
+                "ops_per_entry": round(ops / (n * n), 3),
                 "peak_source": "152 SMs x 2 FP64 ops/clk x 2.07 GHz (unit counts and max clock)"}
     else:
         roof = mf_roofline(n, ns.n_interior, avg_ms)
     roof["traffic"] = MEASURED_TRAFFIC.get((wl["name"], dom))
     kname = ("gemv_n (p = A z) and gemv_t (r = A^T w)" if storage == R.RBF_ASSEMBLED
-             else ("k_mf_partial_f64" if prec == R.RBF_FP64 else "k_mf_sym") + " (p = A z, r = A^T w, matrix-free)")
+             else ("k_mf_sym_f64" if prec == R.RBF_FP64 else "k_mf_sym") + " (p = A z, r = A^T w, matrix-free)")
     roof.update({"kernel": kname, "avg_launch_ms": round(avg_ms, 5),
                  "avg_launch_ms_how": "union of the product launch intervals / launches (CUDA events on the "
                                       "launching streams, timed region)",

@@ -28,6 +28,15 @@ def test_scaled_oracle_baseline_on_a_small_casing():
     assert "100 of 1500 rows" in out["sample"] and "GCV-HKT(20)" in out["sample"]
 
 
+def test_mf_pair_ops_f64_counts_every_pair_once():
+    import bench
+    for n, ni in [(1, 0), (1, 1), (7, 3), (12, 12), (9, 0)]:
+        cost = {(True, True): 17, (False, False): 14}
+        ref = sum(cost.get((i < ni, j < ni), 18) for i in range(n) for j in range(i + 1, n))
+        ref += sum(16 if i < ni else 13 for i in range(n))
+        assert bench.mf_pair_ops_f64(n, ni) == ref
+
+
 def test_mf_pair_ops_counts_every_pair_once():
     import bench
     for n, ni in [(1, 0), (1, 1), (7, 3), (12, 12), (9, 0)]:

@@ -169,17 +169,23 @@ def test_matvec_mixed_matrix_free_folded_slots(ctx, R):
     assert e0 < 1e-5 and e1 < 1e-5
 
 
-@pytest.mark.parametrize("n", [6, 1029, 5000])
-def test_matvec_fp64_matrix_free(ctx, R, n):
+# FP64 matrix-free products by tile pairs of 128-node blocks: the same edge
+# cases as the FP32 tile pairs (n_interior at 0, n, inside a 32-column group,
+# on group and block edges; n = 1; ragged last blocks).
+@pytest.mark.parametrize("n,ni", [(1, 0), (1, 1), (6, 4), (31, 31), (33, 0), (128, 100), (129, 128), (300, 160),
+                                  (300, 161), (1029, 771), (5000, 3750)])
+def test_matvec_fp64_matrix_free(ctx, R, n, ni):
     """FP64 operators regenerate the entries in FP64 (matrix-free): products
-    agree with the dense FP64 matrix to rounding."""
-    ns = random_nodes(n, (3 * n) // 4, n + 5)
+    agree with the dense FP64 matrix to rounding, bitwise the same on a rerun."""
+    ns = random_nodes(n, ni, n + 5)
     c, k = 0.25, 3.0
-    op = ctx.rbf_operator_init(dev(ns.soa()), n, ns.n_interior, c, k, R.RBF_MATRIX_FREE, R.RBF_FP64)
-    A = OM.assemble(ns.X, ns.n_interior, c, k)
+    op = ctx.rbf_operator_init(dev(ns.soa()), n, ni, c, k, R.RBF_MATRIX_FREE, R.RBF_FP64)
+    A = OM.assemble(ns.X, ni, c, k)
     x, y0, y1 = _products(ctx, R, op, n, 3)
     assert np.max(np.abs(y0 - A @ x) / (np.abs(A) @ np.abs(x))) < 1e-13
     assert np.max(np.abs(y1 - A.T @ x) / (np.abs(A).T @ np.abs(x))) < 1e-13
+    _, z0, z1 = _products(ctx, R, op, n, 3)
+    assert np.array_equal(z0, y0) and np.array_equal(z1, y1)
 
 
 def test_gkb_fp64_matrix_free_matches_assembled(ctx, R):
