@@ -18,12 +18,16 @@ __device__ __forceinline__ float warp_sumf(float v) {
     return v;
 }
 
-// 1/sqrt(x) in FP64 for x in the normal float range: an FP32 hardware
-// estimate refined by one third-order step of the Newton iteration for
-// y = x^{-1/2}: with e = 1 - x y0^2, y = y0 (1 + e/2 + 3 e^2 / 8), which
-// cubes the relative error of y0 (about 2^-22) to below FP64 rounding.
+// 1/sqrt(x) in FP64 for normal x: the hardware's FP64 reciprocal-square-root
+// estimate (PTX rsqrt.approx.ftz.f64, no FP32 round trip: two conversions
+// fewer on the FP64 pipe than an FP32 estimate) refined by one third-order
+// step of the Newton iteration for y = x^{-1/2}: with e = 1 - x y0^2,
+// y = y0 (1 + e/2 + 3 e^2 / 8), which cubes the relative error of y0 to below
+// FP64 rounding (the collocation entries built on it agree with their FP64
+// definition to 2e-15 relative for s from 1e-6 to 3e4 in the tests).
 __device__ __forceinline__ double rsqrt_f64(double x) {
-    double y0 = (double)rsqrtf((float)x);
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(x));
     double t = x * y0;
     double e = fma(-t, y0, 1.0);
     double c = fma(0.375, e, 0.5);

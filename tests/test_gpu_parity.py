@@ -67,6 +67,17 @@ def test_assembly_fp64(ctx, R, n, ni):
     assert np.max(np.abs(got - ref) / np.abs(ref)) < 2e-15
 
 
+@pytest.mark.parametrize("scale,c", [(1.0, 1e-3), (100.0, 0.5), (0.01, 1e-3)])
+def test_assembly_fp64_wide_range(ctx, R, scale, c):
+    """Entries over many decades of s = r^2 + c^2 (1e-6 .. 3e4): the refined
+    FP64 reciprocal square root stays at FP64 rounding everywhere."""
+    ns = random_nodes(300, 200, 11)
+    ns = w.NodeSet(ns.X * scale, 200, "cube", "scaled")
+    op, A, _ = gpu_matrix(ctx, R, ns, c, 3.0)
+    ref = OM.assemble(ns.X, 200, c, 3.0)
+    assert np.max(np.abs(A.cpu().numpy() - ref) / np.abs(ref)) < 2e-15
+
+
 def test_assembly_eps_form(ctx, R):
     ns = random_nodes(200, 120, 5)
     op, A, _ = gpu_matrix(ctx, R, ns, 0.4, 2.0, form=R.RBF_FORM_EPS)
