@@ -161,7 +161,8 @@ rbf_status rbf_check_all(rbf_ctx* ctx) {
     };
     const Unit units[] = {{"ctx.cu", rbf_check_take_ctx},         {"gemv.cu", rbf_check_take_gemv},
                           {"gkb.cu", rbf_check_take_gkb},         {"batch.cu", rbf_check_take_batch},
-                          {"select.cu", rbf_check_take_select},   {"assemble.cu", rbf_check_take_assemble}};
+                          {"select.cu", rbf_check_take_select},   {"assemble.cu", rbf_check_take_assemble},
+                          {"mf.cu", rbf_check_take_mf}};
     rbf_status st = RBF_OK;
     for (const Unit& u : units) {
         const unsigned line = u.take();

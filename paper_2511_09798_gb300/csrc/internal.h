@@ -103,6 +103,7 @@ unsigned rbf_check_take_gkb();
 unsigned rbf_check_take_batch();
 unsigned rbf_check_take_select();
 unsigned rbf_check_take_assemble();
+unsigned rbf_check_take_mf();
 rbf_status rbf_check_all(rbf_ctx* ctx);
 
 #define RBF_CUDA(ctx, call)                                                             \

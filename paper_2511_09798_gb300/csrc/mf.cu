@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(MS_W * 32) k_mf_sym(const float* __restrict__ 
     if (gkb_done(done)) return;
     int64_t I, J;
     ms_tile(blockIdx.x, nb, I, J);
+    if (!RBF_IN_RANGE(J, nb) || !RBF_IN_RANGE(I, J + 1)) return;  // a tile of the triangle: slots I, J < nb
     ms_tile_product<TRANS, R>(X, n, ni, c2, k2, scale, x32, I, J, part);
 }
 
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(MS_W * 32) k_mf_sym_f64(const double* __restri
     __shared__ double own[MS_W][MD_R][32];
     int64_t I, J;
     ms_tile(blockIdx.x, nb, I, J);
+    if (!RBF_IN_RANGE(J, nb) || !RBF_IN_RANGE(I, J + 1)) return;  // a tile of the triangle: slots I, J < nb
     const bool sym = I != J;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t row0 = I * B, col0 = J * B;
@@ -318,3 +320,5 @@ rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, co
     }
     return RBF_OK;
 }
+
+RBF_CHECK_READER(mf)

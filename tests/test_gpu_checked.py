@@ -4,8 +4,8 @@ Its device index tests must (a) report a failure through the normal error path
 (a self-test index that fails by construction and touches no memory), and
 (b) stay silent over runs of every kernel family at ragged sizes: assembly,
 FP64 and mixed products (assembled and matrix-free), GKB with its half-step
-kernels, concurrent lanes, the projected solves, the batched driver and the
-reconstruction.  The library is loaded once per process, so the checked runs
+kernels, concurrent lanes, the projected solves, the batched driver, the
+reconstruction and the matrix-free tile pairs with folded partial slots.  The library is loaded once per process, so the checked runs
 happen in a child process with RBFKR_CHECKED=1."""
 import os
 import subprocess
@@ -70,6 +70,16 @@ bt, kb = R.make_batch(torch, sets, [0.3] * 4, [2.0] * 4, [w.plane_wave_rhs(s, 2.
 ctx.rbf_batch_gkb(bt, L)
 T = int(kb["offsets"][-1])
 ctx.rbf_batch_hkt(bt, R.RBF_GCV, torch.empty(T, dtype=torch.float64, device="cuda"))
+# the matrix-free tile pairs with folded partial slots (26 000 nodes, FP32) and
+# the 256-node blocks (9001 nodes), both products
+for n, ni in ((26000, 20000), (9001, 6000)):
+    X = np.random.default_rng(n).uniform(0, 1, (3, n))
+    nodes = torch.as_tensor(X, device="cuda")
+    op = ctx.rbf_operator_init(nodes, n, ni, 0.1, 8.0, 1, 1)
+    x = torch.as_tensor(np.random.default_rng(1).normal(size=n), device="cuda")
+    y = torch.empty_like(x)
+    ctx.rbf_matvec(op, 0, x, y)
+    ctx.rbf_matvec(op, 1, x, y)
 ctx.rbf_check()
 print("checked build: no index check failed")
 '''
