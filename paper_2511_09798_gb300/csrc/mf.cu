@@ -1,8 +1,7 @@
 // Matrix-free products with the collocation matrix, by tile pairs.
 //
-// Rows and columns of A are the
-// same node list, s_ij = |X_i - X_j|^2 + c^2 = s_ji, and an entry depends on
-// its row's type only (L Phi for PDE rows, Phi for Dirichlet rows), so the
+// Rows and columns of A are the same node list, s_ij = |X_i - X_j|^2 + c^2 =
+// s_ji, and an entry depends on its row's type only (L Phi for PDE rows, Phi for Dirichlet rows), so the
 // PDE x PDE and Dirichlet x Dirichlet blocks are symmetric.  The nodes are cut
 // into nb blocks of B; CTA (I, J), I < J, evaluates s and s^{-1/2} once per
 // node pair (i in I, j in J) and feeds both A_ij and A_ji (one value when the
@@ -46,7 +45,9 @@ __device__ __forceinline__ void ms_tile(int64_t t, int64_t nb, int64_t& I, int64
     J = nb - 1 - (u - r * (r + 1) / 2);
 }
 
-// One tile per CTA, tiles in the order of ms_tile.
+// One tile per CTA, tiles in the order of ms_tile.  When the half-step would
+// stage too many slots, the slots are written after G group rows and folded
+// into them (k_ms_fold); otherwise part holds the nb slots directly.
 template <int TRANS, int R>
 __global__ void __launch_bounds__(MS_W * 32) k_mf_sym(const float* __restrict__ X, int64_t n, int64_t ni, float c2,
                                                     float k2, double scale, const float* __restrict__ x32,
