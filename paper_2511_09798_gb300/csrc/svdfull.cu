@@ -378,40 +378,47 @@ __global__ void __launch_bounds__(BT) k_bidiag(double* __restrict__ W, int64_t n
         __syncthreads();
         const double tau2 = sc[0], scale2 = sc[1];
         if (tau2 != 0.0) {
-            // 32-row blocks over the CTAs; warp q takes the columns c = q, q+8, ...
-            // (coalesced along the rows), partial dots combined in shared memory
+            // blocks of RB rows over the CTAs (RB = 32, 16 or 8: the largest that
+            // still gives every CTA a block); lane = (row r, column lane cl), warp
+            // q takes the columns c = q CPL + cl, stepping by BW CPL (coalesced
+            // along the rows); partial dots combined in shared memory in a fixed
+            // order (for RB = 32 one column per warp step, as before)
             const int64_t rows = n - k - 1;
-            const int64_t nblk = (rows + 31) / 32;
+            const int RB = rows >= 32 * (int64_t)gridDim.x ? 32 : (rows >= 16 * (int64_t)gridDim.x ? 16 : 8);
+            const int CPL = 32 / RB, CW = BW * CPL;
+            const int r = lane % RB, cl = lane / RB;
+            const int64_t nblk = (rows + RB - 1) / RB;
             for (int64_t rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
-                const int64_t i = k + 1 + rb * 32 + lane;
+                const int64_t i = k + 1 + rb * RB + r;
                 const bool ok = i < n;
                 double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-                int64_t c = 1 + warp;
-                for (; c + 3 * BW < m2; c += 4 * BW) {
+                int64_t c = 1 + warp * CPL + cl;
+                for (; c + 3 * CW < m2; c += 4 * CW) {
                     if (ok) {
                         a0 = fma(W[(k + 1 + c) * n + i], W[(k + 1 + c) * n + k], a0);
-                        a1 = fma(W[(k + 1 + c + BW) * n + i], W[(k + 1 + c + BW) * n + k], a1);
-                        a2 = fma(W[(k + 1 + c + 2 * BW) * n + i], W[(k + 1 + c + 2 * BW) * n + k], a2);
-                        a3 = fma(W[(k + 1 + c + 3 * BW) * n + i], W[(k + 1 + c + 3 * BW) * n + k], a3);
+                        a1 = fma(W[(k + 1 + c + CW) * n + i], W[(k + 1 + c + CW) * n + k], a1);
+                        a2 = fma(W[(k + 1 + c + 2 * CW) * n + i], W[(k + 1 + c + 2 * CW) * n + k], a2);
+                        a3 = fma(W[(k + 1 + c + 3 * CW) * n + i], W[(k + 1 + c + 3 * CW) * n + k], a3);
                     }
                 }
-                for (; c < m2; c += BW)
+                for (; c < m2; c += CW)
                     if (ok) a0 = fma(W[(k + 1 + c) * n + i], W[(k + 1 + c) * n + k], a0);
                 rp[warp][lane] = (a0 + a1) + (a2 + a3);
                 __syncthreads();
-                if (warp == 0) {
+                if (warp == 0 && lane < RB) {
                     double t = 0.0;
-#pragma unroll
-                    for (int q = 0; q < BW; ++q) t += rp[q][lane];
-                    const double x0 = ok ? W[(k + 1) * n + i] : 0.0;
+                    for (int q = 0; q < BW; ++q)
+                        for (int l = 0; l < CPL; ++l) t += rp[q][l * RB + lane];
+                    const int64_t ir = k + 1 + rb * RB + lane;
+                    const double x0 = ir < n ? W[(k + 1) * n + ir] : 0.0;
                     rw[lane] = tau2 * fma(scale2, t, x0);  // t_i = tau (u . w_i)
                 }
                 __syncthreads();
-                const double ti = rw[lane];
+                const double ti = rw[r];
                 if (ok) {
-                    if (warp == 0) W[(k + 1) * n + i] -= ti;
+                    if (warp == 0 && cl == 0) W[(k + 1) * n + i] -= ti;
                     const double tsi = ti * scale2;
-                    for (int64_t cc = 1 + warp; cc < m2; cc += BW)
+                    for (int64_t cc = 1 + warp * CPL + cl; cc < m2; cc += CW)
                         W[(k + 1 + cc) * n + i] = fma(-tsi, W[(k + 1 + cc) * n + k], W[(k + 1 + cc) * n + i]);
                 }
                 __syncthreads();
