@@ -26,28 +26,30 @@ __device__ __forceinline__ float mq_entry_f32(float dx, float dy, float dz, floa
 }
 
 // FP32 assembly (mixed precision): one column per thread, AS_TM rows per CTA.
+// The coordinates are rounded to FP32 once per row (shared memory) and once
+// per column (registers), not once per entry: the conversions run at the
+// FP64 rate.
 __global__ void __launch_bounds__(AS_TN) k_assemble_f32(const double* __restrict__ X, int64_t n, int64_t ni,
                                                         double c, double k, double scale, float* __restrict__ A,
                                                         int64_t lda) {
-    __shared__ double rx[AS_TM], ry[AS_TM], rz[AS_TM];
+    __shared__ float rx[AS_TM], ry[AS_TM], rz[AS_TM];
     const int64_t j = (int64_t)blockIdx.x * AS_TN + threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.y * AS_TM;
     if (threadIdx.x < AS_TM) {
         int64_t i = i0 + threadIdx.x;
         bool ok = i < n;
-        rx[threadIdx.x] = ok ? X[i] : 0.0;
-        ry[threadIdx.x] = ok ? X[n + i] : 0.0;
-        rz[threadIdx.x] = ok ? X[2 * n + i] : 0.0;
+        rx[threadIdx.x] = ok ? (float)X[i] : 0.f;
+        ry[threadIdx.x] = ok ? (float)X[n + i] : 0.f;
+        rz[threadIdx.x] = ok ? (float)X[2 * n + i] : 0.f;
     }
     __syncthreads();
     if (j >= n) return;
-    const double xj = X[j], yj = X[n + j], zj = X[2 * n + j];
-    const double c2 = c * c, k2 = k * k;
+    const float xj = (float)X[j], yj = (float)X[n + j], zj = (float)X[2 * n + j];
+    const float c2 = (float)(c * c), k2 = (float)(k * k), sc = (float)scale;
     const int rows = (int)min((int64_t)AS_TM, n - i0);
     for (int r = 0; r < rows; ++r) {
         const int64_t i = i0 + r;
-        A[i * lda + j] = mq_entry_f32((float)rx[r] - (float)xj, (float)ry[r] - (float)yj, (float)rz[r] - (float)zj,
-                                      (float)c2, (float)k2, i < ni) * (float)scale;
+        A[i * lda + j] = mq_entry_f32(rx[r] - xj, ry[r] - yj, rz[r] - zj, c2, k2, i < ni) * sc;
     }
 }
 
