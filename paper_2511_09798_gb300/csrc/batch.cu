@@ -61,15 +61,15 @@ constexpr int UPD_GROUPS_B = HB_THREADS / UPD_ROWS_B;
 template <int TRANS, int R>
 __global__ void __launch_bounds__(MS_W * 32) k_mf_batch(const MfItem* __restrict__ items, const BInst* __restrict__ inst,
                                                       const float* __restrict__ X32_all,
-                                                      const float* __restrict__ x32_all, double* __restrict__ part_all,
+                                                      const float* __restrict__ x32_all, float* __restrict__ part_all,
                                                       const int* __restrict__ done) {
     const MfItem it = items[blockIdx.x];
     if (done && done[it.b]) return;
     const BInst I = inst[it.b];
     // the tile lies inside its instance's block triangle
     if (!RBF_IN_RANGE(it.bj, I.chunks) || !RBF_IN_RANGE(it.bi, it.bj + 1)) return;
-    ms_tile_product<TRANS, R>(X32_all + 3 * I.off, I.n, I.ni, I.c2, I.k2, I.scale, x32_all + I.off, it.bi, it.bj,
-                              part_all + I.poff);
+    ms_tile_product<TRANS, R, float>(X32_all + 3 * I.off, I.n, I.ni, I.c2, I.k2, I.scale, x32_all + I.off, it.bi,
+                                     it.bj, part_all + I.poff);
 }
 
 // ---------------------------------------------------------------------------
@@ -134,7 +134,7 @@ struct HalfBArgs {
     const double* qraw_all;  // vector whose norm is finalised
     double* v_all;           // new vector
     float* v32_all;          // its FP32 copy
-    const double* part_all;  // product partials
+    const float* part_all;   // product partial slots (FP32 runs, unscaled)
     double* hpart_all;
     double* h_all;           // [B][L+2]
     double* npart_all;       // per-instance norm partials
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
         const double* u = a.side == 0 ? (a.j >= 2 ? Zb + (int64_t)(a.j - 2) * n : nullptr) : Wb + (int64_t)(a.j - 1) * n;
         double* bout = a.side == 0 ? Wb + (int64_t)(a.j - 1) * n : Zb + (int64_t)(a.j - 1) * n;
         const double* qr = a.qraw_all + I.off;
-        const double* part = a.part_all + I.poff;
+        const float* part = a.part_all + I.poff;
         const double nrm = seg_nrm[sx], inv = seg_inv[sx];
         for (int64_t i = seg_i0[sx] + threadIdx.x; i < seg_i1[sx]; i += HB_THREADS) {
             if (seg_brk[sx] == 2) {  // w_j = 0 after a beta breakdown
@@ -268,18 +268,27 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
                 bout[i] = qr[i] * inv;
                 continue;
             }
-            // the instance's partial slots (one per block of the tile-pair
-            // product): four running sums, so that four loads are in flight
-            double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+            // the instance's partial slots (one FP32 run per block of the
+            // tile-pair product), added in order by a compensated FP32 sum
+            // (Neumaier: hi + lo carries the sum to ~2^-48 relative; FP64 adds
+            // would cost as much as the reorthogonalization's FMAs here)
+            float hi = 0.f, lo = 0.f;
+            auto add = [&hi, &lo](float t) {
+                const float sm = hi + t;
+                lo += fabsf(hi) >= fabsf(t) ? (hi - sm) + t : (t - sm) + hi;
+                hi = sm;
+            };
             int q = 0;
-            for (; q + 3 < I.chunks; q += 4) {
-                p0 += part[(int64_t)q * n + i];
-                p1 += part[(int64_t)(q + 1) * n + i];
-                p2 += part[(int64_t)(q + 2) * n + i];
-                p3 += part[(int64_t)(q + 3) * n + i];
+            for (; q + 3 < I.chunks; q += 4) {  // four loads in flight, added in order
+                const float t0 = part[(int64_t)q * n + i], t1 = part[(int64_t)(q + 1) * n + i];
+                const float t2 = part[(int64_t)(q + 2) * n + i], t3 = part[(int64_t)(q + 3) * n + i];
+                add(t0);
+                add(t1);
+                add(t2);
+                add(t3);
             }
-            for (; q < I.chunks; ++q) p0 += part[(int64_t)q * n + i];
-            double v = ((p0 + p1) + (p2 + p3)) * inv;
+            for (; q < I.chunks; ++q) add(part[(int64_t)q * n + i]);
+            double v = ((double)hi + (double)lo) * I.scale * inv;
             if (u) v = fma(-nrm, u[i], v);
             const int64_t vi = seg_base[sx] + (i - seg_i0[sx]);
             if (RBF_IN_RANGE(vi, a.rmax)) vs[vi] = v;
@@ -476,7 +485,7 @@ constexpr int N_CANDS = sizeof(MF_CANDS) / sizeof(MF_CANDS[0]);
 
 template <int TRANS>
 void launch_mf_cand(int c, int items, cudaStream_t s, const MfItem* it, const BInst* in, const float* X32,
-                    const float* x32, double* part, const int* done) {
+                    const float* x32, float* part, const int* done) {
     if (c == 0) k_mf_batch<TRANS, 4><<<items, MS_W * 32, 0, s>>>(it, in, X32, x32, part, done);
     else k_mf_batch<TRANS, 8><<<items, MS_W * 32, 0, s>>>(it, in, X32, x32, part, done);
 }
@@ -657,7 +666,7 @@ struct BatchWs {
     BInst* inst;
     int64_t* offs;
     MfItem* items;
-    double* part;
+    float* part;  // the products' partial slots (FP32 runs, unscaled)
     float* X32;  // node coordinates rounded to FP32, like the nodes [3][n] per instance
     double* hpart;
     double* h;
@@ -678,7 +687,7 @@ size_t batch_ws_layout(const BatchPlan& P, size_t n_items_max, BatchWs* w, void*
     t.inst = wc.take<BInst>(P.B);
     t.offs = wc.take<int64_t>(P.B + 1);
     t.items = wc.take<MfItem>(n_items_max);
-    t.part = wc.take<double>(P.part_max);
+    t.part = wc.take<float>(P.part_max);
     t.X32 = wc.take<float>((size_t)3 * P.T);
     t.hpart = wc.take<double>(P.hpart_total);
     t.h = wc.take<double>((size_t)P.B * (P.L + 2));

@@ -149,10 +149,13 @@ __device__ __forceinline__ void ms_dispatch(int rt, int ct, const MfNode* cols, 
 // I*B + lane + 32 r (r < R).  Writes the contributions to the outputs of block
 // I into slot J (part[J][.]) and, for I < J, those to the outputs of block J
 // into slot I.  X: FP32 node coordinates SoA [3][n]; x32: the FP32 input.
-template <int TRANS, int R>
+// SlotT double: a slot holds the FP64 value of the FP32 run times scale;
+// SlotT float: the FP32 run itself, unscaled (the batched half-step adds the
+// slots with compensated FP32 sums and applies scale).
+template <int TRANS, int R, typename SlotT = double>
 __device__ __forceinline__ void ms_tile_product(const float* __restrict__ X, int64_t n, int64_t ni, float c2,
                                                 float k2, double scale, const float* __restrict__ x32, int64_t I,
-                                                int64_t J, double* __restrict__ part) {
+                                                int64_t J, SlotT* __restrict__ part) {
     constexpr int NP = R / 2, B = 32 * R, CW = B / MS_W;  // CW columns per warp
     static_assert(CW % 32 == 0, "a warp takes whole groups of 32 columns");
     __shared__ MfNode cols[MS_W][32];
@@ -209,7 +212,10 @@ __device__ __forceinline__ void ms_tile_product(const float* __restrict__ X, int
             for (int m = 0; m < 32; ++m) v[m & 3] += colpart[warp][lane][m];
             const float vs = (v[0] + v[1]) + (v[2] + v[3]);
             const int64_t j = cb + lane;
-            if (j < n) part[I * n + j] = scaled ? (double)vs * scale : (double)vs;
+            if (j < n) {
+                if constexpr (sizeof(SlotT) == sizeof(float)) part[I * n + j] = vs;
+                else part[I * n + j] = scaled ? (double)vs * scale : (double)vs;
+            }
             __syncwarp();
         }
     }
@@ -228,7 +234,10 @@ __device__ __forceinline__ void ms_tile_product(const float* __restrict__ X, int
         float acc = 0.f;
 #pragma unroll
         for (int w = 0; w < MS_W; ++w) acc += own[w][r][l];
-        if (i < n) part[J * n + i] = scaled ? (double)acc * scale : (double)acc;
+        if (i < n) {
+            if constexpr (sizeof(SlotT) == sizeof(float)) part[J * n + i] = acc;
+            else part[J * n + i] = scaled ? (double)acc * scale : (double)acc;
+        }
     }
 }
 
