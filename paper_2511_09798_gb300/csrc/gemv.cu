@@ -242,6 +242,22 @@ __global__ void k_reduce_partials(int64_t n, int chunks, const double* __restric
     y[i] = s;
 }
 
+// y_i = scale * (sum of the FP32 slots of row i), added in slot order by a
+// compensated (Neumaier) FP32 sum carried to FP64 as hi + lo.
+__global__ void k_reduce_slots_f32(int64_t n, int chunks, const float* __restrict__ part, double scale,
+                                   double* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float hi = 0.f, lo = 0.f;
+    for (int q = 0; q < chunks; ++q) {
+        const float t = part[(int64_t)q * n + i];
+        const float sm = hi + t;
+        lo += fabsf(hi) >= fabsf(t) ? (hi - sm) + t : (t - sm) + hi;
+        hi = sm;
+    }
+    y[i] = ((double)hi + (double)lo) * scale;
+}
+
 __global__ void k_to_f32(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) y[i] = (float)x[i];
@@ -405,6 +421,12 @@ rbf_status launch_reduce_partials(rbf_ctx* ctx, int64_t n, int chunks, const dou
     return RBF_OK;
 }
 
+rbf_status launch_reduce_slots_f32(rbf_ctx* ctx, int64_t n, int chunks, const float* part, double scale, double* y) {
+    k_reduce_slots_f32<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, chunks, part, scale, y);
+    RBF_LAUNCHED(ctx, "k_reduce_slots_f32");
+    return RBF_OK;
+}
+
 rbf_status launch_to_f32(rbf_ctx* ctx, int64_t n, const double* x, float* y, cudaStream_t s) {
     k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s ? s : ctx->stream>>>(n, x, y);
     RBF_LAUNCHED(ctx, "k_to_f32");
@@ -429,6 +451,9 @@ extern "C" rbf_status rbf_matvec(rbf_ctx* ctx, const rbf_operator* op, int trans
             RBF_TRY(launch_to_f32(ctx, 3 * n, op->d_nodes, X32));
         }
         RBF_TRY(launch_mf_partial(ctx, op, trans, d_x, x32, X32, part, nullptr));
+        if (mf_slots_f32(ctx, op))
+            return launch_reduce_slots_f32(ctx, n, mf_chunks(ctx, op), (const float*)part,
+                                           op->form == RBF_FORM_EPS ? 1.0 / op->c : 1.0, d_y);
         return launch_reduce_partials(ctx, n, mf_chunks(ctx, op), part, d_y);
     }
     RBF_TRY(rbf_ws_reserve(ctx, gemv_ws_bytes(ctx, n)));

@@ -138,6 +138,10 @@ __device__ __forceinline__ void cp_async8(double* smem_dst, const double* gsrc) 
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 struct HalfArgs {
@@ -145,6 +149,8 @@ struct HalfArgs {
     int64_t n;
     int chunks;
     const double* part;   // product partials [chunks][n]
+    const float* part32;  // or FP32 slots [chunks][n] (unscaled FP32 runs), null otherwise
+    double slot_scale;    // scale of the FP32 slots (1 or 1/c)
     int side;             // 0: r-side (beta_j), 1: p-side (alpha_j)
     int j;                // 1-based step
     int resume;           // first r-side of a resumed run: scalars are preset
@@ -199,16 +205,23 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
     const int M = a.mcount;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double* Qs = dsm;                                 // [M][RM]   (STAGE)
-    double* ps = Qs + (STAGE ? (size_t)M * RM : 0);   // [chunks][RM]
-    double* vs = ps + (size_t)a.chunks * RM;          // [RM]  v' of the slab
+    double* ps = Qs + (STAGE ? (size_t)M * RM : 0);   // [chunks][RM] (FP32 slots: half of it)
+    double* vs = ps + (a.part32 ? ((size_t)a.chunks * RM + 1) / 2 : (size_t)a.chunks * RM);  // [RM]  v' of the slab
     double* us = vs + RM;                             // [RM]  u of the slab
     double* qs = us + RM;                             // [RM]  q_raw of the slab
     double* r4 = qs + RM;                             // [SPLIT][RM]  (partial sums only)
     double* d4 = r4;                                  // [SPLIT][M]   (passes only: shares r4's space)
     double* hs = d4 + (size_t)SPLIT * M;              // [M]   Q^T v'
     // ---- stage the slab's product partials, u, q_raw and (STAGE) its rows of Q
-    for (int q = warp; q < a.chunks; q += SL_WARPS)
-        for (int i = lane; i < R; i += 32) cp_async8(ps + (size_t)q * RM + i, a.part + (int64_t)q * a.n + s.r0 + i);
+    if (a.part32) {
+        float* ps32 = (float*)ps;
+        for (int q = warp; q < a.chunks; q += SL_WARPS)
+            for (int i = lane; i < R; i += 32)
+                cp_async4(ps32 + (size_t)q * RM + i, a.part32 + (int64_t)q * a.n + s.r0 + i);
+    } else {
+        for (int q = warp; q < a.chunks; q += SL_WARPS)
+            for (int i = lane; i < R; i += 32) cp_async8(ps + (size_t)q * RM + i, a.part + (int64_t)q * a.n + s.r0 + i);
+    }
     for (int i = threadIdx.x; i < R; i += SL_THREADS) {
         if (a.u) cp_async8(us + i, a.u + s.r0 + i);
         cp_async8(qs + i, a.q_raw + s.r0 + i);
@@ -273,24 +286,42 @@ __global__ void __launch_bounds__(SL_THREADS) k_half(HalfArgs a) {
             }
         }
     }
-    // ---- R1: v' = (sum of partials) - fu u, the chunk sum split SPLIT ways
+    // ---- R1: v' = (sum of partials) - fu u: FP64 partials split SPLIT ways;
+    // FP32 slots added in order by a compensated (Neumaier) FP32 sum, hi + lo
+    // carried to FP64 and scaled
     const double fu = fu_s;
-    for (int p = threadIdx.x; p < SPLIT * R; p += SL_THREADS) {
-        const int i = p % R, k = p / R;
-        double t0 = 0.0, t1 = 0.0;
-        int q = k;
-        for (; q + SPLIT < a.chunks; q += 2 * SPLIT) {
-            t0 += ps[(size_t)q * RM + i];
-            t1 += ps[(size_t)(q + SPLIT) * RM + i];
+    if (a.part32) {
+        const float* ps32 = (const float*)ps;
+        for (int i = threadIdx.x; i < R; i += SL_THREADS) {
+            float hi = 0.f, lo = 0.f;
+            for (int q = 0; q < a.chunks; ++q) {
+                const float t = ps32[(size_t)q * RM + i];
+                const float sm = hi + t;
+                lo += fabsf(hi) >= fabsf(t) ? (hi - sm) + t : (t - sm) + hi;
+                hi = sm;
+            }
+            double v = ((double)hi + (double)lo) * a.slot_scale;
+            if (a.u) v = fma(-fu, us[i], v);
+            vs[i] = v;
         }
-        if (q < a.chunks) t0 += ps[(size_t)q * RM + i];
-        r4[(size_t)k * RM + i] = t0 + t1;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < R; i += SL_THREADS) {
-        double v = (r4[i] + r4[RM + i]) + (r4[2 * RM + i] + r4[3 * RM + i]);
-        if (a.u) v = fma(-fu, us[i], v);
-        vs[i] = v;
+    } else {
+        for (int p = threadIdx.x; p < SPLIT * R; p += SL_THREADS) {
+            const int i = p % R, k = p / R;
+            double t0 = 0.0, t1 = 0.0;
+            int q = k;
+            for (; q + SPLIT < a.chunks; q += 2 * SPLIT) {
+                t0 += ps[(size_t)q * RM + i];
+                t1 += ps[(size_t)(q + SPLIT) * RM + i];
+            }
+            if (q < a.chunks) t0 += ps[(size_t)q * RM + i];
+            r4[(size_t)k * RM + i] = t0 + t1;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < R; i += SL_THREADS) {
+            double v = (r4[i] + r4[RM + i]) + (r4[2 * RM + i] + r4[3 * RM + i]);
+            if (a.u) v = fma(-fu, us[i], v);
+            vs[i] = v;
+        }
     }
     __syncthreads();
     if (brk_s) {
@@ -439,9 +470,10 @@ static size_t half_stage_limit(const rbf_ctx* ctx) {
     return (size_t)200 * 1024 / (size_t)lanes - 4 * 1024;
 }
 
-static size_t half_smem_bytes(bool stage, int mcount, int chunks, int rmax) {
+static size_t half_smem_bytes(bool stage, int mcount, int chunks, int rmax, bool f32slots) {
     const size_t scratch = std::max((size_t)SPLIT * rmax, (size_t)(SPLIT + 1) * mcount);
-    return ((stage ? (size_t)mcount * rmax : 0) + (size_t)chunks * rmax + (size_t)3 * rmax + scratch) * sizeof(double);
+    const size_t slots = f32slots ? ((size_t)chunks * rmax + 1) / 2 : (size_t)chunks * rmax;
+    return ((stage ? (size_t)mcount * rmax : 0) + slots + (size_t)3 * rmax + scratch) * sizeof(double);
 }
 
 static int slab_grid(const rbf_ctx* ctx, int64_t n) {
@@ -509,6 +541,8 @@ struct GkbRun {
     int G = 0, chT = 0, chN = 0, rmax = 0, bar_group = 0, bar_k = 0, j_begin = 1;
     double *part = nullptr, *vr = nullptr, *vp = nullptr, *hpart = nullptr, *gpart = nullptr, *npart = nullptr;
     float *vr32 = nullptr, *vp32 = nullptr, *X32 = nullptr;  // X32: FP32 node coordinates (matrix-free FP32)
+    bool f32slots = false;    // the products' partials are FP32 slots (mf_slots_f32)
+    double slot_scale = 1.0;  // their scale
     unsigned* bar = nullptr;
     const double* q_raw = nullptr;
     unsigned epochs = 0;  // barriers on `bar` since it was zeroed
@@ -527,6 +561,8 @@ struct GkbRun {
         WsCarve wc(ctx->ws);
         chT = product_chunks(ctx, op, 1);
         chN = product_chunks(ctx, op, 0);
+        f32slots = mf_slots_f32(ctx, op);
+        slot_scale = op->form == RBF_FORM_EPS ? 1.0 / op->c : 1.0;
         const int prow = op->storage == RBF_MATRIX_FREE ? mf_part_rows(ctx, op) : 0;
         part = wc.take<double>((size_t)std::max(prow, std::max(chT, chN)) * n);
         vr = wc.take<double>((size_t)n);
@@ -552,7 +588,7 @@ struct GkbRun {
         // the step, so long runs on large N stage their early steps only); the
         // unstaged kernel must fit for the largest basis.
         {
-            const size_t need = half_smem_bytes(false, st->capacity + 1, chmax, rmax);
+            const size_t need = half_smem_bytes(false, st->capacity + 1, chmax, rmax, f32slots);
             if (need > HALF_SMEM_STAGE_MAX)
                 return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "half-step shared memory too large (%zu bytes)", need);
             if (need > 48 * 1024)
@@ -594,6 +630,8 @@ struct GkbRun {
         a.n = n;
         a.chunks = chunks;
         a.part = part;
+        a.part32 = f32slots ? (const float*)part : nullptr;
+        a.slot_scale = slot_scale;
         a.side = side;
         a.j = j;
         a.resume = resume;
@@ -619,8 +657,8 @@ struct GkbRun {
         a.epoch0 = epochs;
         a.budget = ctx->opt.wait_budget;
         void* args[] = {&a};
-        const bool stage = half_smem_bytes(true, mcount, chunks, rmax) <= half_stage_limit(ctx);
-        const size_t smem = half_smem_bytes(stage, mcount, chunks, rmax);
+        const bool stage = half_smem_bytes(true, mcount, chunks, rmax, f32slots) <= half_stage_limit(ctx);
+        const size_t smem = half_smem_bytes(stage, mcount, chunks, rmax, f32slots);
         const int slot = rbf_prod_begin(ctx, 2);
         cudaError_t e = cudaLaunchCooperativeKernel(stage ? (const void*)k_half<true> : (const void*)k_half<false>,
                                                     dim3(G), dim3(SL_THREADS), args, smem, ctx->stream);
@@ -754,7 +792,7 @@ extern "C" rbf_status rbf_gkb_many(rbf_ctx* ctx, int count, const rbf_operator* 
         const int G = slab_grid(ctx, n);
         const int rmax = (int)((n + G - 1) / G) | 1;
         const int chmax = std::max(product_chunks(ctx, &ops[i], 0), product_chunks(ctx, &ops[i], 1));
-        const size_t need = half_smem_bytes(false, states[i].capacity + 1, chmax, rmax);
+        const size_t need = half_smem_bytes(false, states[i].capacity + 1, chmax, rmax, mf_slots_f32(ctx, &ops[i]));
         if (need > HALF_SMEM_STAGE_MAX) continue;  // the run itself is refused with RBF_ERR_UNSUPPORTED below
         int per_sm = 0;
         if (need > 48 * 1024)

@@ -183,6 +183,11 @@ rbf_status launch_reduce_partials(rbf_ctx* ctx, int64_t n, int chunks, const dou
 // (mf_part_rows >= mf_chunks; the FP32 tile-pair product folds its slots).
 int mf_chunks(const rbf_ctx* ctx, const rbf_operator* op);
 int mf_part_rows(const rbf_ctx* ctx, const rbf_operator* op);
+// FP32 matrix-free products whose partial slots are the FP32 runs themselves
+// (unscaled floats, added by the consumer with a compensated FP32 sum and
+// multiplied by the form's scale): every FP32 matrix-free plan without a fold.
+bool mf_slots_f32(const rbf_ctx* ctx, const rbf_operator* op);
+rbf_status launch_reduce_slots_f32(rbf_ctx* ctx, int64_t n, int chunks, const float* part, double scale, double* y);
 size_t mf_ws_bytes(const rbf_ctx* ctx, int64_t n);
 // x: FP64 input (FP64 operators); x32 and X32 (the node coordinates, SoA
 // [3][n], rounded to FP32): inputs of FP32 operators.

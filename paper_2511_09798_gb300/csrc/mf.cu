@@ -45,19 +45,21 @@ __device__ __forceinline__ void ms_tile(int64_t t, int64_t nb, int64_t& I, int64
     J = nb - 1 - (u - r * (r + 1) / 2);
 }
 
-// One tile per CTA, tiles in the order of ms_tile.  When the half-step would
-// stage too many slots, the slots are written after G group rows and folded
-// into them (k_ms_fold); otherwise part holds the nb slots directly.
-template <int TRANS, int R>
+// One tile per CTA, tiles in the order of ms_tile.  Without a fold the nb
+// slots hold the FP32 runs themselves (SlotT float; the consumer adds them with
+// a compensated FP32 sum and applies scale); when the half-step would stage
+// too many slots they are FP64 (run times scale), written after G group rows
+// and folded into them (k_ms_fold).
+template <int TRANS, int R, typename SlotT>
 __global__ void __launch_bounds__(MS_W * 32) k_mf_sym(const float* __restrict__ X, int64_t n, int64_t ni, float c2,
                                                     float k2, double scale, const float* __restrict__ x32,
-                                                    int64_t nb, double* __restrict__ part,
+                                                    int64_t nb, SlotT* __restrict__ part,
                                                     const int* __restrict__ done) {
     if (gkb_done(done)) return;
     int64_t I, J;
     ms_tile(blockIdx.x, nb, I, J);
     if (!RBF_IN_RANGE(J, nb) || !RBF_IN_RANGE(I, J + 1)) return;  // a tile of the triangle: slots I, J < nb
-    ms_tile_product<TRANS, R>(X, n, ni, c2, k2, scale, x32, I, J, part);
+    ms_tile_product<TRANS, R, SlotT>(X, n, ni, c2, k2, scale, x32, I, J, part);
 }
 
 // Fold the nb slots (rows G .. G + nb - 1 of the partial buffer) into G
@@ -244,7 +246,7 @@ MsPlan ms_plan(const rbf_ctx* ctx, int64_t n, bool fp64) {
         pl.R = MD_R;
         pl.nb = (n + 32 * MD_R - 1) / (32 * MD_R);
     } else if (t8 >= (int64_t)ctx->sm_count *
-                         pair_occupancy(occ, ctx, k_mf_sym<0, 8>, k_mf_sym<1, 8>, MS_W * 32, 4)) {
+                         pair_occupancy(occ, ctx, k_mf_sym<0, 8, double>, k_mf_sym<1, 8, double>, MS_W * 32, 4)) {
         pl.R = 8;
         pl.nb = nb8;
     } else {
@@ -270,6 +272,10 @@ MsPlan ms_plan(const rbf_ctx* ctx, int64_t n, bool fp64) {
 
 int mf_chunks(const rbf_ctx* ctx, const rbf_operator* op) {
     return ms_plan(ctx, op->n, op->precision == RBF_FP64).G;
+}
+
+bool mf_slots_f32(const rbf_ctx* ctx, const rbf_operator* op) {
+    return op->storage == RBF_MATRIX_FREE && op->precision != RBF_FP64 && ms_plan(ctx, op->n, false).k == 1;
 }
 
 int mf_part_rows(const rbf_ctx* ctx, const rbf_operator* op) {
@@ -305,13 +311,24 @@ rbf_status launch_mf_partial(rbf_ctx* ctx, const rbf_operator* op, int trans, co
     } else {
         if (!X32 || !x32) return rbf_fail(ctx, RBF_ERR_INTERNAL, "FP32 product without its FP32 inputs");
         const float c2 = (float)(op->c * op->c), k2 = (float)(op->k * op->k);
-        if (pl.R == 8) {
-            if (trans) k_mf_sym<1, 8><<<grid, MS_W * 32, 0, ctx->stream>>>(X32, n, ni, c2, k2, scale, x32, pl.nb, slots, done);
-            else k_mf_sym<0, 8><<<grid, MS_W * 32, 0, ctx->stream>>>(X32, n, ni, c2, k2, scale, x32, pl.nb, slots, done);
+#define MS_LAUNCH(T_, R_, S_) \
+    k_mf_sym<T_, R_, S_><<<grid, MS_W * 32, 0, ctx->stream>>>(X32, n, ni, c2, k2, scale, x32, pl.nb, (S_*)slots, done)
+        if (pl.k == 1) {  // FP32 slots
+            if (pl.R == 8) {
+                if (trans) MS_LAUNCH(1, 8, float);
+                else MS_LAUNCH(0, 8, float);
+            } else {
+                if (trans) MS_LAUNCH(1, 4, float);
+                else MS_LAUNCH(0, 4, float);
+            }
+        } else if (pl.R == 8) {
+            if (trans) MS_LAUNCH(1, 8, double);
+            else MS_LAUNCH(0, 8, double);
         } else {
-            if (trans) k_mf_sym<1, 4><<<grid, MS_W * 32, 0, ctx->stream>>>(X32, n, ni, c2, k2, scale, x32, pl.nb, slots, done);
-            else k_mf_sym<0, 4><<<grid, MS_W * 32, 0, ctx->stream>>>(X32, n, ni, c2, k2, scale, x32, pl.nb, slots, done);
+            if (trans) MS_LAUNCH(1, 4, double);
+            else MS_LAUNCH(0, 4, double);
         }
+#undef MS_LAUNCH
         RBF_LAUNCHED(ctx, "k_mf_sym");
     }
     if (pl.k > 1) {
