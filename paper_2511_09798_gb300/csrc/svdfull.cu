@@ -293,7 +293,14 @@ __global__ void k_fsvd_lift(const double* __restrict__ V, int64_t n, const int* 
 // ---------------------------------------------------------------------------
 constexpr int BT = 256;
 constexpr int BW = BT / 32;
+// the bidiagonalization kernel runs one CTA per SM of NT threads: 1024 above
+// n = 2048, so that enough loads of the trailing matrix are in flight (with 8
+// warps per SM the passes over it were bound by load latency: 1.26 -> 0.91 s
+// per GCV Tikhonov at n = 4000), 256 below (the per-step block reductions
+// over 32 warps cost more than they gain there: 48 -> 59 ms at n = 1000)
+constexpr int BIDIAG_BIG_N = 2048;
 
+template <int NW>
 __device__ __forceinline__ double block_sum1(double v, double* red) {
     v = warp_sum(v);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -302,7 +309,7 @@ __device__ __forceinline__ double block_sum1(double v, double* red) {
     __syncthreads();
     double t = 0.0;
 #pragma unroll
-    for (int w = 0; w < BW; ++w) t += red[w];
+    for (int w = 0; w < NW; ++w) t += red[w];
     return t;
 }
 
@@ -325,23 +332,25 @@ __device__ __forceinline__ void reflector(double x0, double ss, double* sc) {
 // W column-major n x (n+1) (ld n), the last column f.  On return: dg = diag
 // of B, eg = superdiagonal, column n = Q_L^T f, the right reflectors in rows
 // k (entries k+2..n-1, unscaled) with taur / scaler.
-__global__ void __launch_bounds__(BT) k_bidiag(double* __restrict__ W, int64_t n, double* __restrict__ dg,
+template <int NT>
+__global__ void __launch_bounds__(NT) k_bidiag(double* __restrict__ W, int64_t n, double* __restrict__ dg,
                                                double* __restrict__ eg, double* __restrict__ taur,
                                                double* __restrict__ scaler, rbf_dev_state* __restrict__ stt,
                                                unsigned* __restrict__ bar, int group, long long budget) {
-    __shared__ double red[BW];
+    constexpr int NW = NT / 32;
+    __shared__ double red[NW];
     __shared__ double sc[3];
-    __shared__ double rp[BW][32];
+    __shared__ double rp[NW][32];
     __shared__ double rw[32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t GW = (int64_t)gridDim.x * BW, gw = (int64_t)blockIdx.x * BW + warp;
+    const int64_t GW = (int64_t)gridDim.x * NW, gw = (int64_t)blockIdx.x * NW + warp;
     for (int64_t k = 0; k < n; ++k) {
         // left reflector of column k (rows k..n-1), every CTA computes it
         const double* xk = W + k * n + k;
         const int64_t m = n - k;
         double ss = 0.0;
-        for (int64_t i = 1 + threadIdx.x; i < m; i += BT) ss = fma(xk[i], xk[i], ss);
-        ss = block_sum1(ss, red);
+        for (int64_t i = 1 + threadIdx.x; i < m; i += NT) ss = fma(xk[i], xk[i], ss);
+        ss = block_sum1<NW>(ss, red);
         if (threadIdx.x == 0) reflector(xk[0], ss, sc);
         __syncthreads();
         const double tau = sc[0], scale = sc[1];
@@ -369,23 +378,23 @@ __global__ void __launch_bounds__(BT) k_bidiag(double* __restrict__ W, int64_t n
         // right reflector of row k (columns k+1..n-1)
         const int64_t m2 = n - k - 1;
         double ss2 = 0.0;
-        for (int64_t c = 1 + threadIdx.x; c < m2; c += BT) {
+        for (int64_t c = 1 + threadIdx.x; c < m2; c += NT) {
             const double y = W[(k + 1 + c) * n + k];
             ss2 = fma(y, y, ss2);
         }
-        ss2 = block_sum1(ss2, red);
+        ss2 = block_sum1<NW>(ss2, red);
         if (threadIdx.x == 0) reflector(W[(k + 1) * n + k], ss2, sc);
         __syncthreads();
         const double tau2 = sc[0], scale2 = sc[1];
         if (tau2 != 0.0) {
             // blocks of RB rows over the CTAs (RB = 32, 16 or 8: the largest that
             // still gives every CTA a block); lane = (row r, column lane cl), warp
-            // q takes the columns c = q CPL + cl, stepping by BW CPL (coalesced
+            // q takes the columns c = q CPL + cl, stepping by NW CPL (coalesced
             // along the rows); partial dots combined in shared memory in a fixed
             // order (for RB = 32 one column per warp step, as before)
             const int64_t rows = n - k - 1;
             const int RB = rows >= 32 * (int64_t)gridDim.x ? 32 : (rows >= 16 * (int64_t)gridDim.x ? 16 : 8);
-            const int CPL = 32 / RB, CW = BW * CPL;
+            const int CPL = 32 / RB, CW = NW * CPL;
             const int r = lane % RB, cl = lane / RB;
             const int64_t nblk = (rows + RB - 1) / RB;
             for (int64_t rb = blockIdx.x; rb < nblk; rb += gridDim.x) {
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(BT) k_bidiag(double* __restrict__ W, int64_t n
                 __syncthreads();
                 if (warp == 0 && lane < RB) {
                     double t = 0.0;
-                    for (int q = 0; q < BW; ++q)
+                    for (int q = 0; q < NW; ++q)
                         for (int l = 0; l < CPL; ++l) t += rp[q][l * RB + lane];
                     const int64_t ir = k + 1 + rb * RB + lane;
                     const double x0 = ir < n ? W[(k + 1) * n + ir] : 0.0;
@@ -449,7 +458,7 @@ __global__ void __launch_bounds__(BT) k_vt_g(const double* __restrict__ Vt, int6
     const double* v = Vt + (int64_t)blockIdx.x * n;
     double a = 0.0;
     for (int64_t k = threadIdx.x; k < n; k += BT) a = fma(v[k], g[k], a);
-    a = block_sum1(a, red);
+    a = block_sum1<BW>(a, red);
     if (threadIdx.x == 0) fhat[blockIdx.x] = a;
 }
 
@@ -479,7 +488,7 @@ __global__ void __launch_bounds__(BT) k_apply_qr(const double* __restrict__ W, i
         const double z0 = z[k + 1];
         double sd = 0.0;
         for (int64_t c = 1 + threadIdx.x; c < m2; c += BT) sd = fma(W[(k + 1 + c) * n + k], z[k + 1 + c], sd);
-        sd = block_sum1(sd, red);
+        sd = block_sum1<BW>(sd, red);
         const double t = tau * fma(scale, sd, z0);
         const double ts = t * scale;
         for (int64_t c = 1 + threadIdx.x; c < m2; c += BT) z[k + 1 + c] = fma(-ts, W[(k + 1 + c) * n + k], z[k + 1 + c]);
@@ -620,7 +629,10 @@ rbf_status fsvd_jacobi(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fs
 rbf_status fsvd_bidiag(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fsvd* F) {
     const int64_t n = op->n;
     int group, bar_k;
-    const int G = coop_grid(ctx, (const void*)k_bidiag, BT, ctx->sm_count, &group, &bar_k);
+    const bool big = n > BIDIAG_BIG_N;
+    const void* kbid = big ? (const void*)k_bidiag<1024> : (const void*)k_bidiag<256>;
+    const int nt = big ? 1024 : 256;
+    const int G = coop_grid(ctx, kbid, nt, ctx->sm_count, &group, &bar_k);
     const int J = ctx->opt.grid_j;
     const int L = (int)n;
     const size_t need = ws_align((size_t)n * (n + 1) * 8) + ws_align((size_t)n * n * 8) +
@@ -672,7 +684,7 @@ rbf_status fsvd_bidiag(rbf_ctx* ctx, const rbf_operator* op, const double* f, Fs
         int grp = group;
         long long budget = ctx->opt.wait_budget;
         void* args[] = {&Wp, &nn, &dp, &ep, &tp, &sp, &stt, &bp, &grp, &budget};
-        RBF_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_bidiag, dim3(G), dim3(BT), args, 0, s));
+        RBF_CUDA(ctx, cudaLaunchCooperativeKernel(kbid, dim3(G), dim3(nt), args, 0, s));
         ctx->launches++;
     }
     int err = 0;
