@@ -17,7 +17,8 @@
 //     (top-down and bottom-up LDL^T of T - s I, twist where |gamma| is
 //     smallest) gives the eigenvector without iteration.
 //  3. k_tgk_clusters one warp per cluster of close singular values (relative
-//     gap < cluster_tol): three steps of inverse iteration with the stored
+//     gap < cluster_tol; as many CTAs as needed for one cluster per warp):
+//     three steps of inverse iteration with the stored
 //     factorizations, all members in parallel lanes, Gram-Schmidt in order
 //     (the scheme of LAPACK's dstein), so the cluster basis is orthonormal.
 //  4. k_tgk_finalize split into u~ and v~, normalise, f~_i = beta_1 u~_i[0];
@@ -211,10 +212,14 @@ __global__ void k_tgk_vectors(ProjDims d, const double* __restrict__ alpha_all,
 constexpr int CL_WARPS = 8;
 constexpr int CL_MAX = 32;
 
+// Grid (B, gy): CTA y takes the clusters of index y CL_WARPS .. y CL_WARPS +
+// CL_WARPS - 1 (in the order of the descending singular values), one per warp;
+// every CTA finds them with the same scan.  A cluster's member vectors are
+// iterated in place in X.
 __global__ void k_tgk_clusters(ProjDims d, const double* __restrict__ sigma_all, double tol,
                                const double* __restrict__ invdp_all, const double* __restrict__ rp_all,
-                               double* __restrict__ X_all, double* __restrict__ tmp_all, int* __restrict__ cl_all) {
-    __shared__ int ncl;
+                               double* __restrict__ X_all) {
+    __shared__ int own_start[CL_WARPS], own_end[CL_WARPS];
     const int b = blockIdx.x;
     const int l = proj_l(d, b);
     if (l < 1) return;
@@ -224,67 +229,65 @@ __global__ void k_tgk_clusters(ProjDims d, const double* __restrict__ sigma_all,
     const double* invdp = invdp_all + sc;
     const double* rp = rp_all + sc;
     double* X = X_all + sc;
-    double* tmp = tmp_all + (size_t)b * CL_WARPS * CL_MAX * NT;
-    int* cl_start = cl_all + (size_t)b * (L + 2);  // at most l/2 clusters of >= 2 members
-    int* cl_end = cl_start + L / 2 + 1;
+    if (threadIdx.x < CL_WARPS) own_start[threadIdx.x] = -1;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        const int c0 = blockIdx.y * CL_WARPS;
         int c = 0;
         int i = 0;
-        while (i < l) {
+        while (i < l && c < c0 + CL_WARPS) {
             int j = i;
             while (j + 1 < l && j - i + 1 < CL_MAX && fabs(sigma[j] - sigma[j + 1]) < tol * sigma[j]) ++j;
             if (j > i) {
-                cl_start[c] = i;
-                cl_end[c] = j;
+                if (c >= c0) {
+                    own_start[c - c0] = i;
+                    own_end[c - c0] = j;
+                }
                 ++c;
             }
             i = j + 1;
         }
-        ncl = c;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nt = 2 * l + 1;
-    double* y = tmp + (size_t)warp * CL_MAX * NT;  // member vectors of this warp's cluster
-    for (int c = warp; c < ncl; c += CL_WARPS) {
-        const int a0 = cl_start[c], a1 = cl_end[c];
-        const int mcnt = a1 - a0 + 1;
-        // deterministic start vectors
-        for (int a = 0; a < mcnt; ++a)
-            for (int k = lane; k < nt; k += 32) y[(size_t)a * NT + k] = sin(0.7 * (double)(k + 1) * (a + 1) + 0.3);
+    const int a0 = own_start[warp];
+    if (a0 < 0) return;
+    const int a1 = own_end[warp];
+    const int mcnt = a1 - a0 + 1;
+    double* y = X + (size_t)a0 * NT;  // member vectors of this warp's cluster, in place
+    // deterministic start vectors
+    for (int a = 0; a < mcnt; ++a)
+        for (int k = lane; k < nt; k += 32) y[(size_t)a * NT + k] = sin(0.7 * (double)(k + 1) * (a + 1) + 0.3);
+    __syncwarp();
+    for (int it = 0; it < 3; ++it) {
+        // lane a solves (T - s_a I) x = y_a:  L D L^T with L_{k+1,k} = rp_k
+        if (lane < mcnt) {
+            const int ia = a0 + lane;
+            double* v = y + (size_t)lane * NT;
+            for (int k = 1; k < nt; ++k) v[k] = fma(-rp[(size_t)(k - 1) * L + ia], v[k - 1], v[k]);
+            for (int k = 0; k < nt; ++k) v[k] *= invdp[(size_t)k * L + ia];
+            for (int k = nt - 2; k >= 0; --k) v[k] = fma(-rp[(size_t)k * L + ia], v[k + 1], v[k]);
+        }
         __syncwarp();
-        for (int it = 0; it < 3; ++it) {
-            // lane a solves (T - s_a I) x = y_a:  L D L^T with L_{k+1,k} = rp_k
-            if (lane < mcnt) {
-                const int ia = a0 + lane;
-                double* v = y + (size_t)lane * NT;
-                for (int k = 1; k < nt; ++k) v[k] = fma(-rp[(size_t)(k - 1) * L + ia], v[k - 1], v[k]);
-                for (int k = 0; k < nt; ++k) v[k] *= invdp[(size_t)k * L + ia];
-                for (int k = nt - 2; k >= 0; --k) v[k] = fma(-rp[(size_t)k * L + ia], v[k + 1], v[k]);
-            }
-            __syncwarp();
-            // modified Gram-Schmidt in member order
-            for (int a = 0; a < mcnt; ++a) {
-                double* va = y + (size_t)a * NT;
-                for (int bb = 0; bb < a; ++bb) {
-                    const double* vb = y + (size_t)bb * NT;
-                    double dot = 0.0;
-                    for (int k = lane; k < nt; k += 32) dot = fma(vb[k], va[k], dot);
-                    dot = warp_sum(dot);
-                    for (int k = lane; k < nt; k += 32) va[k] = fma(-dot, vb[k], va[k]);
-                    __syncwarp();
-                }
-                double n2 = 0.0;
-                for (int k = lane; k < nt; k += 32) n2 = fma(va[k], va[k], n2);
-                n2 = warp_sum(n2);
-                const double inv = rsqrt(n2);
-                for (int k = lane; k < nt; k += 32) va[k] *= inv;
+        // modified Gram-Schmidt in member order
+        for (int a = 0; a < mcnt; ++a) {
+            double* va = y + (size_t)a * NT;
+            for (int bb = 0; bb < a; ++bb) {
+                const double* vb = y + (size_t)bb * NT;
+                double dot = 0.0;
+                for (int k = lane; k < nt; k += 32) dot = fma(vb[k], va[k], dot);
+                dot = warp_sum(dot);
+                for (int k = lane; k < nt; k += 32) va[k] = fma(-dot, vb[k], va[k]);
                 __syncwarp();
             }
+            double n2 = 0.0;
+            for (int k = lane; k < nt; k += 32) n2 = fma(va[k], va[k], n2);
+            n2 = warp_sum(n2);
+            const double inv = rsqrt(n2);
+            for (int k = lane; k < nt; k += 32) va[k] *= inv;
+            __syncwarp();
         }
-        for (int a = 0; a < mcnt; ++a)
-            for (int k = lane; k < nt; k += 32) X[(size_t)(a0 + a) * NT + k] = y[(size_t)a * NT + k];
-        __syncwarp();
     }
 }
 
@@ -374,9 +377,7 @@ size_t svd_ws_bytes_batch(int L, int B) {
     const size_t NT = 2 * (size_t)L + 1;
     size_t b = 0;
     b += 4 * ws_align(NT * L * 8 * B);            // X, invdp, rp, rm
-    b += ws_align((size_t)CL_WARPS * CL_MAX * NT * 8 * B);
     b += ws_align((size_t)8 * B);
-    b += ws_align((size_t)(L + 2) * 4 * B);  // cluster bounds
     return b + 4096;
 }
 
@@ -392,9 +393,7 @@ rbf_status launch_projected_svd_batch(rbf_ctx* ctx, ProjDims d, const double* al
     double* invdp = wc.take<double>(NT * L * B);
     double* rp = wc.take<double>(NT * L * B);
     double* rm = wc.take<double>(NT * L * B);
-    double* tmp = wc.take<double>((size_t)CL_WARPS * CL_MAX * NT * B);
     double* bound = wc.take<double>((size_t)B);
-    int* cl = wc.take<int>((size_t)(L + 2) * B);
     cudaStream_t s = ctx->stream;
     const size_t sh_b = 2 * (size_t)L * sizeof(double);  // also the vectors' e
     const size_t sh_f = ((size_t)L + 1) * sizeof(double);
@@ -408,7 +407,10 @@ rbf_status launch_projected_svd_batch(rbf_ctx* ctx, ProjDims d, const double* al
     RBF_LAUNCHED(ctx, "k_tgk_bisect");
     k_tgk_vectors<<<dim3((L + 31) / 32, B), 32, sh_b, s>>>(d, alpha, beta, sigma, bound, invdp, rp, rm, X);
     RBF_LAUNCHED(ctx, "k_tgk_vectors");
-    k_tgk_clusters<<<B, CL_WARPS * 32, 0, s>>>(d, sigma, ctx->opt.cluster_tol, invdp, rp, X, tmp, cl);
+    // at most l / 2 clusters of two or more: one warp each
+    const int gy = ((L + 1) / 2 + CL_WARPS - 1) / CL_WARPS;
+    if (gy > 65535) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "too many clusters for the grid");
+    k_tgk_clusters<<<dim3(B, gy), CL_WARPS * 32, 0, s>>>(d, sigma, ctx->opt.cluster_tol, invdp, rp, X);
     RBF_LAUNCHED(ctx, "k_tgk_clusters");
     k_tgk_finalize<<<B, 256, sh_f, s>>>(d, alpha, beta, X, ftil, V, ldv, B == 1 ? ctx->d_state : nullptr, sigma,
                                         sigma1_out, ftil_last_out, U, ldu);
