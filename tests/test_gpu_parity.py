@@ -158,6 +158,28 @@ def test_matvec_mixed_matrix_free_tile_pairs(ctx, R, n, ni):
     assert np.array_equal(z0, y0) and np.array_equal(z1, y1)
 
 
+@pytest.mark.parametrize("n", [300, 5000])
+def test_mixed_matrix_free_eps_form(ctx, R, n):
+    """The eps form scales every entry by 1/c: the FP32 slots are unscaled runs
+    and the consumers (the matvec's reduction, the GKB half-step) apply 1/c.
+    Products against the dense eps-form oracle matrix, and the first GKB
+    scalars against the oracle's run (FP32 entries: rel <= 1e-5)."""
+    ns = random_nodes(n, (2 * n) // 3, n + 9)
+    c, k = 0.3, 3.0
+    op = ctx.rbf_operator_init(dev(ns.soa()), n, ns.n_interior, c, k, R.RBF_MATRIX_FREE, R.RBF_MIXED,
+                               R.RBF_FORM_EPS)
+    A = OM.assemble(ns.X, ns.n_interior, c, k, form="eps")
+    x, y0, y1 = _products(ctx, R, op, n, 8)
+    assert np.max(np.abs(y0 - A @ x) / (np.abs(A) @ np.abs(x))) < 1e-5
+    assert np.max(np.abs(y1 - A.T @ x) / (np.abs(A).T @ np.abs(x))) < 1e-5
+    f = w.plane_wave_rhs(ns, k)
+    g = OG.gkb(A, None, f, 6)
+    st, _, _, al, be = run_gkb(ctx, R, op, f, 6, n)
+    assert st.steps_done == 6
+    assert np.max(np.abs(al[:4] - g.alpha[:4]) / g.alpha[:4]) < 1e-5
+    assert np.max(np.abs(be[1:5] - g.beta[1:5]) / g.beta[1:5]) < 1e-5
+
+
 def test_matvec_mixed_matrix_free_folded_slots(ctx, R):
     """26 000 nodes: 102 blocks of 256, more partial slots than the half-step
     stages (71 at 172 rows per SM), folded in pairs before it.  Checked on
