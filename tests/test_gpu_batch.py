@@ -65,6 +65,20 @@ def _state_view(R, keep, bt, b, L):
     return st
 
 
+def test_batch_eps_form_against_oracle(ctx, R):
+    """Eps form: the batched half-step applies 1/c to its FP32 slot sums."""
+    sets, cs, ks, fs = _instances()
+    L = 10
+    bt, keep = R.make_batch(torch, sets, cs, ks, fs, L)
+    ctx.rbf_batch_gkb(bt, L, form=R.RBF_FORM_EPS)
+    alpha = keep["alpha"].cpu().numpy().reshape(len(sets), L)
+    beta = keep["beta"].cpu().numpy().reshape(len(sets), L + 1)
+    for b, (ns, c, k, f) in enumerate(zip(sets, cs, ks, fs)):
+        g = OG.gkb(OM.assemble(ns.X, ns.n_interior, c, k, form="eps"), None, f, L)
+        assert np.abs(alpha[b, 0] - g.alpha[0]) / g.alpha[0] < 1e-5, b
+        assert np.max(np.abs(beta[b, :2] - g.beta[:2]) / g.beta[:2]) < 1e-5, b
+
+
 def test_batch_against_oracle_and_single_path(ctx, R):
     sets, cs, ks, fs = _instances()
     L = 40
