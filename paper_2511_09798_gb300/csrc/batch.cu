@@ -48,6 +48,8 @@ struct MfItem {  // tile (bi, bj), bi <= bj, of instance b
 };
 
 constexpr int HB_THREADS = 256;
+constexpr int DG_LOG = 2;
+constexpr int DG = 1 << DG_LOG;  // basis vectors per warp in the half-step's dot products
 constexpr int HB_WARPS = HB_THREADS / 32;
 constexpr int SEGMAX = 16;       // instances intersecting one slab
 constexpr int UPD_ROWS_B = 64;
@@ -150,7 +152,7 @@ struct HalfBArgs {
     int rmax;
 };
 
-__global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
+__global__ void __launch_bounds__(HB_THREADS, 4) k_half_batch(HalfBArgs a) {
     extern __shared__ double dsm[];
     __shared__ int seg_b[SEGMAX], seg_base[SEGMAX], seg_act[SEGMAX], seg_brk[SEGMAX], seg_stop[SEGMAX];
     __shared__ int64_t seg_i0[SEGMAX], seg_i1[SEGMAX];
@@ -307,19 +309,40 @@ __global__ void __launch_bounds__(HB_THREADS) k_half_batch(HalfBArgs a) {
             const int rows = (int)(seg_i1[sx] - i0);
             const int cslot = blockIdx.x - I.cfirst;
             const double* v = vs + seg_base[sx];
-            // one warp per basis vector, lanes along the rows (coalesced loads of
-            // the basis column), reduced across the warp in a fixed order
-            for (int m = warp; m < M; m += HB_WARPS) {
-                const double* q = Q + (int64_t)m * I.n + i0;
-                double a0 = 0.0, a1 = 0.0;
-                int i = lane;
-                for (; i + 32 < rows; i += 64) {
-                    a0 = fma(q[i], v[i], a0);
-                    a1 = fma(q[i + 32], v[i + 32], a1);
+            // one warp per group of DG basis vectors, lanes along the rows
+            // (coalesced loads of the basis columns); the DG lane sums are
+            // reduced together by a transposing butterfly (offsets 16, 8, 4
+            // halve the vectors a lane holds, the smaller offsets finish): 6 FP64
+            // adds per lane for DG = 4 vectors instead of 5 per vector (8 vectors
+            // per warp spilled registers at 4 CTAs per SM and were slower)
+            for (int m0 = warp * DG; m0 < M; m0 += HB_WARPS * DG) {
+                const int gc = min(DG, M - m0);
+                double acc[DG];
+#pragma unroll
+                for (int g = 0; g < DG; ++g) acc[g] = 0.0;
+                const double* q = Q + (int64_t)m0 * I.n + i0;
+                for (int i = lane; i < rows; i += 32) {
+                    const double vi = v[i];
+#pragma unroll
+                    for (int g = 0; g < DG; ++g)
+                        if (g < gc) acc[g] = fma(q[(int64_t)g * I.n + i], vi, acc[g]);
                 }
-                if (i < rows) a0 = fma(q[i], v[i], a0);
-                const double t = warp_sum(a0 + a1);
-                if (lane == 0 && RBF_IN_RANGE(cslot, I.ncta) && RBF_IN_RANGE(m, L + 2))
+#pragma unroll
+                for (int w = DG / 2, off = 16; w >= 1; w >>= 1, off >>= 1) {
+                    const bool hi = (lane & off) != 0;
+#pragma unroll
+                    for (int g = 0; g < w; ++g) {
+                        const double send = hi ? acc[g] : acc[g + w];
+                        const double keep = hi ? acc[g + w] : acc[g];
+                        acc[g] = keep + __shfl_xor_sync(RBF_FULL_MASK, send, off);
+                    }
+                }
+                double t = acc[0];
+#pragma unroll
+                for (int off = 16 >> DG_LOG; off >= 1; off >>= 1) t += __shfl_xor_sync(RBF_FULL_MASK, t, off);
+                const int m = m0 + ((lane >> (5 - DG_LOG)) & (DG - 1));  // the vector lane holds
+                if ((lane & ((32 >> DG_LOG) - 1)) == 0 && m < M && RBF_IN_RANGE(cslot, I.ncta) &&
+                    RBF_IN_RANGE(m, L + 2))
                     a.hpart_all[I.hoff + (int64_t)m * I.ncta + cslot] = t;
             }
         }
