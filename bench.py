@@ -56,6 +56,7 @@ FP32_LANE_TOPS = 152 * 128 * 2.07e9 / 1e12  # FP32 pipe: one operation per lane 
 # DRAM bytes (read + write) per launch of the dominant product kernel, from one
 # ncu capture of that kernel at the workload's size (dram__bytes_read.sum +
 # dram__bytes_write.sum); None where the kernel changed after its capture.
+FX_MAX_N = 16384  # FP64 assembled operators up to this size take the fixed-point products
 MEASURED_TRAFFIC = {
     ("cube8000", 0): 512.113e6 + 0.166e6,                      # k_gemv_flat_f64
     ("cube8000", 1): 512.116e6 + 4.010e6,                      # k_gemv_t_f64
@@ -281,7 +282,8 @@ def run_ours(args, rank, world, local_rank):
     prec = R.RBF_FP64 if wl["precision"] == "fp64" else R.RBF_MIXED
     storage = R.RBF_ASSEMBLED if wl["storage"] == "assembled" else R.RBF_MATRIX_FREE
     stream = torch.cuda.current_stream()
-    ctx = R.Context(local_rank, stream=stream, timing=2)
+    fma = int(bool(getattr(args, "fma_products", False)))
+    ctx = R.Context(local_rank, stream=stream, timing=2, fma_products=fma)
     n, m = ns.n, wl["points"].shape[0]
     # device-resident inputs
     nodes_h = torch.from_numpy(ns.soa()).pin_memory()
@@ -366,7 +368,7 @@ def run_ours(args, rank, world, local_rank):
     forms = forms_comparison(local_rank) if wl["name"] == "cube8000" and not args.no_forms else None
     mf_roof = mf_product_roofline(local_rank) if wl["name"] == "cube8000" and not args.no_forms else None
     # phase shares (separate context with synchronising per-phase timers)
-    ctx_ph = R.Context(local_rank, stream=stream, timing=1)
+    ctx_ph = R.Context(local_rank, stream=stream, timing=1, fma_products=fma)
     phases = {}
     for ci, (c, k) in enumerate(cases[:1]):
         op = ctx_ph.rbf_operator_init(nodes_d, n, ns.n_interior, c, k, storage, prec, R.RBF_FORM_C,
@@ -400,7 +402,19 @@ def run_ours(args, rank, world, local_rank):
     if storage == R.RBF_ASSEMBLED:
         alg_bytes = s * n * n
         gbs = alg_bytes / (avg_ms / 1e3) / 1e9
-        if prec == R.RBF_FP64:
+        fixed_point = prec == R.RBF_FP64 and not fma and n <= FX_MAX_N
+        if fixed_point:
+            # exact integer fixed-point products (k_gemv_flat_fx, k_gemv_t_fx): the
+            # FP64 pipe is out of the inner loop and HBM is the bound
+            tflops = 2.0 * n * n / (avg_ms / 1e3) / 1e12
+            roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": round(gbs / peaks.get("hbm_gbs", 6790.7), 4), "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                    "arithmetic": "int64 fixed point: 6 IMAD.WIDE (32x32+64) per 8-byte entry, exact sums, "
+                                  "one FP64 rounding per partial",
+                    "fp64_fma_equivalent_tflops": round(tflops, 4),
+                    "fp64_fma_equivalent_frac_of_fp64_peak": round(tflops / FP64_PEAK_TFLOPS, 4)}
+        elif prec == R.RBF_FP64:
             tflops = 2.0 * n * n / (avg_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
                     "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": None,
@@ -423,8 +437,10 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": "152 SMs x 2 FP64 ops/clk x 2.07 GHz (unit counts and max clock)"}
     else:
         roof = mf_roofline(n, ns.n_interior, avg_ms)
-    roof["traffic"] = MEASURED_TRAFFIC.get((wl["name"], dom))
-    kname = ("gemv_n (p = A z) and gemv_t (r = A^T w)" if storage == R.RBF_ASSEMBLED
+    fixed_point = storage == R.RBF_ASSEMBLED and prec == R.RBF_FP64 and not fma and n <= FX_MAX_N
+    roof["traffic"] = MEASURED_TRAFFIC.get((wl["name"] + ("-fx" if fixed_point else ""), dom))
+    kname = ("k_gemv_flat_fx (p = A z) and k_gemv_t_fx (r = A^T w), int64 fixed point" if fixed_point
+             else "gemv_n (p = A z) and gemv_t (r = A^T w)" if storage == R.RBF_ASSEMBLED
              else ("k_mf_sym_f64" if prec == R.RBF_FP64 else "k_mf_sym") + " (p = A z, r = A^T w, matrix-free)")
     roof.update({"kernel": kname, "avg_launch_ms": round(avg_ms, 5),
                  "avg_launch_ms_how": "union of the product launch intervals / launches (CUDA events on the "
@@ -1381,7 +1397,7 @@ def single_solve(args):
     ns, (c, k), L = wl["ns"], wl["cases"][0], wl["steps"]
     prec = R.RBF_FP64 if wl["precision"] == "fp64" else R.RBF_MIXED
     storage = R.RBF_ASSEMBLED if wl["storage"] == "assembled" else R.RBF_MATRIX_FREE
-    ctx = R.Context(0)
+    ctx = R.Context(0, fma_products=int(args.fma_products))
     n, m = ns.n, wl["points"].shape[0]
     nodes = torch.from_numpy(ns.soa()).cuda()
     pts = torch.from_numpy(wl["points"].T.copy()).cuda()
@@ -1420,6 +1436,8 @@ def main():
     ap.add_argument("--jsonl", default=None, help="also append the result line to this JSONL file")
     ap.add_argument("--single-solve", action="store_true",
                     help="run one untimed solve of the first case and exit (profiling target)")
+    ap.add_argument("--fma-products", action="store_true",
+                    help="FP64 assembled products with FP64 FMAs on A instead of the exact fixed-point copies")
     args = ap.parse_args()
     if args.single_solve:
         single_solve(args)

@@ -96,6 +96,20 @@ typedef struct {
                                 RBF_ERR_TIMEOUT instead of waiting for ever (default
                                 2^23, several seconds; a tiny value forces the timeout
                                 path, which leaves the context usable) */
+    int fma_products;        /* FP64 assembled operators, n <= 16384: GKB (and LSQR on
+                                its state) computes A z and A^T w in exact integer
+                                fixed point from two int64 copies of A made at the
+                                start of each run (2 x 8 n lda bytes more workspace).
+                                Sums are exact; every value is rounded at 2^-62 of the
+                                largest in its row / column / vector (exact for values
+                                within 2^9 of it), then one FP64 rounding per partial:
+                                error <~ 2^-61 (max|A_ij| |w|_1 + |A_.j|_1 max|w_i|) per
+                                output, below FP64 FMAs' for matrices like the
+                                collocation matrices, normwise rather than componentwise
+                                for rows / columns scaled over many orders of magnitude;
+                                not bound by the FP64 pipe.  1: FP64 FMAs on A itself
+                                instead.  Without room for the copies (the workspace cap
+                                or device memory) the FMA products run. */
 } rbf_options;
 
 /* Operator description; filled by rbf_operator_init. */
@@ -190,7 +204,9 @@ rbf_status rbf_destroy(rbf_ctx* ctx);
 const char* rbf_last_error(const rbf_ctx* ctx);
 
 /* Upper bound of the internal workspace bytes for a GKB of `steps` steps plus
- * the projected solve, for an operator of size n. */
+ * the projected solve, for an operator of size n (FP64 assembled, unless
+ * opt.fma_products: with the two fixed-point copies of A, lda = n rounded up
+ * to even). */
 size_t rbf_workspace_bytes(const rbf_ctx* ctx, int64_t n, int steps, int storage, int precision);
 
 /* Timings of the most recent calls (zeros unless opt.timing was set). */

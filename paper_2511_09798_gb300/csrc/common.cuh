@@ -43,6 +43,21 @@ __device__ __forceinline__ bool gkb_done(const int* done) {
     return done != nullptr && *(volatile const int*)done != 0;
 }
 
+// Flat split of a row-major n x n matrix over W warps (the A z products):
+// warp w owns the elements [b_w, b_{w+1}) with b_w = floor(n^2 w / W), its
+// column rounded down to a multiple of FLAT_ALIGN (16-byte aligned vector
+// loads, full 128-column blocks), so every warp streams the same number of
+// entries to within FLAT_ALIGN.  n^2 W stays far below 2^63 for any matrix
+// that fits in device memory.
+constexpr int64_t FLAT_ALIGN = 128;
+
+__device__ __forceinline__ int64_t flat_bound(int64_t n, int64_t W, int64_t w) {
+    if (w >= W) return n * n;
+    const int64_t b = n * n * w / W;
+    const int64_t r = b / n;
+    return r * n + ((b - r * n) & ~(FLAT_ALIGN - 1));
+}
+
 // Lambda grid coordinate t_idx = t_lo + idx * step, step = (t_hi - t_lo) /
 // (J - 1), rounded as two separate operations (no contraction); the last
 // point is exactly t_hi.

@@ -162,7 +162,7 @@ rbf_status rbf_check_all(rbf_ctx* ctx) {
     const Unit units[] = {{"ctx.cu", rbf_check_take_ctx},         {"gemv.cu", rbf_check_take_gemv},
                           {"gkb.cu", rbf_check_take_gkb},         {"batch.cu", rbf_check_take_batch},
                           {"select.cu", rbf_check_take_select},   {"assemble.cu", rbf_check_take_assemble},
-                          {"mf.cu", rbf_check_take_mf}};
+                          {"mf.cu", rbf_check_take_mf},           {"fx.cu", rbf_check_take_fx}};
     rbf_status st = RBF_OK;
     for (const Unit& u : units) {
         const unsigned line = u.take();
@@ -336,9 +336,14 @@ rbf_status rbf_get_timings(const rbf_ctx* ctx, rbf_timings* out) {
 }
 
 size_t rbf_workspace_bytes(const rbf_ctx* ctx, int64_t n, int steps, int storage, int precision) {
-    (void)storage;
     if (!ctx || n <= 0 || steps <= 0) return 0;
     size_t a = gkb_ws_bytes(ctx, n, steps, precision);
+    rbf_operator fake{};  // the fixed-point copies of an FP64 assembled operator (lda padded to even)
+    fake.n = n;
+    fake.lda = (n + 1) & ~(int64_t)1;
+    fake.storage = storage;
+    fake.precision = precision;
+    if (fx_eligible(ctx, &fake)) a += fx_ws_bytes(&fake);
     size_t b = svd_ws_bytes(steps) + select_ws_bytes(ctx, steps);
     size_t c = gemv_ws_bytes(ctx, n) + ws_align((size_t)n * 8) * 2 + 4096;
     size_t m = a > b ? a : b;

@@ -24,25 +24,12 @@ __device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p
 __device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
 
 // ---------------------------------------------------------------------------
-// FP64 A x by a flat split of the matrix: warp w (of W active warps) owns the
-// row-major elements [b_w, b_{w+1}) with b_w = floor(n^2 w / W), its column
-// rounded down to a multiple of 128 (16-byte aligned double2 loads, full
-// 128-column blocks), so every warp streams the same number of entries to
-// within 128.  Each row piece of a warp is
-// reduced across the warp and written to part[slot][row], slot = w minus the
-// first warp that touches the row; the warp holding the end of a row writes
-// zeros into the row's remaining slots, so part[0 .. chunks-1][row] always sum
-// to (A x)_row.  n^2 W stays far below 2^63 for any matrix that fits in
-// device memory.
+// FP64 A x by the flat split of the matrix (flat_bound): each row piece of a
+// warp is reduced across the warp and written to part[slot][row], slot = w
+// minus the first warp that touches the row; the warp holding the end of a
+// row writes zeros into the row's remaining slots, so part[0 .. chunks-1][row]
+// always sum to (A x)_row.
 // ---------------------------------------------------------------------------
-constexpr int64_t FLAT_ALIGN = 128;  // piece starts within a row: multiples of 128 columns
-
-__device__ __forceinline__ int64_t flat_bound(int64_t n, int64_t W, int64_t w) {
-    if (w >= W) return n * n;
-    const int64_t b = n * n * w / W;
-    const int64_t r = b / n;
-    return r * n + ((b - r * n) & ~(FLAT_ALIGN - 1));
-}
 
 __global__ void __launch_bounds__(GN_THREADS) k_gemv_flat_f64(
     const double* __restrict__ A, int64_t lda, int64_t n, const double* __restrict__ x, int64_t W, int chunks,
@@ -279,7 +266,7 @@ static void plan_t_sms(int sm_count, int64_t n, int vec, int* panel_cols, int* p
     *chunks = q;
 }
 
-static void plan_t(const rbf_ctx* ctx, int64_t n, int vec, int* panel_cols, int* panels, int* chunks) {
+void plan_t(const rbf_ctx* ctx, int64_t n, int vec, int* panel_cols, int* panels, int* chunks) {
     plan_t_sms(ctx->sm_count, n, vec, panel_cols, panels, chunks);
 }
 
@@ -321,9 +308,9 @@ static int gemv_n_occupancy(const rbf_ctx* ctx, bool fp64) {
 // into more than 8 pieces (the partial-sum rows the workspace provides).  A
 // row of n entries meets at most ceil(n / (per - 2)) + 1 warp ranges, per =
 // floor(n^2 / W) (each boundary is rounded down by at most one entry).
-static void gemv_flat_plan(const rbf_ctx* ctx, int64_t n, int* grid, int64_t* W_out, int* chunks) {
+void flat_split_plan(int64_t n, int64_t Wmax, int64_t* W_out, int* chunks) {
     const int64_t e = n * n;
-    int64_t W = (int64_t)ctx->sm_count * gemv_n_occupancy(ctx, true) * (GN_THREADS / 32);
+    int64_t W = Wmax;
     if (W > e / 256) W = e / 256;
     if (W < 1) W = 1;
     // a warp owns at least per - FLAT_ALIGN entries (each bound is rounded down
@@ -336,8 +323,12 @@ static void gemv_flat_plan(const rbf_ctx* ctx, int64_t n, int* grid, int64_t* W_
     };
     while (W > 1 && pieces(W) > 8) --W;
     *W_out = W;
-    *grid = (int)((W + GN_THREADS / 32 - 1) / (GN_THREADS / 32));
     *chunks = (int)pieces(W);
+}
+
+static void gemv_flat_plan(const rbf_ctx* ctx, int64_t n, int* grid, int64_t* W_out, int* chunks) {
+    flat_split_plan(n, (int64_t)ctx->sm_count * gemv_n_occupancy(ctx, true) * (GN_THREADS / 32), W_out, chunks);
+    *grid = (int)((*W_out + GN_THREADS / 32 - 1) / (GN_THREADS / 32));
 }
 
 // FP32 A x: grid = one wave of resident CTAs; S column segments per row chosen

@@ -503,6 +503,7 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
         fake.precision = prec;
         ch = std::max(ch, std::max(gemv_t_chunks(ctx, &fake), gemv_n_chunks(ctx, &fake)));
     }
+    ch = std::max(ch, 8);  // the fixed-point A z (flat split: at most 8 pieces per row)
     const int G = slab_grid(ctx, n);
     size_t b = 0;
     b += ws_align((size_t)ch * n * 8);                // partials
@@ -517,15 +518,31 @@ size_t gkb_ws_bytes(const rbf_ctx* ctx, int64_t n, int steps, int precision) {
 }
 
 // Launch the product "part = M q_raw" for one half-step.
+// fx: the run's fixed-point copies of A (FP64 assembled operators), or null.
 static rbf_status gkb_product(rbf_ctx* ctx, const rbf_operator* op, int trans, const double* q_raw,
-                              const float* q32, const float* X32, double* part, const int* done) {
+                              const float* q32, const float* X32, const FxCopies* fx, double* part,
+                              const int* done) {
     const int slot = rbf_prod_begin(ctx, trans);
     rbf_status st;
     if (op->storage == RBF_MATRIX_FREE) st = launch_mf_partial(ctx, op, trans, q_raw, q32, X32, part, done);
+    else if (fx) st = trans ? launch_fx_t(ctx, op, *fx, q_raw, part, done) : launch_fx_n(ctx, op, *fx, q_raw, part, done);
     else if (trans) st = launch_gemv_t_partial(ctx, op, q_raw, q32, part, done);
     else st = launch_gemv_n(ctx, op, q_raw, q32, part, done);
     rbf_prod_end(ctx, trans, slot);
     return st;
+}
+
+// Workspace of one GKB run on op: the fixed-point copies of A are included
+// (*fx = true) when the operator takes them and they fit under the cap.
+static size_t run_ws_bytes(const rbf_ctx* ctx, const rbf_operator* op, int capacity, bool* fx) {
+    const size_t base = gkb_ws_bytes(ctx, op->n, capacity, op->precision);
+    *fx = fx_eligible(ctx, op);
+    if (*fx) {
+        const size_t full = base + fx_ws_bytes(op);
+        if (ctx->opt.workspace_cap > 0 && full > (size_t)ctx->opt.workspace_cap) *fx = false;
+        else return full;
+    }
+    return base;
 }
 
 // One GKB run split into its launch sequence, so that several independent runs
@@ -541,6 +558,8 @@ struct GkbRun {
     int G = 0, chT = 0, chN = 0, rmax = 0, bar_group = 0, bar_k = 0, j_begin = 1;
     double *part = nullptr, *vr = nullptr, *vp = nullptr, *hpart = nullptr, *gpart = nullptr, *npart = nullptr;
     float *vr32 = nullptr, *vp32 = nullptr, *X32 = nullptr;  // X32: FP32 node coordinates (matrix-free FP32)
+    FxCopies fx;              // fixed-point copies of A (use_fx)
+    bool use_fx = false;
     bool f32slots = false;    // the products' partials are FP32 slots (mf_slots_f32)
     double slot_scale = 1.0;  // their scale
     unsigned* bar = nullptr;
@@ -557,10 +576,18 @@ struct GkbRun {
         G = slab_grid(ctx, n);
         if ((n + G - 1) / G > SL_MAX_ROWS) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "n too large for slab kernels");
         if (st->capacity + 1 > 1024) return rbf_fail(ctx, RBF_ERR_UNSUPPORTED, "capacity above 1023 steps");
-        RBF_TRY(rbf_ws_reserve(ctx, gkb_ws_bytes(ctx, n, st->capacity, op->precision)));
+        {
+            const size_t need = run_ws_bytes(ctx, op, st->capacity, &use_fx);
+            const rbf_status e = rbf_ws_reserve(ctx, need);
+            if (e != RBF_OK) {
+                if (!use_fx) return e;
+                use_fx = false;  // no room for the fixed-point copies: FP64 FMA products
+                RBF_TRY(rbf_ws_reserve(ctx, gkb_ws_bytes(ctx, n, st->capacity, op->precision)));
+            }
+        }
         WsCarve wc(ctx->ws);
         chT = product_chunks(ctx, op, 1);
-        chN = product_chunks(ctx, op, 0);
+        chN = use_fx ? fx_n_chunks(ctx, n) : product_chunks(ctx, op, 0);
         f32slots = mf_slots_f32(ctx, op);
         slot_scale = op->form == RBF_FORM_EPS ? 1.0 / op->c : 1.0;
         const int prow = op->storage == RBF_MATRIX_FREE ? mf_part_rows(ctx, op) : 0;
@@ -598,6 +625,10 @@ struct GkbRun {
                                                (int)HALF_SMEM_STAGE_MAX));
         }
         npart = wc.take<double>((size_t)G);
+        if (use_fx) {
+            fx = fx_carve(wc, op);
+            RBF_TRY(launch_fx_prepare(ctx, op, fx));
+        }
         mixed = op->precision == RBF_MIXED;
         rbf_dev_state* dst = ctx->d_state;
         epochs = 0;
@@ -676,11 +707,11 @@ struct GkbRun {
         double* Z = st->d_Z;
         const int64_t ldw = st->ldw, ldz = st->ldz;
         // ---------------- r-side: r = A^T w_j - beta_j z_{j-1} ----------------
-        RBF_TRY(gkb_product(ctx, op, 1, q_raw, vp32, X32, part, done));
+        RBF_TRY(gkb_product(ctx, op, 1, q_raw, vp32, X32, use_fx ? &fx : nullptr, part, done));
         RBF_TRY(half(0, j, (j == j_begin && j_begin > 1) ? 1 : 0, j >= 2 ? Z + (int64_t)(j - 2) * ldz : nullptr,
                      q_raw, W + (int64_t)(j - 1) * ldw, vr, mixed ? vr32 : nullptr, Z, ldz, j - 1, chT));
         // ---------------- p-side: p = A z_j - alpha_j w_j ----------------
-        RBF_TRY(gkb_product(ctx, op, 0, vr, vr32, X32, part, done));
+        RBF_TRY(gkb_product(ctx, op, 0, vr, vr32, X32, use_fx ? &fx : nullptr, part, done));
         RBF_TRY(half(1, j, 0, W + (int64_t)(j - 1) * ldw, vr, Z + (int64_t)(j - 1) * ldz, vp,
                      mixed ? vp32 : nullptr, W, ldw, j, chN));
         q_raw = vp;
@@ -791,7 +822,8 @@ extern "C" rbf_status rbf_gkb_many(rbf_ctx* ctx, int count, const rbf_operator* 
         const int64_t n = ops[i].n;
         const int G = slab_grid(ctx, n);
         const int rmax = (int)((n + G - 1) / G) | 1;
-        const int chmax = std::max(product_chunks(ctx, &ops[i], 0), product_chunks(ctx, &ops[i], 1));
+        int chmax = std::max(product_chunks(ctx, &ops[i], 0), product_chunks(ctx, &ops[i], 1));
+        if (fx_eligible(ctx, &ops[i])) chmax = std::max(chmax, fx_n_chunks(ctx, n));
         const size_t need = half_smem_bytes(false, states[i].capacity + 1, chmax, rmax, mf_slots_f32(ctx, &ops[i]));
         if (need > HALF_SMEM_STAGE_MAX) continue;  // the run itself is refused with RBF_ERR_UNSUPPORTED below
         int per_sm = 0;
@@ -822,11 +854,17 @@ extern "C" rbf_status rbf_gkb_many(rbf_ctx* ctx, int count, const rbf_operator* 
     for (int l = 0; l < L; ++l) RBF_TRY(rbf_lane(ctx, l, &lane[l]));
     // workspace sized once per lane for the largest of its runs (growing it
     // between runs would synchronise the lane)
+    // (with the fixed-point copies of A where they fit; a lane without room
+    // for them runs its FP64 assembled products with FMAs, see GkbRun::begin)
     for (int l = 0; l < L; ++l) {
-        size_t need = 0;
-        for (int i = l; i < count; i += L)
-            need = std::max(need, gkb_ws_bytes(lane[l], ops[i].n, states[i].capacity, ops[i].precision));
+        size_t need = 0, base = 0;
+        for (int i = l; i < count; i += L) {
+            bool fx_i = false;
+            need = std::max(need, run_ws_bytes(lane[l], &ops[i], states[i].capacity, &fx_i));
+            base = std::max(base, gkb_ws_bytes(lane[l], ops[i].n, states[i].capacity, ops[i].precision));
+        }
         rbf_status e = rbf_ws_reserve(lane[l], need);
+        if (e != RBF_OK && need > base) e = rbf_ws_reserve(lane[l], base);
         if (e != RBF_OK) {
             rbf_lanes_join(ctx, L);
             return rbf_fail(ctx, e, "lane %d: %s", l, rbf_last_error(lane[l]));

@@ -104,6 +104,7 @@ unsigned rbf_check_take_batch();
 unsigned rbf_check_take_select();
 unsigned rbf_check_take_assemble();
 unsigned rbf_check_take_mf();
+unsigned rbf_check_take_fx();
 rbf_status rbf_check_all(rbf_ctx* ctx);
 
 #define RBF_CUDA(ctx, call)                                                             \
@@ -178,6 +179,29 @@ rbf_status launch_gemv_n(rbf_ctx* ctx, const rbf_operator* op, const double* x, 
 rbf_status launch_gemv_t_partial(rbf_ctx* ctx, const rbf_operator* op, const double* x,
                                  const float* x32, double* part, const int* done);
 rbf_status launch_reduce_partials(rbf_ctx* ctx, int64_t n, int chunks, const double* part, double* y);
+// Flat split of an n x n matrix over at most Wmax warps (flat_bound): the warps
+// used and the most pieces a row is split into (at most 8).
+void flat_split_plan(int64_t n, int64_t Wmax, int64_t* W, int* chunks);
+// Column panels x row chunks of the A^T x kernels (vec columns per thread).
+void plan_t(const rbf_ctx* ctx, int64_t n, int vec, int* panel_cols, int* panels, int* chunks);
+// fx.cu: the FP64 assembled GKB products in exact integer fixed point, from two
+// int64 copies of A (row-scaled NR for A z, column-scaled NC for A^T w) made
+// once per GKB run, and the largest exponent field of each row / column.
+struct FxCopies {
+    long long* NR = nullptr;
+    long long* NC = nullptr;
+    int* rowE = nullptr;
+    int* colE = nullptr;
+};
+bool fx_eligible(const rbf_ctx* ctx, const rbf_operator* op);
+size_t fx_ws_bytes(const rbf_operator* op);
+FxCopies fx_carve(WsCarve& wc, const rbf_operator* op);
+int fx_n_chunks(const rbf_ctx* ctx, int64_t n);  // partial rows of the fixed-point A z (<= 8)
+rbf_status launch_fx_prepare(rbf_ctx* ctx, const rbf_operator* op, const FxCopies& f);
+rbf_status launch_fx_n(rbf_ctx* ctx, const rbf_operator* op, const FxCopies& f, const double* x, double* part,
+                       const int* done);
+rbf_status launch_fx_t(rbf_ctx* ctx, const rbf_operator* op, const FxCopies& f, const double* x, double* part,
+                       const int* done);
 // mf.cu (matrix-free products, FP32 or FP64; partial sums over `mf_chunks` centre chunks)
 // Partial rows the consumer sums (mf_chunks) and rows the product writes
 // (mf_part_rows >= mf_chunks; the FP32 tile-pair product folds its slots).

@@ -34,7 +34,7 @@ class Options(C.Structure):
     _fields_ = [("grid_j", C.c_int), ("grid_t_lo", C.c_double), ("grid_t_hi", C.c_double),
                 ("breakdown_factor", C.c_double), ("cluster_tol", C.c_double),
                 ("workspace_cap", C.c_int64), ("timing", C.c_int), ("svd_method", C.c_int),
-                ("wait_budget", C.c_int64)]
+                ("wait_budget", C.c_int64), ("fma_products", C.c_int)]
 
 
 class Operator(C.Structure):
