@@ -60,6 +60,8 @@ FX_MAX_N = 16384  # FP64 assembled operators up to this size take the fixed-poin
 MEASURED_TRAFFIC = {
     ("cube8000", 0): 512.113e6 + 0.166e6,                      # k_gemv_flat_f64
     ("cube8000", 1): 512.116e6 + 4.010e6,                      # k_gemv_t_f64
+    ("cube8000-fx", 0): 512.184e6 + 3.377e6,                   # k_gemv_flat_fx
+    ("cube8000-fx", 1): 512.147e6 + 3.250e6,                   # k_gemv_t_fx
     ("sphere20000-mixed-assembled", 0): 1600.665e6 + 4.324e6,  # k_gemv_nseg_f32
     ("sphere20000-mixed-assembled", 1): 1600.146e6 + 3.266e6,  # k_gemv_t_f32
 }
