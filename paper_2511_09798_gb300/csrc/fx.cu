@@ -37,6 +37,8 @@
 // non-finite vector value sets its scale to 2047: the rows, columns or chunks
 // concerned come out NaN, as in FP64 arithmetic, so the GKB breakdown test
 // (code 3) sees them.
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -327,10 +329,13 @@ size_t fxn_smem(int64_t n) { return (size_t)3 * ((n + 1) & ~(int64_t)1) * sizeof
 
 // CTAs of k_gemv_flat_fx resident per SM at this n (cached per device for the
 // last n asked; the shared-memory limit is raised once to the largest size).
+// Contexts on different host threads share the cache, hence the mutex.
 int fxn_per_sm(const rbf_ctx* ctx, int64_t n) {
+    static std::mutex mu;
     static int64_t last_n[64] = {0};
     static int last_per[64] = {0};
     static bool raised[64] = {false};
+    std::lock_guard<std::mutex> lock(mu);
     const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
     if (last_n[dev] == n && last_per[dev] > 0) return last_per[dev];
     if (!raised[dev]) {
@@ -401,6 +406,10 @@ rbf_status launch_fx_prepare(rbf_ctx* ctx, const rbf_operator* op, const FxCopie
     const int64_t n = op->n;
     int pc, pn, ch, rows_max;
     fxt_plan(ctx, n, &pc, &pn, &ch, &rows_max);
+    // the exponent scan and the conversion cover 2 * FXE_THREADS columns per panel
+    if (pc != 2 * FXE_THREADS)
+        return rbf_fail(ctx, RBF_ERR_INTERNAL, "fixed-point copies: panel of %d columns, kernels cover %d", pc,
+                        2 * FXE_THREADS);
     RBF_CUDA(ctx, cudaMemsetAsync(f.rowE, 0, (size_t)n * sizeof(int), ctx->stream));
     RBF_CUDA(ctx, cudaMemsetAsync(f.colE, 0, (size_t)n * sizeof(int), ctx->stream));
     const size_t smem = (size_t)rows_max * sizeof(int);
