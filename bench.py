@@ -461,6 +461,9 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": wl["name"], "n": n, "n_interior": ns.n_interior, "gkb_steps": L,
                    "cases_c_k": cases, "solves_per_step": len(cases), "precision": wl["precision"],
                    "storage": wl["storage"], "rule": "gcv", "test_points": m,
+                   "products": ("int64 fixed point (exact sums, FP64 in and out)" if fixed_point
+                                else "FP64 FMA" if prec == R.RBF_FP64 and storage == R.RBF_ASSEMBLED
+                                else "matrix-free" if storage == R.RBF_MATRIX_FREE else "FP32"),
                    "parallelism": f"replicas x{world}; the step's independent solves on "
                                   f"{args.lanes or min(len(cases), 8)} streams",
                    "l2": "inputs larger than L2 (A or node set streamed each product)"},
